@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the elastic FDTD operator pair H, H^T on B300.
+
+One bench step = one time step of the forward operator H (velocity + phi,
+stress + psi, receiver sampling) and one time step of its adjoint H^T
+(transposed halves, receiver injection) over the full grid.  The timed region
+runs pact_forward over K time steps and then pact_adjoint over the resulting
+(K+1) x L traces: one application of H and one of H^T, as in one gradient
+evaluation of a least-squares reconstruction.
+
+Workload (default): the skull-like 512^3 grid, dx 0.2 mm, 20-cell C-PML,
+1024 hemisphere receivers, dt at CFL 0.3.  Inputs are synthetic and seeded.
+The nine wavefield arrays (537 MB each) exceed the 126 MB L2, so no L2 flush is
+needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (weak scaling, no collective on the data
+path); value = updates of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elastic FDTD grid-pt updates/s (fwd+adj)"
+UNIT = "grid-pt updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["skull-512", "skull-256", "skull-192"], default="skull-512")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_1709_02733_b300 import synth
+    return {"skull-512": synth.skull_512, "skull-256": synth.skull_256, "skull-192": synth.skull_192}[name]()
+
+
+def workload_config(w, name):
+    d = w.desc
+    return {
+        "workload": f"{name}: {d.nx}^3 skull-like elastic medium (water / 7 mm shell / tissue), dx {d.dx * 1e3:.2f} mm, "
+                    f"dt {d.dt * 1e9:.2f} ns, {d.npml}-cell C-PML, {w.rec.shape[0]} hemisphere receivers, "
+                    f"forward + adjoint",
+        "grid": [d.nx, d.ny, d.nz],
+        "receivers": int(w.rec.shape[0]),
+        "npml": d.npml,
+        "full_solve_steps": w.nsteps,
+        "l2": "no flush: inputs larger than L2 (9 wavefield arrays of %.0f MB each)" % (d.N * 4 / 1e6),
+    }
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes of each kernel role (one launch over the whole grid)
+# --------------------------------------------------------------------------
+def slab_points(d):
+    if d.npml <= 0:
+        return [0, 0, 0]
+    W = 2 * d.npml + 1
+    return [d.nz * d.ny * W, d.nz * W * d.nx, W * d.ny * d.nx]
+
+
+def algorithmic_bytes(kind, d, L):
+    """Compulsory DRAM bytes of one launch: every array the kernel must read
+    once and write once (neighbour reads served from cache are not counted)."""
+    N = d.N
+    S = sum(slab_points(d))
+    f = 4
+    if kind == "fwd_velocity":   # read 6 sigma, 3 u, rho, alpha; write 3 u; phi^{ij} r+w on slabs
+        return f * (11 * N + 3 * N) + 2 * f * 3 * S
+    if kind == "fwd_stress":     # read 3 u, 6 sigma, lambda, mu; write 6 sigma; psi^{ij} r+w on slabs
+        return f * (11 * N + 6 * N) + 2 * f * 3 * S
+    if kind == "adj_a":          # read 6 sigma, lambda, mu, 3 u, rho, alpha; write 3 u; psi read, phi r+w
+        return f * (13 * N + 3 * N) + f * 3 * S + 2 * f * 3 * S
+    if kind == "adj_b":          # read 3 u, rho, 6 sigma; write 6 sigma; lambda, mu, phi read, psi r+w on slabs
+        return f * (10 * N + 6 * N) + f * 2 * S + f * 3 * S + 2 * f * 3 * S
+    if kind == "sample":
+        return f * (3 * 8 * L + L) + 8 * 8 * L
+    if kind == "inject":
+        return f * (2 * 3 * 8 * L + L) + 8 * 8 * L
+    return 0
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1709_02733_b300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kind):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+    except Exception:
+        return None
+    e = t.get(kind)
+    if not e or e.get("source_sha") != source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "of measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "of fallback"
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+def crop_workload(w, n):
+    import numpy as np
+    from paper_1709_02733_b300.synth import GridDesc
+    c = w.desc.nx // 2
+    lo = c - n // 2
+    sl = (slice(lo, lo + n),) * 3
+    d = GridDesc(n, n, n, w.desc.dx, w.desc.dt, npml=min(w.desc.npml, max(0, (n - 2) // 2 - 1)),
+                 pml_vmax=w.desc.pml_vmax)
+    med = [np.ascontiguousarray(m[sl]) for m in w.medium]
+    return d, med, np.ascontiguousarray(w.p0[sl])
+
+
+def oracle_rate(w, n, fwd_steps, adj_steps, max_seconds=None):
+    """Time the oracle's own forward step and transposed step on an n^3 crop of
+    the workload; returns (updates/s, steps done, seconds)."""
+    from oracle import Oracle
+    d, med, p0 = crop_workload(w, n)
+    o = Oracle(d.as_dict(), *med)
+    st = o.inject(p0)
+    st2 = o.inject(p0)
+    done, t = 0, 0.0
+    for k in range(max(fwd_steps, adj_steps)):
+        if k < fwd_steps:
+            t0 = time.perf_counter()
+            o.step(st)
+            t += time.perf_counter() - t0
+            done += 1
+        if k < adj_steps:
+            t0 = time.perf_counter()
+            o.step_T(st2)
+            t += time.perf_counter() - t0
+            done += 1
+        if max_seconds is not None and t > max_seconds:
+            break
+    return done * d.N / t, done, t, d
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline(w):
+    import oracle
+    oracle.build()
+    rate, done, t, d = oracle_rate(w, 256 if w.desc.nx >= 256 else w.desc.nx, 10, 10, max_seconds=20.0)
+    return {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"FP64 C oracle (OpenMP) on the central {d.nx}^3 crop of the workload "
+                      f"({d.npml}-cell C-PML), {done} single time steps alternating forward W' and "
+                      f"transposed W'^T, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = make_workload(args.workload)
+    # calibrate, then size the crop so the whole run takes about two minutes
+    r0, _, _, _ = oracle_rate(w, 64, 1, 1)
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    n = int(max(24, min(256, w.desc.nx, (per_step * r0 / 2.0) ** (1.0 / 3.0))))
+    from oracle import Oracle
+    d, med, p0 = crop_workload(w, n)
+    o = Oracle(d.as_dict(), *med)
+    st = o.inject(p0)
+    st2 = o.inject(p0)
+    for _ in range(args.warmup):
+        o.step(st)
+        o.step_T(st2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(st)
+        o.step_T(st2)
+    t = time.perf_counter() - t0
+    value = 2.0 * d.N * args.steps / t
+    sample = (f"FP64 C oracle on the central {n}^3 crop of the {args.workload} workload; each step one forward "
+              f"W' and one transposed W'^T time step")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(w, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_02733_b300 import build as pbuild
+    from paper_1709_02733_b300 import pact
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = make_workload(args.workload)
+    d = w.desc
+    K, W = args.steps, args.warmup
+    L = w.rec.shape[0]
+    stream = torch.cuda.current_stream()
+    g = pact.Grid(d, stream=stream)
+    g.set_medium(*[torch.from_numpy(m).cuda() for m in w.medium])
+    p0 = torch.from_numpy(w.p0).cuda()
+    traces = torch.empty((K + 1, L), device="cuda")
+    image = torch.empty(d.shape, device="cuda")
+
+    # warm-up
+    wt = g.forward(p0, w.rec, W)
+    g.adjoint(wt, w.rec)
+    torch.cuda.synchronize()
+
+    # timed region: H over K steps, then H^T over the K+1 samples
+    g.profile(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.forward(p0, w.rec, K, out=traces)
+    g.adjoint(traces, w.rec, out=image)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    prof = g.profile_read()
+    g.profile(False)
+    updates = 2.0 * d.N * K * world
+    value = updates / (ms * 1e-3)
+
+    # roofline of the dominant kernel (measured live over the timed region)
+    steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b"]
+    dom = max(steps_kinds, key=lambda k: prof[k][1])
+    n_launch, dom_ms = prof[dom]
+    avg_s = dom_ms * 1e-3 / max(n_launch, 1)
+    alg = algorithmic_bytes(dom, d, L)
+    pk, which = peaks()
+    achieved = alg / avg_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "peak_source": which + " (hbm_gbs, STREAM-style copy)",
+                "traffic": traffic_for(dom), "algorithmic_bytes_per_launch": alg,
+                "avg_launch_ms": avg_s * 1e3, "bytes_per_update": alg / d.N}
+    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+
+    # end to end through the host-pointer C-ABI calls (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        hp0 = torch.from_numpy(w.p0).pin_memory().numpy()
+        htr = torch.empty((K + 1, L), dtype=torch.float32).pin_memory().numpy()
+        him = torch.empty(d.shape, dtype=torch.float32).pin_memory().numpy()
+        barrier()
+        t0 = time.perf_counter()
+        g.forward_host(hp0, w.rec, K, out=htr)
+        g.adjoint_host(htr, w.rec, out=him)
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": updates / te, "unit": UNIT, "h2d_bytes_per_step": (d.N * 4 + (K + 1) * L * 4) / K,
+               "d2h_bytes_per_step": ((K + 1) * L * 4 + d.N * 4) / K,
+               "note": "pact_forward_host + pact_adjoint_host: p0 in, traces out, traces in, image out"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded skull-like medium, vessel tubes, Fibonacci receivers)",
+                "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}"),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "kernels": kernels, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * pact.h -- C ABI of libpact.so: the elastic-wave photoacoustic forward
+ * operator H and its exact discrete adjoint H^T on one NVIDIA B300 (sm_103a).
+ *
+ * The operator pair follows Mitsuhashi et al., "A forward-adjoint operator pair
+ * based on the elastic wave equation for use in transcranial photoacoustic
+ * computed tomography": H maps an initial pressure p0 to receiver traces
+ * through the staggered-grid velocity-stress FDTD recursion with a
+ * convolutional PML (Appendix A.3, Eq. (HPML)); H^T is its matrix transpose
+ * applied by the backward recursion of Eq. (AdjupPML).
+ *
+ * Conventions shared by every call
+ *  - Grid: nx * ny * nz vertices, spacing dx [m]; every 3-D array is float32,
+ *    C order [z][y][x] (x fastest), N = nx*ny*nz entries.  This is the
+ *    lexicographic order of the paper's field vectors (Sec. 2.2).
+ *  - Staggering (Sec. 2.2): p0, rho, lambda, mu, alpha and the normal stresses
+ *    at integer nodes (i,j,k); u^1 at (i+1/2,j,k), u^2 at (i,j+1/2,k),
+ *    u^3 at (i,j,k+1/2); sigma^23, sigma^13, sigma^12 at the matching two-half
+ *    positions.  rho and alpha are averaged arithmetically onto the velocity
+ *    nodes, mu harmonically onto the shear nodes.  Values outside the grid are
+ *    zero (zero padding).
+ *  - Receivers: rec_xyz is a HOST array of L float triples (x, y, z) in
+ *    grid-index units on the integer lattice; each must satisfy
+ *    0 <= x <= nx-2 (same for y, z).  Sampling is trilinear (Eq. (interpgrid)).
+ *  - Traces: float32 [(nsteps+1)][L], time-major: row m is p_hat_m, the
+ *    negative sum of the three normal stresses at time m*dt (Sec. 2.3).
+ *  - Source: sigma^11 = sigma^22 = sigma^33 = -p0/3 at t = 0, everything else
+ *    zero (Eq. (Ini)); so row 0 of the traces is the trilinear interpolant of p0.
+ *  - Device pointers (p0, traces, image, medium arrays) must be cudaMalloc'd or
+ *    torch CUDA memory on the handle's device; the caller keeps ownership.
+ *  - Every compute call is asynchronous and ordered on the handle's stream;
+ *    host-pointer variants (*_host) copy in and out and return after the
+ *    stream has finished.  A handle must not be used from two host threads at
+ *    once.  No C++ exception crosses this interface.
+ *  - Errors: every call returns a PACT_* code; pact_last_error(h) gives the
+ *    message of the last failure on h (pact_last_error(NULL) the last failure
+ *    of a call that had no valid handle).
+ */
+#ifndef PACT_H
+#define PACT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PACT_OK 0
+#define PACT_EINVAL 1   /* bad dimensions, pointers, receivers or sizes            */
+#define PACT_ECFL 2     /* c_max * dt / dx >= 6 / (7 sqrt 3) (4th-order stability) */
+#define PACT_ENOMEM 3   /* device allocation failed                                */
+#define PACT_ECUDA 4    /* a CUDA runtime call failed (message has the detail)     */
+#define PACT_ETIMEOUT 5 /* a bounded device wait expired                           */
+#define PACT_ESTATE 6   /* call out of order (e.g. forward before set_medium)      */
+
+typedef struct pact_grid* pact_handle;
+
+/* Grid and time step of one operator pair.  C-PML (Appendix A.1-A.3, kappa = 1):
+ * layer npml cells thick on every face; damping d(s) = d0 (s/npml)^2 with
+ * d0 = -3 vmax ln(R0) / (2 npml dx), s the depth into the layer in cells;
+ * frequency shift beta(s) = pi f0 (1 - s/npml).  pml_vmax <= 0 means "use the
+ * largest compressional speed of the medium". */
+typedef struct {
+    int nx, ny, nz;   /* vertices per axis, each >= max(4, 2*npml + 2)             */
+    double dx;        /* grid spacing [m]                                          */
+    double dt;        /* time step [s]                                             */
+    int npml;         /* C-PML thickness in cells (0: zero-padded boundary)        */
+    double pml_R0;    /* nominal normal-incidence reflection, e.g. 1e-4            */
+    double pml_f0;    /* CFS shift frequency [Hz], e.g. 1e6                        */
+    double pml_vmax;  /* speed scaling the damping [m/s]; <= 0: medium maximum     */
+} pact_grid_desc;
+
+/* Create a handle for one grid (Sec. 2.2 discretisation).  Allocates the
+ * wavefield (9 arrays of N floats), the medium copy (4 x N), the C-PML memory
+ * variables (18 arrays, stored only on the layer slabs) and the profile tables
+ * on the current CUDA device.  stream: a cudaStream_t (NULL = legacy default
+ * stream) on which every later call of this handle is ordered.
+ * Errors: PACT_EINVAL (bad desc or out == NULL), PACT_ENOMEM, PACT_ECUDA. */
+int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out);
+
+/* Copy the medium into the handle: density rho [kg/m^3] > 0, Lame lambda and
+ * mu [Pa] (mu >= 0, lambda + 2 mu > 0), absorption alpha [1/s] >= 0, all
+ * device arrays of N floats at the integer nodes (Sec. 2.1, Eq. (Elastic)).
+ * Builds the C-PML profile tables.  Synchronises the stream (it reduces the
+ * medium to check it).  Errors: PACT_EINVAL (NULL pointer or a value out of
+ * range), PACT_ECFL (c_max dt / dx >= 6/(7 sqrt 3), or alpha dt >= 1),
+ * PACT_ECUDA. */
+int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const float* mu,
+                    const float* alpha);
+
+/* p_hat = H p0 (Eq. (H); with the C-PML Eq. (HPML)): load sigma^ii = -p0/3,
+ * sample p_hat_0, then nsteps times apply one leapfrog step (velocity and
+ * memory variables phi, then stress and memory variables psi; Appendix A.3) and
+ * sample.  p0: device, N floats.  traces: device, (nsteps+1)*L floats,
+ * overwritten.  nsteps >= 0, L >= 1.  Errors: PACT_EINVAL, PACT_ESTATE (no
+ * medium), PACT_ECUDA. */
+int pact_forward(pact_handle h, const float* p0, const float* rec_xyz, int L, int nsteps, float* traces);
+
+/* p_adj = H^T p_hat (Eq. (adjHPML)) by the backward recursion of Eq. (AdjupPML):
+ * v = Theta^T p_hat_{nsteps}; for m = nsteps..1: v = W^T v + Theta^T p_hat_{m-1};
+ * p_adj = tau^T v = -(sigma^11 + sigma^22 + sigma^33)/3.  W^T applies the
+ * transposed sub-updates in reverse order (Sec. 4, Eq. (backwardstep)).
+ * traces: device, (nsteps+1)*L floats (read only).  image: device, N floats,
+ * overwritten.  Errors as pact_forward. */
+int pact_adjoint(pact_handle h, const float* traces, const float* rec_xyz, int L, int nsteps, float* image);
+
+/* Same as pact_forward / pact_adjoint with HOST p0 / traces / image buffers:
+ * copies in, runs, copies out, and returns after the stream has finished.
+ * Device staging buffers are owned by the handle and reused. */
+int pact_forward_host(pact_handle h, const float* p0, const float* rec_xyz, int L, int nsteps, float* traces);
+int pact_adjoint_host(pact_handle h, const float* traces, const float* rec_xyz, int L, int nsteps, float* image);
+
+/* Release everything the handle owns (waits for its stream first). */
+int pact_destroy(pact_handle h);
+
+/* Message of the last failure on h (or of a handle-less call for h == NULL).
+ * The pointer stays valid until the next failing call on the same handle. */
+const char* pact_last_error(pact_handle h);
+
+/* Device bytes a handle with this desc will allocate (fields, medium, C-PML
+ * slabs and tables, receiver tables for L receivers).  Used for admission
+ * against a memory budget.  Errors: PACT_EINVAL. */
+int pact_query_bytes(const pact_grid_desc* desc, int L, int nsteps, size_t* bytes);
+
+/* Diagnostics: copy the current wavefield to HOST memory, 9*N floats in the
+ * order u^1, u^2, u^3, sigma^11, sigma^22, sigma^33, sigma^23, sigma^13, sigma^12
+ * (Sec. 2.2 vectors u_bar, sigma_bar).  Synchronises the stream. */
+int pact_get_wavefield(pact_handle h, float* host_out);
+
+/* Measurement support (not part of the method).  Kernel roles counted and
+ * timed by pact_profile / pact_profile_read. */
+#define PACT_K_FWD_VELOCITY 0 /* velocity + phi update of one forward step        */
+#define PACT_K_FWD_STRESS 1   /* stress + psi update of one forward step          */
+#define PACT_K_ADJ_A 2        /* velocity-side half of one adjoint step           */
+#define PACT_K_ADJ_B 3        /* stress-side half of one adjoint step             */
+#define PACT_K_SAMPLE 4       /* receiver sampling Theta                          */
+#define PACT_K_INJECT 5       /* receiver injection Theta^T                       */
+#define PACT_K_SOURCE 6       /* source tau                                       */
+#define PACT_K_READOUT 7      /* read-out tau^T                                   */
+#define PACT_NKIND 8
+
+/* Reset this handle's launch counters and, if enable != 0, start recording a
+ * CUDA event after every kernel launch on the handle's stream (so a launch's
+ * device time is the time since the previous event; the stream is busy between
+ * consecutive launches of one call).  Synchronises the stream. */
+int pact_profile(pact_handle h, int enable);
+
+/* Launches of one kernel role since pact_profile, and their summed device time
+ * in milliseconds (0 if recording was off).  Synchronises the stream.
+ * Errors: PACT_EINVAL (kind out of range or NULL output). */
+int pact_profile_read(pact_handle h, int kind, long long* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PACT_H */

@@ -1,0 +1,587 @@
+// pact_abi.cu -- host side of the C ABI declared in include/pact.h.
+//
+// A handle owns, on one device: the wavefield (9 x N floats), a copy of the
+// medium (4 x N), the C-PML memory variables on the layer slabs, the 1-D C-PML
+// profile tables, the receiver tables and staging buffers for the host-pointer
+// calls.  All work is queued on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pact.h"
+#include "pact_internal.cuh"
+
+void launch_fwd_velocity(const StepParams& p, cudaStream_t st);
+void launch_fwd_stress(const StepParams& p, cudaStream_t st);
+void launch_adj_a(const StepParams& p, cudaStream_t st);
+void launch_adj_b(const StepParams& p, cudaStream_t st);
+void launch_source(const float* p0, const StepParams& p, cudaStream_t st);
+void launch_readout(float* img, const StepParams& p, cudaStream_t st);
+void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStream_t st);
+void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st);
+void launch_medium_check(const float* rho, const float* lam, const float* mu, const float* alpha, size_t n,
+                         unsigned int* out, cudaStream_t st);
+
+namespace {
+
+thread_local std::string g_err;
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pact_grid {
+    pact_grid_desc d{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t N = 0;
+    float* fields = nullptr;      // 9N
+    float* medium = nullptr;      // 4N
+    float* tables = nullptr;      // 3 axes x 2 lattices x 3 (a,b,chi) x nmax
+    int nmax = 0;
+    float* slabs[3] = {nullptr, nullptr, nullptr};  // 6 x slab size per axis
+    size_t slab_n[3] = {0, 0, 0};
+    unsigned int* scratch_u32 = nullptr;            // medium-check reduction
+    bool medium_set = false;
+    double cmax = 0.0;
+    // receivers
+    std::vector<float> rec_host;
+    int L = 0;
+    int rec_cap = 0;
+    int* rec_corner = nullptr;
+    float* rec_weight = nullptr;
+    int ncorner = 0;
+    int* inj_point = nullptr;
+    int* inj_off = nullptr;
+    int* inj_rec = nullptr;
+    float* inj_w = nullptr;
+    // staging for *_host calls
+    float* stage_a = nullptr;
+    size_t stage_a_n = 0;
+    float* stage_b = nullptr;
+    size_t stage_b_n = 0;
+    // launch accounting and optional per-launch events (pact_profile)
+    long long launches[PACT_NKIND] = {};
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;  // kind of the launch that ends at event i (-1: origin)
+    std::string err;
+};
+
+static int fail(pact_handle h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    g_err = msg;
+    return code;
+}
+
+#define CK(h, call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? PACT_ENOMEM : PACT_ECUDA,     \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+// Count a launch of `kind`; in profile mode record an event after it on the
+// stream, so that the launch's duration is the time since the previous event.
+static void mark(pact_handle h, int kind) {
+    if (kind >= 0) h->launches[kind]++;
+    if (!h->prof) return;
+    const size_t i = h->ev_kind.size();
+    if (i >= h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            h->prof = false;
+            return;
+        }
+        h->ev_pool.push_back(e);
+    }
+    cudaEventRecord(h->ev_pool[i], h->stream);
+    h->ev_kind.push_back(kind);
+}
+
+static size_t slab_points(const pact_grid_desc& d, int axis) {
+    if (d.npml <= 0) return 0;
+    const size_t W = 2 * (size_t)d.npml + 1;
+    if (axis == 0) return (size_t)d.nz * d.ny * W;
+    if (axis == 1) return (size_t)d.nz * W * d.nx;
+    return W * d.ny * d.nx;
+}
+
+static int check_desc(const pact_grid_desc* d, std::string& why) {
+    if (!d) { why = "desc is NULL"; return PACT_EINVAL; }
+    if (d->npml < 0) { why = "npml < 0"; return PACT_EINVAL; }
+    const int need = std::max(4, 2 * d->npml + 2);
+    if (d->nx < need || d->ny < need || d->nz < need) {
+        why = "every grid dimension must be >= max(4, 2*npml+2)";
+        return PACT_EINVAL;
+    }
+    if (!(d->dx > 0) || !(d->dt > 0) || !std::isfinite(d->dx) || !std::isfinite(d->dt)) {
+        why = "dx and dt must be positive";
+        return PACT_EINVAL;
+    }
+    if ((size_t)d->nx * d->ny * d->nz >= (size_t)1 << 31) {
+        why = "grid too large (N must be < 2^31)";
+        return PACT_EINVAL;
+    }
+    if (d->npml > 0 && (!(d->pml_R0 > 0 && d->pml_R0 < 1) || !(d->pml_f0 >= 0))) {
+        why = "C-PML needs 0 < pml_R0 < 1 and pml_f0 >= 0";
+        return PACT_EINVAL;
+    }
+    return PACT_OK;
+}
+
+static size_t desc_bytes(const pact_grid_desc& d, int L, int nsteps) {
+    const size_t N = (size_t)d.nx * d.ny * d.nz;
+    size_t b = 13 * N * sizeof(float);  // fields + medium
+    for (int a = 0; a < 3; ++a) b += 6 * slab_points(d, a) * sizeof(float);
+    const int nmax = std::max(d.nx, std::max(d.ny, d.nz));
+    b += 18 * (size_t)nmax * sizeof(float) + 16;
+    if (L > 0) b += (size_t)L * 8 * (4 + 4 + 4 + 4 + 4 + 4) + 4;  // corner, weight, inj tables
+    if (L > 0 && nsteps >= 0) b += (N + (size_t)(nsteps + 1) * L) * sizeof(float);  // host-call staging
+    return b;
+}
+
+// C-PML 1-D profile (Appendix A.1, kappa = 1) at grid coordinate pos on an axis of n nodes.
+static void pml_coef(int n, int P, double dx, double dt, double vmax, double R0, double f0, double pos,
+                     double& a, double& b, double& chi) {
+    a = 0.0;
+    b = 1.0;
+    chi = 0.0;
+    if (P <= 0) return;
+    double s = 0.0;
+    if (pos < P) s = P - pos;
+    else if (pos > n - 1 - P) s = pos - (n - 1 - P);
+    if (s <= 0.0) return;
+    s = std::min(s, (double)P);
+    const double d0 = -3.0 * vmax * std::log(R0) / (2.0 * P * dx);
+    const double r = s / P;
+    const double dd = d0 * r * r;
+    const double beta = M_PI * f0 * (1.0 - r);
+    b = std::exp(-(dd + beta) * dt);
+    a = (dd + beta) > 0.0 ? dd * (b - 1.0) / (dd + beta) : 0.0;
+    chi = 1.0;
+}
+
+static StepParams make_params(pact_handle h) {
+    StepParams p{};
+    const pact_grid_desc& d = h->d;
+    p.nx = d.nx;
+    p.ny = d.ny;
+    p.nz = d.nz;
+    p.P = d.npml;
+    p.dt = (float)d.dt;
+    p.inv_dx = (float)(1.0 / d.dx);
+    for (int i = 0; i < 3; ++i) p.u[i] = h->fields + i * h->N;
+    for (int v = 0; v < 6; ++v) p.s[v] = h->fields + (3 + v) * h->N;
+    p.rho = h->medium;
+    p.lam = h->medium + h->N;
+    p.mu = h->medium + 2 * h->N;
+    p.alpha = h->medium + 3 * h->N;
+    for (int a = 0; a < 3; ++a)
+        for (int l = 0; l < 2; ++l)
+            for (int w = 0; w < 3; ++w) p.tab[a][l][w] = h->tables + ((a * 2 + l) * 3 + w) * (size_t)h->nmax;
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+            p.phi[i][j] = h->slabs[j] ? h->slabs[j] + i * h->slab_n[j] : nullptr;
+            p.psi[i][j] = h->slabs[j] ? h->slabs[j] + (3 + i) * h->slab_n[j] : nullptr;
+        }
+    return p;
+}
+
+static RecTable make_rec(pact_handle h) {
+    RecTable r{};
+    r.L = h->L;
+    r.corner = h->rec_corner;
+    r.weight = h->rec_weight;
+    r.ncorner = h->ncorner;
+    r.inj_point = h->inj_point;
+    r.inj_off = h->inj_off;
+    r.inj_rec = h->inj_rec;
+    r.inj_w = h->inj_w;
+    return r;
+}
+
+static void free_rec(pact_handle h) {
+    cudaFree(h->rec_corner);
+    cudaFree(h->rec_weight);
+    cudaFree(h->inj_point);
+    cudaFree(h->inj_off);
+    cudaFree(h->inj_rec);
+    cudaFree(h->inj_w);
+    h->rec_corner = nullptr;
+    h->rec_weight = nullptr;
+    h->inj_point = h->inj_off = h->inj_rec = nullptr;
+    h->inj_w = nullptr;
+    h->rec_cap = 0;
+}
+
+// Validate the HOST receiver array and (re)build the device tables when it changed.
+static int set_receivers(pact_handle h, const float* rec, int L) {
+    if (!rec || L < 1) return fail(h, PACT_EINVAL, "receivers: rec_xyz must be non-NULL and L >= 1");
+    const pact_grid_desc& d = h->d;
+    const int lim[3] = {d.nx - 2, d.ny - 2, d.nz - 2};
+    for (int l = 0; l < L; ++l)
+        for (int a = 0; a < 3; ++a) {
+            const float v = rec[3 * l + a];
+            if (!std::isfinite(v) || v < 0.0f || v > (float)lim[a]) {
+                char buf[160];
+                snprintf(buf, sizeof buf, "receiver %d coordinate %d = %g outside [0, %d]", l, a, (double)v, lim[a]);
+                return fail(h, PACT_EINVAL, buf);
+            }
+        }
+    if (L == h->L && !h->rec_host.empty() && std::memcmp(h->rec_host.data(), rec, sizeof(float) * 3 * L) == 0)
+        return PACT_OK;
+    // host tables
+    std::vector<int> corner(8 * (size_t)L);
+    std::vector<float> weight(8 * (size_t)L);
+    struct Contrib {
+        int point, rec;
+        float w;
+    };
+    std::vector<Contrib> con(8 * (size_t)L);
+    for (int l = 0; l < L; ++l) {
+        const double x = rec[3 * l], y = rec[3 * l + 1], z = rec[3 * l + 2];
+        const int i0 = std::min((int)std::floor(x), d.nx - 2);
+        const int j0 = std::min((int)std::floor(y), d.ny - 2);
+        const int k0 = std::min((int)std::floor(z), d.nz - 2);
+        const double fx = x - i0, fy = y - j0, fz = z - k0;
+        int c = 0;
+        for (int cz = 0; cz < 2; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx, ++c) {
+                    const double w = (cx ? fx : 1 - fx) * (cy ? fy : 1 - fy) * (cz ? fz : 1 - fz);
+                    const int q = ((k0 + cz) * d.ny + (j0 + cy)) * d.nx + (i0 + cx);
+                    corner[8 * l + c] = q;
+                    weight[8 * l + c] = (float)w;
+                    con[8 * l + c] = {q, l, (float)w};
+                }
+    }
+    std::stable_sort(con.begin(), con.end(), [](const Contrib& a, const Contrib& b) { return a.point < b.point; });
+    std::vector<int> ipoint, ioff, irec(con.size());
+    std::vector<float> iw(con.size());
+    for (size_t e = 0; e < con.size(); ++e) {
+        if (e == 0 || con[e].point != con[e - 1].point) {
+            ipoint.push_back(con[e].point);
+            ioff.push_back((int)e);
+        }
+        irec[e] = con[e].rec;
+        iw[e] = con[e].w;
+    }
+    ioff.push_back((int)con.size());
+    // device tables (grow only; wait for queued work before freeing)
+    if (L > h->rec_cap) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        free_rec(h);
+        const size_t E = 8 * (size_t)L;
+        CK(h, cudaMalloc(&h->rec_corner, E * sizeof(int)));
+        CK(h, cudaMalloc(&h->rec_weight, E * sizeof(float)));
+        CK(h, cudaMalloc(&h->inj_point, E * sizeof(int)));
+        CK(h, cudaMalloc(&h->inj_off, (E + 1) * sizeof(int)));
+        CK(h, cudaMalloc(&h->inj_rec, E * sizeof(int)));
+        CK(h, cudaMalloc(&h->inj_w, E * sizeof(float)));
+        h->rec_cap = L;
+    }
+    cudaStream_t s = h->stream;
+    CK(h, cudaMemcpyAsync(h->rec_corner, corner.data(), corner.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->rec_weight, weight.data(), weight.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->inj_point, ipoint.data(), ipoint.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->inj_off, ioff.data(), ioff.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->inj_rec, irec.data(), irec.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemcpyAsync(h->inj_w, iw.data(), iw.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    // pageable sources: the copies are staged before return, but keep the order
+    // explicit by waiting here (receivers change rarely)
+    CK(h, cudaStreamSynchronize(s));
+    h->ncorner = (int)ipoint.size();
+    h->L = L;
+    h->rec_host.assign(rec, rec + 3 * (size_t)L);
+    return PACT_OK;
+}
+
+static int zero_state(pact_handle h) {
+    CK(h, cudaMemsetAsync(h->fields, 0, 9 * h->N * sizeof(float), h->stream));
+    for (int a = 0; a < 3; ++a)
+        if (h->slabs[a]) CK(h, cudaMemsetAsync(h->slabs[a], 0, 6 * h->slab_n[a] * sizeof(float), h->stream));
+    return PACT_OK;
+}
+
+static int precheck(pact_handle h, const void* a, const void* b, int nsteps) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (!h->medium_set) return fail(h, PACT_ESTATE, "pact_set_medium must be called first");
+    if (!a || !b) return fail(h, PACT_EINVAL, "NULL data pointer");
+    if (nsteps < 0) return fail(h, PACT_EINVAL, "nsteps < 0");
+    CK(h, cudaSetDevice(h->device));
+    return PACT_OK;
+}
+
+static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps) {
+    int rc = zero_state(h);
+    if (rc) return rc;
+    const StepParams p = make_params(h);
+    const RecTable r = make_rec(h);
+    mark(h, -1);
+    launch_source(p0, p, h->stream);
+    mark(h, PACT_K_SOURCE);
+    launch_sample(p, r, traces, h->stream);
+    mark(h, PACT_K_SAMPLE);
+    for (int m = 1; m <= nsteps; ++m) {
+        launch_fwd_velocity(p, h->stream);
+        mark(h, PACT_K_FWD_VELOCITY);
+        launch_fwd_stress(p, h->stream);
+        mark(h, PACT_K_FWD_STRESS);
+        launch_sample(p, r, traces + (size_t)m * h->L, h->stream);
+        mark(h, PACT_K_SAMPLE);
+    }
+    CK(h, cudaGetLastError());
+    return PACT_OK;
+}
+
+static int run_adjoint(pact_handle h, const float* traces, float* image, int nsteps) {
+    int rc = zero_state(h);
+    if (rc) return rc;
+    const StepParams p = make_params(h);
+    const RecTable r = make_rec(h);
+    mark(h, -1);
+    launch_inject(p, r, traces + (size_t)nsteps * h->L, h->stream);
+    mark(h, PACT_K_INJECT);
+    for (int m = nsteps; m >= 1; --m) {
+        launch_adj_a(p, h->stream);
+        mark(h, PACT_K_ADJ_A);
+        launch_adj_b(p, h->stream);
+        mark(h, PACT_K_ADJ_B);
+        launch_inject(p, r, traces + (size_t)(m - 1) * h->L, h->stream);
+        mark(h, PACT_K_INJECT);
+    }
+    launch_readout(image, p, h->stream);
+    mark(h, PACT_K_READOUT);
+    CK(h, cudaGetLastError());
+    return PACT_OK;
+}
+
+static int ensure_stage(pact_handle h, float** buf, size_t* cap, size_t n) {
+    if (*cap >= n) return PACT_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    CK(h, cudaMalloc(buf, n * sizeof(float)));
+    *cap = n;
+    return PACT_OK;
+}
+
+extern "C" {
+
+int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out) {
+    std::string why;
+    if (!out) return fail(nullptr, PACT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_desc(desc, why);
+    if (rc) return fail(nullptr, rc, why);
+    pact_grid* h = new (std::nothrow) pact_grid();
+    if (!h) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
+    h->d = *desc;
+    h->stream = (cudaStream_t)stream;
+    h->N = (size_t)desc->nx * desc->ny * desc->nz;
+    h->nmax = std::max(desc->nx, std::max(desc->ny, desc->nz));
+    auto bail = [&](int code) {
+        g_err = h->err;
+        pact_destroy(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        h->err = "cudaGetDevice failed";
+        return bail(PACT_ECUDA);
+    }
+    cudaError_t e = cudaMalloc(&h->fields, 9 * h->N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->medium, 4 * h->N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->tables, 18 * (size_t)h->nmax * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->scratch_u32, 4 * sizeof(unsigned int));
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        h->slab_n[a] = slab_points(*desc, a);
+        if (h->slab_n[a]) e = cudaMalloc(&h->slabs[a], 6 * h->slab_n[a] * sizeof(float));
+    }
+    if (e != cudaSuccess) {
+        h->err = std::string("allocation: ") + cudaGetErrorString(e);
+        return bail(e == cudaErrorMemoryAllocation ? PACT_ENOMEM : PACT_ECUDA);
+    }
+    *out = h;
+    return PACT_OK;
+}
+
+int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const float* mu, const float* alpha) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (!rho || !lambda || !mu || !alpha) return fail(h, PACT_EINVAL, "NULL medium pointer");
+    CK(h, cudaSetDevice(h->device));
+    const size_t N = h->N;
+    cudaStream_t s = h->stream;
+    CK(h, cudaMemcpyAsync(h->medium, rho, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(h->medium + N, lambda, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(h->medium + 2 * N, mu, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(h->medium + 3 * N, alpha, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemsetAsync(h->scratch_u32, 0, 4 * sizeof(unsigned int), s));
+    launch_medium_check(h->medium, h->medium + N, h->medium + 2 * N, h->medium + 3 * N, N, h->scratch_u32, s);
+    CK(h, cudaGetLastError());
+    unsigned int red[4];
+    CK(h, cudaMemcpyAsync(red, h->scratch_u32, sizeof red, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    h->medium_set = false;
+    if (red[2] != 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "medium: %u nodes violate rho > 0, mu >= 0, lambda + 2 mu > 0, alpha >= 0",
+                 red[2]);
+        return fail(h, PACT_EINVAL, buf);
+    }
+    float c2, amax;
+    std::memcpy(&c2, &red[0], 4);
+    std::memcpy(&amax, &red[1], 4);
+    const double cmax = std::sqrt((double)c2);
+    const double courant = cmax * h->d.dt / h->d.dx;
+    const double limit = 6.0 / (7.0 * std::sqrt(3.0));
+    if (!(courant < limit)) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "CFL: c_max dt / dx = %.4f >= 6/(7 sqrt 3) = %.4f (c_max = %.1f m/s)", courant,
+                 limit, cmax);
+        return fail(h, PACT_ECFL, buf);
+    }
+    if (!((double)amax * h->d.dt < 1.0)) return fail(h, PACT_ECFL, "absorption: alpha_max dt >= 1");
+    h->cmax = cmax;
+    // C-PML profile tables, double precision on the host, stored as float
+    const pact_grid_desc& d = h->d;
+    const double vmax = d.pml_vmax > 0 ? d.pml_vmax : cmax;
+    std::vector<float> tab(18 * (size_t)h->nmax, 0.0f);
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a)
+        for (int l = 0; l < 2; ++l)
+            for (int k = 0; k < dims[a]; ++k) {
+                double ca, cb, cc;
+                pml_coef(dims[a], d.npml, d.dx, d.dt, vmax, d.pml_R0, d.pml_f0, k + 0.5 * l, ca, cb, cc);
+                tab[((a * 2 + l) * 3 + 0) * (size_t)h->nmax + k] = (float)ca;
+                tab[((a * 2 + l) * 3 + 1) * (size_t)h->nmax + k] = (float)cb;
+                tab[((a * 2 + l) * 3 + 2) * (size_t)h->nmax + k] = (float)cc;
+            }
+    CK(h, cudaMemcpyAsync(h->tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(h, cudaStreamSynchronize(s));
+    h->medium_set = true;
+    return PACT_OK;
+}
+
+int pact_forward(pact_handle h, const float* p0, const float* rec_xyz, int L, int nsteps, float* traces) {
+    int rc = precheck(h, p0, traces, nsteps);
+    if (rc) return rc;
+    rc = set_receivers(h, rec_xyz, L);
+    if (rc) return rc;
+    return run_forward(h, p0, traces, nsteps);
+}
+
+int pact_adjoint(pact_handle h, const float* traces, const float* rec_xyz, int L, int nsteps, float* image) {
+    int rc = precheck(h, traces, image, nsteps);
+    if (rc) return rc;
+    rc = set_receivers(h, rec_xyz, L);
+    if (rc) return rc;
+    return run_adjoint(h, traces, image, nsteps);
+}
+
+int pact_forward_host(pact_handle h, const float* p0, const float* rec_xyz, int L, int nsteps, float* traces) {
+    int rc = precheck(h, p0, traces, nsteps);
+    if (rc) return rc;
+    rc = set_receivers(h, rec_xyz, L);
+    if (rc) return rc;
+    const size_t nt = (size_t)(nsteps + 1) * L;
+    if ((rc = ensure_stage(h, &h->stage_a, &h->stage_a_n, h->N))) return rc;
+    if ((rc = ensure_stage(h, &h->stage_b, &h->stage_b_n, nt))) return rc;
+    CK(h, cudaMemcpyAsync(h->stage_a, p0, h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = run_forward(h, h->stage_a, h->stage_b, nsteps))) return rc;
+    CK(h, cudaMemcpyAsync(traces, h->stage_b, nt * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PACT_OK;
+}
+
+int pact_adjoint_host(pact_handle h, const float* traces, const float* rec_xyz, int L, int nsteps, float* image) {
+    int rc = precheck(h, traces, image, nsteps);
+    if (rc) return rc;
+    rc = set_receivers(h, rec_xyz, L);
+    if (rc) return rc;
+    const size_t nt = (size_t)(nsteps + 1) * L;
+    if ((rc = ensure_stage(h, &h->stage_a, &h->stage_a_n, h->N))) return rc;
+    if ((rc = ensure_stage(h, &h->stage_b, &h->stage_b_n, nt))) return rc;
+    CK(h, cudaMemcpyAsync(h->stage_b, traces, nt * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = run_adjoint(h, h->stage_b, h->stage_a, nsteps))) return rc;
+    CK(h, cudaMemcpyAsync(image, h->stage_a, h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PACT_OK;
+}
+
+int pact_destroy(pact_handle h) {
+    if (!h) return PACT_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->fields);
+    cudaFree(h->medium);
+    cudaFree(h->tables);
+    cudaFree(h->scratch_u32);
+    for (int a = 0; a < 3; ++a) cudaFree(h->slabs[a]);
+    free_rec(h);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    cudaFree(h->stage_a);
+    cudaFree(h->stage_b);
+    delete h;
+    return PACT_OK;
+}
+
+const char* pact_last_error(pact_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int pact_query_bytes(const pact_grid_desc* desc, int L, int nsteps, size_t* bytes) {
+    std::string why;
+    if (!bytes) return fail(nullptr, PACT_EINVAL, "bytes is NULL");
+    int rc = check_desc(desc, why);
+    if (rc) return fail(nullptr, rc, why);
+    *bytes = desc_bytes(*desc, L, nsteps);
+    return PACT_OK;
+}
+
+int pact_get_wavefield(pact_handle h, float* host_out) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (!host_out) return fail(h, PACT_EINVAL, "host_out is NULL");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaMemcpyAsync(host_out, h->fields, 9 * h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PACT_OK;
+}
+
+int pact_profile(pact_handle h, int enable) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < PACT_NKIND; ++k) h->launches[k] = 0;
+    h->ev_kind.clear();
+    h->prof = enable != 0;
+    return PACT_OK;
+}
+
+int pact_profile_read(pact_handle h, int kind, long long* launches, double* total_ms) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (kind < 0 || kind >= PACT_NKIND || !launches || !total_ms) return fail(h, PACT_EINVAL, "bad kind or NULL");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *launches = h->launches[kind];
+    double ms = 0.0;
+    for (size_t i = 1; i < h->ev_kind.size(); ++i) {
+        if (h->ev_kind[i] != kind) continue;
+        float t = 0.0f;
+        CK(h, cudaEventElapsedTime(&t, h->ev_pool[i - 1], h->ev_pool[i]));
+        ms += t;
+    }
+    *total_ms = ms;
+    return PACT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libpact.so (include/pact.h).
+
+Argument marshalling only: every step of H and H^T runs in the library's CUDA
+kernels.  PyTorch supplies device memory (``tensor.data_ptr()``) and streams.
+There is no CPU fallback: if the library is missing or fails to load, every
+call raises.
+
+Function names follow the C ABI (``pact_create_grid`` ... ``pact_destroy``);
+``Grid`` wraps one handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .synth import GridDesc
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "libpact.so")
+
+PACT_OK, PACT_EINVAL, PACT_ECFL, PACT_ENOMEM, PACT_ECUDA, PACT_ETIMEOUT, PACT_ESTATE = range(7)
+_NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ESTATE"}
+
+# every symbol include/pact.h declares
+EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
+           "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
+           "pact_profile", "pact_profile_read"]
+
+# kernel roles of pact_profile_read (include/pact.h PACT_K_*)
+KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout"]
+
+
+class PactError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pact {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pact_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("npml", ctypes.c_int),
+                ("pml_R0", ctypes.c_double), ("pml_f0", ctypes.c_double), ("pml_vmax", ctypes.c_double)]
+
+    @classmethod
+    def from_desc(cls, d: GridDesc):
+        return cls(int(d.nx), int(d.ny), int(d.nz), float(d.dx), float(d.dt), int(d.npml), float(d.pml_R0),
+                   float(d.pml_f0), float(d.pml_vmax))
+
+
+_lib = None
+
+
+def load(path: str = SO_PATH):
+    """Load libpact.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpact.so not built at {path}: run `python -m paper_1709_02733_b300.build`")
+    try:  # share the CUDA runtime torch already loaded
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    lib = ctypes.CDLL(path)
+    vp, i, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    D = ctypes.POINTER(pact_grid_desc)
+    lib.pact_create_grid.argtypes = [D, vp, ctypes.POINTER(vp)]
+    lib.pact_set_medium.argtypes = [vp, fp, fp, fp, fp]
+    for name in ("pact_forward", "pact_adjoint", "pact_forward_host", "pact_adjoint_host"):
+        getattr(lib, name).argtypes = [vp, fp, fp, i, i, fp]
+    lib.pact_destroy.argtypes = [vp]
+    lib.pact_last_error.argtypes = [vp]
+    lib.pact_last_error.restype = ctypes.c_char_p
+    lib.pact_query_bytes.argtypes = [D, i, i, ctypes.POINTER(ctypes.c_size_t)]
+    lib.pact_get_wavefield.argtypes = [vp, fp]
+    lib.pact_profile.argtypes = [vp, i]
+    lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+    for name in EXPORTS:
+        if name != "pact_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc, handle=None):
+    if rc != PACT_OK:
+        msg = load().pact_last_error(handle).decode(errors="replace")
+        raise PactError(rc, msg)
+
+
+def pact_query_bytes(desc: GridDesc, L: int = 0, nsteps: int = -1) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().pact_query_bytes(ctypes.byref(pact_grid_desc.from_desc(desc)), int(L), int(nsteps),
+                                   ctypes.byref(out)))
+    return int(out.value)
+
+
+def _dev_ptr(t, numel=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _rec_host(rec):
+    r = np.ascontiguousarray(np.asarray(rec.cpu() if hasattr(rec, "cpu") else rec, dtype=np.float32).reshape(-1, 3))
+    return r, r.shape[0]
+
+
+class Grid:
+    """One pact handle: grid, medium, wavefield and receiver tables on one GPU.
+
+    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream at
+    creation time); every call is ordered on it.
+    """
+
+    def __init__(self, desc: GridDesc, stream=None):
+        import torch
+        self.lib = load()
+        self.desc = desc
+        self.shape = desc.shape
+        self.N = desc.N
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        _check(self.lib.pact_create_grid(ctypes.byref(pact_grid_desc.from_desc(desc)),
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.pact_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls -------------------------------------------------------------
+    def pact_set_medium(self, rho, lam, mu, alpha):
+        _check(self.lib.pact_set_medium(self._h, *[_dev_ptr(a, self.N) for a in (rho, lam, mu, alpha)]), self._h)
+
+    set_medium = pact_set_medium
+
+    def pact_forward(self, p0, rec, nsteps: int, out=None):
+        """traces = H p0, a (nsteps+1, L) float32 CUDA tensor."""
+        import torch
+        r, L = _rec_host(rec)
+        if out is None:
+            out = torch.empty((nsteps + 1, L), device=p0.device, dtype=torch.float32)
+        _check(self.lib.pact_forward(self._h, _dev_ptr(p0, self.N), r.ctypes.data_as(ctypes.c_void_p), L,
+                                     int(nsteps), _dev_ptr(out, (nsteps + 1) * L)), self._h)
+        return out
+
+    forward = pact_forward
+
+    def pact_adjoint(self, traces, rec, out=None):
+        """image = H^T traces, a (nz, ny, nx) float32 CUDA tensor."""
+        import torch
+        r, L = _rec_host(rec)
+        nsteps = traces.shape[0] - 1
+        if out is None:
+            out = torch.empty(self.shape, device=traces.device, dtype=torch.float32)
+        _check(self.lib.pact_adjoint(self._h, _dev_ptr(traces, (nsteps + 1) * L), r.ctypes.data_as(ctypes.c_void_p),
+                                     L, int(nsteps), _dev_ptr(out, self.N)), self._h)
+        return out
+
+    adjoint = pact_adjoint
+
+    def pact_forward_host(self, p0: np.ndarray, rec, nsteps: int, out: Optional[np.ndarray] = None):
+        r, L = _rec_host(rec)
+        p0 = np.ascontiguousarray(p0, dtype=np.float32)
+        assert p0.size == self.N
+        if out is None:
+            out = np.empty((nsteps + 1, L), np.float32)
+        _check(self.lib.pact_forward_host(self._h, p0.ctypes.data_as(ctypes.c_void_p),
+                                          r.ctypes.data_as(ctypes.c_void_p), L, int(nsteps),
+                                          out.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return out
+
+    forward_host = pact_forward_host
+
+    def pact_adjoint_host(self, traces: np.ndarray, rec, out: Optional[np.ndarray] = None):
+        r, L = _rec_host(rec)
+        tr = np.ascontiguousarray(traces, dtype=np.float32)
+        nsteps = tr.shape[0] - 1
+        if out is None:
+            out = np.empty(self.shape, np.float32)
+        _check(self.lib.pact_adjoint_host(self._h, tr.ctypes.data_as(ctypes.c_void_p),
+                                          r.ctypes.data_as(ctypes.c_void_p), L, int(nsteps),
+                                          out.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return out
+
+    adjoint_host = pact_adjoint_host
+
+    def pact_get_wavefield(self) -> np.ndarray:
+        out = np.empty((9,) + self.shape, np.float32)
+        _check(self.lib.pact_get_wavefield(self._h, out.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return out
+
+    get_wavefield = pact_get_wavefield
+
+    def pact_profile(self, enable: bool = True):
+        _check(self.lib.pact_profile(self._h, int(bool(enable))), self._h)
+
+    profile = pact_profile
+
+    def pact_profile_read(self):
+        """{kind: (launches, device_ms)} since the last pact_profile call."""
+        out = {}
+        for k, name in enumerate(KINDS):
+            n, ms = ctypes.c_longlong(0), ctypes.c_double(0.0)
+            _check(self.lib.pact_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)), self._h)
+            out[name] = (int(n.value), float(ms.value))
+        return out
+
+    profile_read = pact_profile_read

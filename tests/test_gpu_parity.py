@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (written in each test): relative L2 error <= 1e-4 on receiver traces and
+adjoint images; inner-product test <= 1e-5 in FP32.  Sizes are small enough
+for the oracle to finish in seconds yet span several thread blocks and ragged
+tails (odd, non-cubic grids); full-size checks use properties that hold at any
+size or samples the oracle can compute one by one on a crop of the grid.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle  # noqa: E402
+from paper_1709_02733_b300 import synth  # noqa: E402
+from paper_1709_02733_b300 import pact  # noqa: E402
+from paper_1709_02733_b300.synth import GridDesc  # noqa: E402
+
+TOL = 1e-4
+DOT_TOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def make_grid(desc, medium):
+    g = pact.Grid(desc)
+    g.set_medium(*[cuda(m) for m in medium])
+    return g
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1709_02733_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _random_case(shape, npml, seed, L=9, absorb=True):
+    rho, lam, mu, al, vmax = synth.random_medium(shape, seed, absorb=absorb)
+    nz, ny, nx = shape
+    dx = 1e-3
+    d = GridDesc(nx, ny, nz, dx, 0.3 * dx / vmax, npml=npml, pml_vmax=vmax)
+    rng = np.random.default_rng(seed + 1)
+    p0 = rng.standard_normal(shape).astype(np.float32)
+    rec = synth.random_receivers(L, shape, seed + 2)
+    return d, (rho, lam, mu, al), p0, rec
+
+
+@pytest.mark.parametrize("shape,npml,nsteps", [((29, 41, 37), 4, 60), ((20, 18, 35), 0, 40), ((16, 16, 16), 3, 30)])
+def test_forward_adjoint_random_medium(shape, npml, nsteps):
+    """Random heterogeneous medium (fluid and solid nodes, absorption), odd grid."""
+    d, med, p0, rec = _random_case(shape, npml, 100 + npml)
+    o = Oracle(d.as_dict(), *med)
+    g = make_grid(d, med)
+    tr = g.forward(cuda(p0), rec, nsteps).cpu().numpy()
+    ref = o.forward(p0, rec, nsteps)
+    assert rel_l2(tr, ref) <= TOL
+    y = np.random.default_rng(5).standard_normal(ref.shape).astype(np.float32)
+    img = g.adjoint(cuda(y), rec).cpu().numpy()
+    ref_img = o.adjoint(y, rec)
+    assert rel_l2(img, ref_img) <= TOL
+
+
+def test_skull_like_48():
+    """Skull-like 48^3 workload (shell, tissue, tubes, hemisphere receivers, 6-cell C-PML)."""
+    w = synth.skull(48, 0.8e-3, 6, 150, 64, seed=9)
+    o = Oracle(w.desc.as_dict(), *w.medium)
+    g = make_grid(w.desc, w.medium)
+    tr = g.forward(cuda(w.p0), w.rec, w.nsteps).cpu().numpy()
+    ref = o.forward(w.p0, w.rec, w.nsteps)
+    assert rel_l2(tr, ref) <= TOL
+    img = g.adjoint(cuda(ref.astype(np.float32)), w.rec).cpu().numpy()
+    assert rel_l2(img, o.adjoint(ref.astype(np.float32), w.rec)) <= TOL
+
+
+def test_plain_fluid_64_full():
+    """The plain 64^3 workload in full: 400 steps, 128 receivers, 3-cell C-PML."""
+    w = synth.plain_fluid_64(npml=3, nsteps=400)
+    o = Oracle(w.desc.as_dict(), *w.medium)
+    g = make_grid(w.desc, w.medium)
+    tr = g.forward(cuda(w.p0), w.rec, w.nsteps).cpu().numpy()
+    ref = o.forward(w.p0, w.rec, w.nsteps)
+    assert rel_l2(tr, ref) <= TOL
+    rng = np.random.default_rng(1)
+    y = (ref + 0.1 * np.sqrt(np.mean(ref ** 2)) * rng.standard_normal(ref.shape)).astype(np.float32)
+    img = g.adjoint(cuda(y), w.rec).cpu().numpy()
+    assert rel_l2(img, o.adjoint(y, w.rec)) <= TOL
+
+
+def _dot_test(g, p0, rec, nsteps, seed=1):
+    tr = g.forward(cuda(p0), rec, nsteps).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(seed)
+    y = tr + 0.1 * np.sqrt(np.mean(tr ** 2)) * rng.standard_normal(tr.shape)
+    img = g.adjoint(cuda(y), rec).cpu().numpy().astype(np.float64)
+    lhs = float(np.sum(tr * y.astype(np.float32).astype(np.float64)))
+    rhs = float(np.sum(p0.astype(np.float64) * img))
+    return abs(lhs - rhs) / abs(lhs)
+
+
+def test_inner_product_fp32_skull():
+    w = synth.skull(96, 0.4e-3, 10, 300, 128, seed=3)
+    g = make_grid(w.desc, w.medium)
+    assert _dot_test(g, w.p0, w.rec, w.nsteps) <= DOT_TOL
+
+
+def test_first_sample_and_zero_steps():
+    """nsteps = 0: traces are p_hat_0 = trilinear interpolation of p0; receivers
+    on the grid edges (0 and n-2) are accepted."""
+    from scipy.ndimage import map_coordinates
+    d, med, p0, rec = _random_case((13, 12, 11), 2, 7, L=6)
+    rec[0] = [0, 0, 0]
+    rec[1] = [d.nx - 2, d.ny - 2, d.nz - 2]
+    g = make_grid(d, med)
+    tr = g.forward(cuda(p0), rec, 0).cpu().numpy()
+    assert tr.shape == (1, 6)
+    ref = map_coordinates(p0.astype(np.float64), [rec[:, 2], rec[:, 1], rec[:, 0]], order=1)
+    np.testing.assert_allclose(tr[0], ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+def test_single_receiver_and_determinism():
+    d, med, p0, rec = _random_case((24, 23, 22), 3, 11, L=1)
+    g = make_grid(d, med)
+    a = g.forward(cuda(p0), rec, 25).cpu().numpy()
+    b = g.forward(cuda(p0), rec, 25).cpu().numpy()
+    assert np.array_equal(a, b)
+    y = cuda(np.random.default_rng(2).standard_normal(a.shape))
+    i1 = g.adjoint(y, rec).cpu().numpy()
+    i2 = g.adjoint(y, rec).cpu().numpy()
+    assert np.array_equal(i1, i2)
+    o = Oracle(d.as_dict(), *med)
+    assert rel_l2(a, o.forward(p0, rec, 25)) <= TOL
+
+
+def test_host_pointer_calls_match_device_calls():
+    d, med, p0, rec = _random_case((20, 21, 22), 3, 13)
+    g = make_grid(d, med)
+    a = g.forward(cuda(p0), rec, 15).cpu().numpy()
+    b = g.forward_host(p0, rec, 15)
+    assert np.array_equal(a, b)
+    i1 = g.adjoint(cuda(a), rec).cpu().numpy()
+    i2 = g.adjoint_host(a, rec)
+    assert np.array_equal(i1, i2)
+
+
+def test_error_paths():
+    d, med, p0, rec = _random_case((16, 16, 16), 2, 17)
+    g = pact.Grid(d)
+    with pytest.raises(pact.PactError) as e:
+        g.forward(cuda(p0), rec, 3)
+    assert e.value.code == pact.PACT_ESTATE
+    g.set_medium(*[cuda(m) for m in med])
+    bad = rec.copy()
+    bad[0, 0] = d.nx - 1.5  # beyond n-2
+    with pytest.raises(pact.PactError) as e:
+        g.forward(cuda(p0), bad, 3)
+    assert e.value.code == pact.PACT_EINVAL
+    rho = med[0].copy()
+    rho[3, 3, 3] = 0.0
+    with pytest.raises(pact.PactError) as e:
+        g.set_medium(cuda(rho), *[cuda(m) for m in med[1:]])
+    assert e.value.code == pact.PACT_EINVAL
+    fast = GridDesc(d.nx, d.ny, d.nz, d.dx, d.dt * 2.0, npml=2, pml_vmax=d.pml_vmax)  # CFL 0.6
+    g2 = pact.Grid(fast)
+    with pytest.raises(pact.PactError) as e:
+        g2.set_medium(*[cuda(m) for m in med])
+    assert e.value.code == pact.PACT_ECFL
+
+
+def _crop_check(w, g, nsteps, centers):
+    """Oracle on a crop around each sample point: after k steps a point depends on
+    the data within 4k cells, so a crop of half-width 4k+2 with no C-PML (the
+    samples are deep in the interior) reproduces the full-grid values there."""
+    fields = g.get_wavefield()  # u1 u2 u3 s11 s22 s33 s23 s13 s12
+    hw = 4 * nsteps + 2
+    errs = []
+    for (x, y, z) in centers:
+        sl = (slice(z - hw, z + hw + 1), slice(y - hw, y + hw + 1), slice(x - hw, x + hw + 1))
+        n = 2 * hw + 1
+        dd = dict(nx=n, ny=n, nz=n, dx=w.desc.dx, dt=w.desc.dt, npml=0, pml_vmax=w.desc.pml_vmax)
+        o = Oracle(dd, *[np.ascontiguousarray(m[sl]) for m in w.medium])
+        st = o.run_state(np.ascontiguousarray(w.p0[sl]), nsteps)
+        v = Oracle.views(st)
+        ref = np.concatenate([v["u"][:, hw, hw, hw], v["sigma"][:, hw, hw, hw]])
+        got = fields[:, z, y, x].astype(np.float64)
+        errs.append(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30))
+    return max(errs)
+
+
+def test_full_size_512_sampled():
+    """The 512^3 skull workload in the launch configuration the bench times:
+    (a) p_hat_0 equals the trilinear interpolation of p0 at every receiver;
+    (b) the wavefield after 2 steps matches the oracle at sampled interior
+        points (oracle on a crop);
+    (c) inner-product test over 12 steps at full size."""
+    from scipy.ndimage import map_coordinates
+    w = synth.skull_512()
+    g = make_grid(w.desc, w.medium)
+    tr0 = g.forward(cuda(w.p0), w.rec, 0).cpu().numpy()
+    ref0 = map_coordinates(w.p0.astype(np.float64), [w.rec[:, 2], w.rec[:, 1], w.rec[:, 0]], order=1)
+    assert np.abs(tr0[0] - ref0).max() <= 1e-5 * max(np.abs(ref0).max(), 1e-6) + 1e-7
+    g.forward(cuda(w.p0), w.rec, 2)
+    idx = np.argwhere(w.p0 > 0.3 * w.p0.max())
+    rng = np.random.default_rng(0)
+    pick = idx[rng.choice(len(idx), 6, replace=False)]
+    centers = [(int(c[2]), int(c[1]), int(c[0])) for c in pick]
+    # plus points in the skull shell (solid, absorbing)
+    shell = np.argwhere(w.mu[::7, ::7, ::7] > 0) * 7
+    for c in shell[rng.choice(len(shell), 4, replace=False)]:
+        centers.append((int(c[2]), int(c[1]), int(c[0])))
+    assert _crop_check(w, g, 2, centers) <= 1e-4
+    assert _dot_test(g, w.p0, w.rec, 12) <= DOT_TOL
