@@ -72,7 +72,7 @@ def test_forward_adjoint_random_medium(shape, npml, nsteps):
 
 def test_skull_like_48():
     """Skull-like 48^3 workload (shell, tissue, tubes, hemisphere receivers, 6-cell C-PML)."""
-    w = synth.skull(48, 0.8e-3, 6, 150, 64, seed=9)
+    w = synth.skull(48, 1.2e-3, 6, 150, 64, seed=9)
     o = Oracle(w.desc.as_dict(), *w.medium)
     g = make_grid(w.desc, w.medium)
     tr = g.forward(cuda(w.p0), w.rec, w.nsteps).cpu().numpy()

@@ -268,7 +268,7 @@ def test_dense_transpose_of_each_substep(k):
 def test_inner_product_test_48():
     """<H p0, y> = <p0, H^T y> to 1e-12 with y = H p0 + noise (Sec. 5), skull-like
     48^3 medium with a 6-cell C-PML."""
-    w = synth.skull(48, 0.8e-3, 6, 120, 64, seed=9)
+    w = synth.skull(48, 1.2e-3, 6, 120, 64, seed=9)
     o = Oracle(w.desc.as_dict(), *w.medium)
     tr = o.forward(w.p0, w.rec, w.nsteps)
     rng = np.random.default_rng(1)
