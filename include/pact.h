@@ -127,6 +127,35 @@ int pact_query_bytes(const pact_grid_desc* desc, int L, int nsteps, size_t* byte
  * (Sec. 2.2 vectors u_bar, sigma_bar).  Synchronises the stream. */
 int pact_get_wavefield(pact_handle h, float* host_out);
 
+/* Forward operator H that allocates no device memory.  The paper has no
+ * counterpart: this is a deployment variant of pact_forward for callers that
+ * cannot call cudaMalloc -- code inside a host application that owns all device
+ * memory through its own pool and forbids outside allocations (they would escape
+ * its accounting, or fail once the pool has reserved the device), and
+ * latency-critical loops where cudaMalloc / cudaFree would add implicit device
+ * synchronisation.
+ * All working memory (wavefield 9N floats, C-PML slabs, profile tables,
+ * receiver tables: about 36 bytes per grid point plus the slabs) comes from one
+ * fixed file-scope device array of PACT_NOALLOC_SCRATCH_BYTES (64 MiB), which
+ * every GPU that loads the library holds until the process exits; a grid too
+ * large for it is rejected with PACT_EINVAL and a message giving the bytes it
+ * would need (roughly up to 110^3 points with a thin layer).  Inputs and outputs
+ * are the caller's: desc as for pact_create_grid; rho, lambda, mu, alpha and p0
+ * device arrays of N floats (read only); rec_xyz a HOST array of L triples;
+ * traces a device array of (nsteps+1)*L floats, overwritten, with the same
+ * values pact_forward produces.  stream: cudaStream_t (NULL = legacy default).
+ * The medium is checked first (one 16-byte read back that waits for the
+ * stream); the steps are then queued asynchronously.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call
+ * reuses the same array and clears what must start at zero; calls that overlap
+ * on the GPU (two streams or two host threads) race and corrupt each other.
+ * Errors: PACT_EINVAL, PACT_ECFL, PACT_ECUDA; message via pact_last_error(NULL). */
+#define PACT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const float* lambda, const float* mu,
+                         const float* alpha, const float* p0, const float* rec_xyz, int L, int nsteps,
+                         float* traces, void* stream);
+
 /* Measurement support (not part of the method).  Kernel roles counted and
  * timed by pact_profile / pact_profile_read. */
 #define PACT_K_FWD_VELOCITY 0 /* velocity + phi update of one forward step        */

@@ -77,6 +77,9 @@ struct pact_grid {
     std::string err;
 };
 
+// message for pact_last_error(NULL) from calls that have no handle
+void pact_note_error(const std::string& msg) { g_err = msg; }
+
 static int fail(pact_handle h, int code, const std::string& msg) {
     if (h) h->err = msg;
     g_err = msg;
@@ -109,7 +112,7 @@ static void mark(pact_handle h, int kind) {
     h->ev_kind.push_back(kind);
 }
 
-static size_t slab_points(const pact_grid_desc& d, int axis) {
+size_t slab_points(const pact_grid_desc& d, int axis) {
     if (d.npml <= 0) return 0;
     const size_t W = 2 * (size_t)d.npml + 1;
     if (axis == 0) return (size_t)d.nz * d.ny * W;
@@ -117,7 +120,7 @@ static size_t slab_points(const pact_grid_desc& d, int axis) {
     return W * d.ny * d.nx;
 }
 
-static int check_desc(const pact_grid_desc* d, std::string& why) {
+int check_desc(const pact_grid_desc* d, std::string& why) {
     if (!d) { why = "desc is NULL"; return PACT_EINVAL; }
     if (d->npml < 0) { why = "npml < 0"; return PACT_EINVAL; }
     const int need = std::max(4, 2 * d->npml + 2);
@@ -152,7 +155,7 @@ static size_t desc_bytes(const pact_grid_desc& d, int L, int nsteps) {
 }
 
 // C-PML 1-D profile (Appendix A.1, kappa = 1) at grid coordinate pos on an axis of n nodes.
-static void pml_coef(int n, int P, double dx, double dt, double vmax, double R0, double f0, double pos,
+void pml_coef(int n, int P, double dx, double dt, double vmax, double R0, double f0, double pos,
                      double& a, double& b, double& chi) {
     a = 0.0;
     b = 1.0;

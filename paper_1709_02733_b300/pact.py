@@ -27,7 +27,7 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 # every symbol include/pact.h declares
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
-           "pact_profile", "pact_profile_read"]
+           "pact_profile", "pact_profile_read", "pact_forward_noalloc"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout"]
@@ -76,6 +76,7 @@ def load(path: str = SO_PATH):
     lib.pact_last_error.restype = ctypes.c_char_p
     lib.pact_query_bytes.argtypes = [D, i, i, ctypes.POINTER(ctypes.c_size_t)]
     lib.pact_get_wavefield.argtypes = [vp, fp]
+    lib.pact_forward_noalloc.argtypes = [D, fp, fp, fp, fp, fp, fp, i, i, fp, vp]
     lib.pact_profile.argtypes = [vp, i]
     lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTS:
@@ -96,6 +97,25 @@ def pact_query_bytes(desc: GridDesc, L: int = 0, nsteps: int = -1) -> int:
     _check(load().pact_query_bytes(ctypes.byref(pact_grid_desc.from_desc(desc)), int(L), int(nsteps),
                                    ctypes.byref(out)))
     return int(out.value)
+
+
+def pact_forward_noalloc(desc: GridDesc, medium, p0, rec, nsteps: int, out=None, stream=None):
+    """traces = H p0 through pact_forward_noalloc: no device memory is
+    allocated by the library (its working memory is a fixed 64 MiB array that
+    all calls share; calls must not overlap on the GPU).  ``out`` must be
+    supplied by callers that cannot allocate."""
+    import torch
+    lib = load()
+    r, L = _rec_host(rec)
+    N = desc.N
+    if out is None:
+        out = torch.empty((nsteps + 1, L), device=p0.device, dtype=torch.float32)
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(lib.pact_forward_noalloc(ctypes.byref(pact_grid_desc.from_desc(desc)),
+                                    *[_dev_ptr(m, N) for m in medium], _dev_ptr(p0, N),
+                                    r.ctypes.data_as(ctypes.c_void_p), L, int(nsteps),
+                                    _dev_ptr(out, (nsteps + 1) * L), ctypes.c_void_p(st)))
+    return out
 
 
 def _dev_ptr(t, numel=None):
