@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -16,6 +17,7 @@
 
 #include "pact.h"
 #include "pact_internal.cuh"
+#include "step_tiled.cuh"
 
 void launch_fwd_velocity(const StepParams& p, cudaStream_t st);
 void launch_fwd_stress(const StepParams& p, cudaStream_t st);
@@ -74,6 +76,9 @@ struct pact_grid {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int> ev_kind;  // kind of the launch that ends at event i (-1: origin)
+    // TMA-staged kernels (nx % 4 == 0) or the direct kernels
+    bool tiled = false;
+    TmaSet tm{};
     std::string err;
 };
 
@@ -326,6 +331,45 @@ static int precheck(pact_handle h, const void* a, const void* b, int nsteps) {
     return PACT_OK;
 }
 
+// a tiled kernel records a timed-out wait in scratch_u32[3]; read at sync points
+static int device_status(pact_handle h) {
+    unsigned int w = 0;
+    CK(h, cudaMemcpyAsync(&w, h->scratch_u32 + 3, sizeof w, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (w) return fail(h, PACT_ETIMEOUT, "a step kernel gave up waiting for its TMA loads");
+    return PACT_OK;
+}
+
+static void fwd_step(pact_handle h, const StepParams& p) {
+    int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
+    if (h->tiled) {
+        launch_vel_tiled(false, p, h->tm, err, h->stream);
+        mark(h, PACT_K_FWD_VELOCITY);
+        launch_str_tiled(false, p, h->tm, err, h->stream);
+        mark(h, PACT_K_FWD_STRESS);
+    } else {
+        launch_fwd_velocity(p, h->stream);
+        mark(h, PACT_K_FWD_VELOCITY);
+        launch_fwd_stress(p, h->stream);
+        mark(h, PACT_K_FWD_STRESS);
+    }
+}
+
+static void adj_step(pact_handle h, const StepParams& p) {
+    int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
+    if (h->tiled) {
+        launch_vel_tiled(true, p, h->tm, err, h->stream);
+        mark(h, PACT_K_ADJ_A);
+        launch_str_tiled(true, p, h->tm, err, h->stream);
+        mark(h, PACT_K_ADJ_B);
+    } else {
+        launch_adj_a(p, h->stream);
+        mark(h, PACT_K_ADJ_A);
+        launch_adj_b(p, h->stream);
+        mark(h, PACT_K_ADJ_B);
+    }
+}
+
 static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps) {
     int rc = zero_state(h);
     if (rc) return rc;
@@ -337,10 +381,7 @@ static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps
     launch_sample(p, r, traces, h->stream);
     mark(h, PACT_K_SAMPLE);
     for (int m = 1; m <= nsteps; ++m) {
-        launch_fwd_velocity(p, h->stream);
-        mark(h, PACT_K_FWD_VELOCITY);
-        launch_fwd_stress(p, h->stream);
-        mark(h, PACT_K_FWD_STRESS);
+        fwd_step(h, p);
         launch_sample(p, r, traces + (size_t)m * h->L, h->stream);
         mark(h, PACT_K_SAMPLE);
     }
@@ -357,10 +398,7 @@ static int run_adjoint(pact_handle h, const float* traces, float* image, int nst
     launch_inject(p, r, traces + (size_t)nsteps * h->L, h->stream);
     mark(h, PACT_K_INJECT);
     for (int m = nsteps; m >= 1; --m) {
-        launch_adj_a(p, h->stream);
-        mark(h, PACT_K_ADJ_A);
-        launch_adj_b(p, h->stream);
-        mark(h, PACT_K_ADJ_B);
+        adj_step(h, p);
         launch_inject(p, r, traces + (size_t)(m - 1) * h->L, h->stream);
         mark(h, PACT_K_INJECT);
     }
@@ -415,6 +453,22 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
     if (e != cudaSuccess) {
         h->err = std::string("allocation: ") + cudaGetErrorString(e);
         return bail(e == cudaErrorMemoryAllocation ? PACT_ENOMEM : PACT_ECUDA);
+    }
+    if (cudaMemset(h->scratch_u32, 0, 4 * sizeof(unsigned int)) != cudaSuccess) {
+        h->err = "cudaMemset of the status words failed";
+        return bail(PACT_ECUDA);
+    }
+    // TMA-staged kernels need 16-byte row strides (nx % 4 == 0); PACT_KERNELS=direct
+    // in the environment selects the one-thread-per-point kernels instead.
+    const char* kenv = getenv("PACT_KERNELS");
+    if (desc->nx % 4 == 0 && !(kenv && std::strcmp(kenv, "direct") == 0)) {
+        float* arrays[TM_N];
+        for (int i = 0; i < 9; ++i) arrays[i] = h->fields + i * h->N;
+        arrays[TM_RHO] = h->medium;
+        arrays[TM_LAM] = h->medium + h->N;
+        arrays[TM_MU] = h->medium + 2 * h->N;
+        arrays[TM_ALPHA] = h->medium + 3 * h->N;
+        h->tiled = make_tma_set(&h->tm, arrays, desc->nx, desc->ny, desc->nz) == 0;
     }
     *out = h;
     return PACT_OK;
@@ -504,8 +558,7 @@ int pact_forward_host(pact_handle h, const float* p0, const float* rec_xyz, int 
     CK(h, cudaMemcpyAsync(h->stage_a, p0, h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     if ((rc = run_forward(h, h->stage_a, h->stage_b, nsteps))) return rc;
     CK(h, cudaMemcpyAsync(traces, h->stage_b, nt * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    return PACT_OK;
+    return device_status(h);
 }
 
 int pact_adjoint_host(pact_handle h, const float* traces, const float* rec_xyz, int L, int nsteps, float* image) {
@@ -519,8 +572,7 @@ int pact_adjoint_host(pact_handle h, const float* traces, const float* rec_xyz, 
     CK(h, cudaMemcpyAsync(h->stage_b, traces, nt * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     if ((rc = run_adjoint(h, h->stage_b, h->stage_a, nsteps))) return rc;
     CK(h, cudaMemcpyAsync(image, h->stage_a, h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    return PACT_OK;
+    return device_status(h);
 }
 
 int pact_destroy(pact_handle h) {
@@ -556,8 +608,7 @@ int pact_get_wavefield(pact_handle h, float* host_out) {
     if (!host_out) return fail(h, PACT_EINVAL, "host_out is NULL");
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaMemcpyAsync(host_out, h->fields, 9 * h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    return PACT_OK;
+    return device_status(h);
 }
 
 int pact_profile(pact_handle h, int enable) {
@@ -584,7 +635,7 @@ int pact_profile_read(pact_handle h, int kind, long long* launches, double* tota
         ms += t;
     }
     *total_ms = ms;
-    return PACT_OK;
+    return device_status(h);
 }
 
 }  // extern "C"
