@@ -21,6 +21,12 @@
 // (see step_direct.cu), computed once per point into shared memory.  The
 // deferred J and B tails of the adjoint are as in step_direct.cu.
 //
+// Every half-step is two launches over disjoint regions of (tile, plane)
+// work: blocks whose tile halo and planes stay off the C-PML slabs run an
+// instantiation without any C-PML code; the rest run the C-PML instantiation,
+// which keeps the per-thread x / y layer coefficients in registers and loads
+// the own-point memory variables one plane ahead with the wavefield values.
+//
 // Requirements: nx % 4 == 0 (TMA global strides are multiples of 16 bytes).
 #include <algorithm>
 #include <mutex>
@@ -40,8 +46,8 @@ constexpr int BOXS = 544;       // box stride in floats (2176 B, 128-B aligned)
 constexpr int OX = 4, OY = 2;   // own point offset inside the box
 constexpr int D = 4;            // stage ring depth (planes)
 
-template <bool ADJ> struct VelCfg {
-    // stage boxes: 0..5 sigma (Voigt), 6 rho, 7 alpha, [8 lambda, 9 mu]
+template <bool ADJ, bool PML> struct VelCfg {
+    // stage boxes: 0..5 sigma (Voigt), 6 rho, 7 alpha, [adjoint: 8 lambda, 9 mu]
     static constexpr int NB = ADJ ? 10 : 8;
     static constexpr int NDER = ADJ ? 6 : 0;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
@@ -50,15 +56,42 @@ template <bool ADJ> struct VelCfg {
     }
 };
 
-template <bool ADJ> struct StrCfg {
-    // stage boxes: 0..2 u; forward: 3 lambda, 4 mu; adjoint: 3 rho
-    static constexpr int NB = ADJ ? 4 : 5;
+template <bool ADJ, bool PML> struct StrCfg {
+    // stage boxes: 0..2 u, then forward: 3 lambda, 4 mu;
+    // adjoint: 3 rho [C-PML variant: 4 lambda, 5 mu, for the psi tails]
+    static constexpr int NB = ADJ ? (PML ? 6 : 4) : 5;
     static constexpr int NDER = ADJ ? 6 : 0;
+    static constexpr int BLAM = ADJ ? 4 : 3, BMU = ADJ ? 5 : 4;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) {
-        return b < 3 ? TM_U0 + b : (ADJ ? TM_RHO : (b == 3 ? TM_LAM : TM_MU));
+        return b < 3 ? TM_U0 + b : (ADJ ? (b == 3 ? TM_RHO : (b == 4 ? TM_LAM : TM_MU)) : (b == 3 ? TM_LAM : TM_MU));
     }
 };
+
+// A rectangular block of work: tiles [tx0,tx1) x [ty0,ty1), planes [za,zb)
+// in chunks of zc planes; bstart = first block index of the region.
+struct Region {
+    int tx0, tx1, ty0, ty1, za, zb, zc, bstart;
+};
+constexpr int kMaxRegions = 7;
+struct RegionList {
+    int n;
+    Region r[kMaxRegions];
+};
+
+__device__ __forceinline__ void locate(const RegionList& rl, int& tile_x, int& tile_y, int& zc0, int& zc1) {
+    const int b = blockIdx.x;
+    int r = 0;
+    while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
+    const Region& R = rl.r[r];
+    const int lb = b - R.bstart;
+    const int ntx = R.tx1 - R.tx0, nt = ntx * (R.ty1 - R.ty0);
+    const int t = lb % nt, ch = lb / nt;
+    tile_x = R.tx0 + t % ntx;
+    tile_y = R.ty0 + t / ntx;
+    zc0 = R.za + ch * R.zc;
+    zc1 = min(zc0 + R.zc, R.zb);
+}
 
 // differences on a box (own index o) and on a register queue
 __device__ __forceinline__ float dpx(const float* v, int o) {
@@ -131,16 +164,67 @@ __device__ __forceinline__ void drain(uint64_t* bar, int pfrom, int pto, int pfi
 
 using namespace tiled;
 
+// per-thread C-PML constants of the own column along x and y
+struct PmlXY {
+    int lx, ly;          // slab coordinate along x / y, -1 outside the layer
+    float c[2][2][3];    // [axis x, y][lattice integer, half][a, b, chi]
+};
+
+__device__ __forceinline__ void pml_xy_init(PmlXY& q, const StepParams& p, int x, int y, bool own) {
+    q.lx = own ? slab_local(x, p.nx, p.P) : -1;
+    q.ly = own ? slab_local(y, p.ny, p.P) : -1;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+            q.c[0][hh][w] = q.lx >= 0 ? tabv(p, 0, hh, w, x) : 0.f;
+            q.c[1][hh][w] = q.ly >= 0 ? tabv(p, 1, hh, w, y) : 0.f;
+        }
+}
+
+// C-PML coefficients of plane z along the z axis
+struct PmlZ {
+    int lz;
+    float c[2][3];
+};
+
+__device__ __forceinline__ void pml_z_init(PmlZ& q, const StepParams& p, int z) {
+    q.lz = (z >= 0 && z < p.nz) ? slab_local(z, p.nz, p.P) : -1;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int w = 0; w < 3; ++w) q.c[hh][w] = q.lz >= 0 ? tabv(p, 2, hh, w, z) : 0.f;
+}
+
+// slab index of the own point (x, y, z) on the slab of `axis`
+__device__ __forceinline__ unsigned own_slab(int axis, const PmlXY& q, int lz, int x, int y, int z,
+                                             const StepParams& p) {
+    const unsigned W = 2 * p.P + 1;
+    if (axis == 0) return ((unsigned)z * p.ny + y) * W + q.lx;
+    if (axis == 1) return ((unsigned)z * W + q.ly) * p.nx + x;
+    return ((unsigned)lz * p.ny + y) * p.nx + x;
+}
+
+__device__ __forceinline__ bool in_axis(int j, const PmlXY& q, int lz) {
+    return j == 0 ? q.lx >= 0 : (j == 1 ? q.ly >= 0 : lz >= 0);
+}
+
+__device__ __forceinline__ float coef(int j, int hh, int w, const PmlXY& q, const PmlZ& qz) {
+    return j < 2 ? q.c[j][hh][w] : qz.c[hh][w];
+}
+
 // ===========================================================================
 // velocity family
 // ===========================================================================
-template <bool ADJ>
-__global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_constant__ TmaSet tm, int zc, int* err) {
-    using Cfg = VelCfg<ADJ>;
+template <bool ADJ, bool PML>
+__global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
+                                                  int* err) {
+    using Cfg = VelCfg<ADJ, PML>;
     extern __shared__ __align__(128) float sm[];
+    int tile_x, tile_y, zc0, zc1;
+    locate(rl, tile_x, tile_y, zc0, zc1);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, p.nz);
+    const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < p.nx && y < p.ny;
     const int pfirst = zc0 - 2, plast = zc1 + 1;
@@ -150,7 +234,9 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
     const int o = (ty + OY) * BW + tx + OX;
     const float dt = p.dt, h = p.inv_dx;
     const int P = p.P;
-    const bool tpml = P > 0 && (x0 - 2 < P || x0 + TX + 2 >= p.nx - P - 1 || y0 - 2 < P || y0 + TY + 2 >= p.ny - P - 1);
+    const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
+    PmlXY px{};
+    if constexpr (PML) pml_xy_init(px, p, x, y, own);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
@@ -162,78 +248,122 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
         const int k = pl - pfirst;
         float* dst = ring.stage(pl);
         mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
-        for (int b = 0; b < Cfg::NB; ++b) tma_load_3d(dst + b * BOXS, &tm.m[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+        for (int b = 0; b < Cfg::NB; ++b)
+            tma_load_3d(dst + b * BOXS, &tm.m[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
 
     float q33[4] = {0, 0, 0, 0}, q13[4] = {0, 0, 0, 0}, q23[4] = {0, 0, 0, 0};
-    const int xc1 = (x + 1 < p.nx) ? 1 : 0;        // clamped +x neighbour offset
-    const int yc1 = (y + 1 < p.ny) ? BW : 0;       // clamped +y neighbour offset
+    const int xc1 = (x + 1 < p.nx) ? 1 : 0;   // clamped +x neighbour offset
+    const int yc1 = (y + 1 < p.ny) ? BW : 0;  // clamped +y neighbour offset
+
+    // own-point values of the next output plane, loaded one visit ahead
+    float nu[3] = {0.f, 0.f, 0.f};
+    float nph[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    auto prefetch = [&](int zn) {
+        if (!own || zn < zc0 || zn >= zc1) return;
+        const unsigned g = (unsigned)zn * nxy + gxy;
+        nu[0] = p.u[0][g];
+        nu[1] = p.u[1][g];
+        nu[2] = p.u[2][g];
+        if constexpr (PML) {
+            const int lz = slab_local(zn, p.nz, P);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (in_axis(j, px, lz)) {
+                    const unsigned si = own_slab(j, px, lz, x, y, zn, p);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) nph[i][j] = p.phi[i][j][si];
+                }
+        }
+    };
+    // adjoint C-PML queue-head memory variables (psi^zz at plane pl, psi^xz and
+    // psi^yz at plane pl-1), loaded one visit ahead
+    float nhp[3] = {0.f, 0.f, 0.f};
+    auto prefetch_heads = [&](int pn) {
+        if constexpr (ADJ && PML) {
+            if (!own) return;
+            if (pn >= 0 && pn < p.nz) {
+                const int l = slab_local(pn, p.nz, P);
+                if (l >= 0) nhp[0] = p.psi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
+            }
+            const int pm = pn - 1;
+            if (pm >= 0 && pm < p.nz) {
+                const int l = slab_local(pm, p.nz, P);
+                if (l >= 0) {
+                    const unsigned si = ((unsigned)l * p.ny + y) * p.nx + x;
+                    nhp[1] = p.psi[0][2][si];
+                    nhp[2] = p.psi[1][2][si];
+                }
+            }
+        }
+    };
+    prefetch_heads(pfirst);
 
     for (int pl = pfirst; pl <= plast; ++pl) {
         const int z = pl - 2;
         const bool out = z >= zc0;
-        // own-point values of the output plane, loaded before the wait
-        const unsigned g = own ? (unsigned)(((size_t)max(z, 0) * p.ny + y) * p.nx + x) : 0u;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-        if (out && own) {
-            u0 = p.u[0][g];
-            u1 = p.u[1][g];
-            u2 = p.u[2][g];
-        }
+        float cu[3] = {nu[0], nu[1], nu[2]};
+        float cph[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) cph[i][j] = nph[i][j];
+        const float chp[3] = {nhp[0], nhp[1], nhp[2]};
+        prefetch(z + 1);
+        prefetch_heads(pl + 1);
         const int kk = pl - pfirst;
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1);
-            drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
-            return;
-        }
         const float* sp = ring.stage(pl);
         const float* spm = (pl - 1 >= pfirst) ? ring.stage(pl - 1) : nullptr;
         // ---- queue heads: integer->half field at plane pl, half->integer at pl-1
-        if constexpr (!ADJ) {
-            push(q33, sp[2 * BOXS + o]);
-            push(q13, spm ? spm[4 * BOXS + o] : 0.f);
-            push(q23, spm ? spm[3 * BOXS + o] : 0.f);
-        } else {
-            float h33 = 0.f, h13 = 0.f, h23 = 0.f;
-            if (pl >= 0 && pl < p.nz) {
-                const float s11 = sp[o], s22 = sp[BOXS + o], s33 = sp[2 * BOXS + o];
-                const float lam = sp[8 * BOXS + o], mu2 = 2.0f * sp[9 * BOXS + o];
-                const float ltr = lam * (s11 + s22 + s33);
-                h33 = dt * (ltr + mu2 * s33);
-                if (own && in_slab_plane(pl, p.nz, P)) {
-                    const long si = slab_at(p, 2, x, y, pl);
-                    const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
-                    h33 += a * (p.psi[2][2][si] + dt * (ltr + mu2 * chi * s33));
+        if (ok) {
+            if constexpr (!ADJ) {
+                push(q33, sp[2 * BOXS + o]);
+                push(q13, spm ? spm[4 * BOXS + o] : 0.f);
+                push(q23, spm ? spm[3 * BOXS + o] : 0.f);
+            } else {
+                float h33 = 0.f, h13 = 0.f, h23 = 0.f;
+                if (pl >= 0 && pl < p.nz) {
+                    const float s11 = sp[o], s22 = sp[BOXS + o], s33 = sp[2 * BOXS + o];
+                    const float lam = sp[8 * BOXS + o], mu2 = 2.0f * sp[9 * BOXS + o];
+                    const float ltr = lam * (s11 + s22 + s33);
+                    h33 = dt * (ltr + mu2 * s33);
+                    if constexpr (PML) {
+                        const int l = slab_local(pl, p.nz, P);
+                        if (own && l >= 0) {
+                            const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
+                            h33 += a * (chp[0] + dt * (ltr + mu2 * chi * s33));
+                        }
+                    }
                 }
-            }
-            const int zm = pl - 1;
-            if (spm && zm >= 0 && zm < p.nz) {
-                const float* mz = spm + 9 * BOXS;                       // mu at plane pl-1
-                const float* mz1 = (pl < p.nz) ? sp + 9 * BOXS : mz;     // mu at plane pl (clamped)
-                const float m13 = harm4f(mz[o], mz[o + xc1], mz1[o], mz1[o + xc1]);
-                const float m23 = harm4f(mz[o], mz[o + yc1], mz1[o], mz1[o + yc1]);
-                const float s13 = spm[4 * BOXS + o], s23 = spm[3 * BOXS + o];
-                h13 = dt * m13 * s13;
-                h23 = dt * m23 * s23;
-                if (own && in_slab_plane(zm, p.nz, P)) {
-                    const long si = slab_at(p, 2, x, y, zm);
-                    const float a = tabv(p, 2, 1, 0, zm), chi = tabv(p, 2, 1, 2, zm);
-                    h13 += a * (p.psi[0][2][si] + chi * h13);
-                    h23 += a * (p.psi[1][2][si] + chi * h23);
+                const int zm = pl - 1;
+                if (spm && zm >= 0 && zm < p.nz) {
+                    const float* mz = spm + 9 * BOXS;                    // mu at plane pl-1
+                    const float* mz1 = (pl < p.nz) ? sp + 9 * BOXS : mz;  // mu at plane pl (clamped)
+                    const float m13 = harm4f(mz[o], mz[o + xc1], mz1[o], mz1[o + xc1]);
+                    const float m23 = harm4f(mz[o], mz[o + yc1], mz1[o], mz1[o + yc1]);
+                    h13 = dt * m13 * spm[4 * BOXS + o];
+                    h23 = dt * m23 * spm[3 * BOXS + o];
+                    if constexpr (PML) {
+                        const int l = slab_local(zm, p.nz, P);
+                        if (own && l >= 0) {
+                            const float a = tabv(p, 2, 1, 0, zm), chi = tabv(p, 2, 1, 2, zm);
+                            h13 += a * (chp[1] + chi * h13);
+                            h23 += a * (chp[2] + chi * h23);
+                        }
+                    }
                 }
+                push(q33, h33);
+                push(q13, h13);
+                push(q23, h23);
             }
-            push(q33, h33);
-            push(q13, h13);
-            push(q23, h23);
         }
 
         if (out) {
             const float* sz = ring.stage(z);
             const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
-            const bool pml = tpml || in_slab_plane(z, p.nz, P);
             const float *XD0, *XD1, *XD2, *YD0, *YD1, *YD2;
             if constexpr (!ADJ) {
                 XD0 = sz;             // s11
@@ -252,14 +382,12 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
                 float* Szy = der + 5 * BOXS;
                 const float* m0 = sz + 9 * BOXS;
                 const float* m1 = sz1 + 9 * BOXS;
-                auto derive = [&](auto PMLT) {
-                    constexpr bool PM = decltype(PMLT)::value;
+                if (ok) {
                     // x-differenced: columns OX-2..OX+TX+1, rows OY..OY+TY-1
                     for (int i = tid; i < (TX + 4) * TY; i += NT) {
                         const int bx = OX - 2 + i % (TX + 4), by = OY + i / (TX + 4);
                         const int q = by * BW + bx;
                         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        const bool in = gx >= 0 && gx < p.nx && gy < p.ny;
                         const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
                         const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
                         const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
@@ -270,7 +398,8 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
                         const float m13 = harm4f(m0[q], m0[qx1], m1[q], m1[qx1]);
                         float v12 = dt * m12 * sz[5 * BOXS + q];
                         float v13 = dt * m13 * sz[4 * BOXS + q];
-                        if constexpr (PM) {
+                        if constexpr (PML) {
+                            const bool in = gx >= 0 && gx < p.nx && gy < p.ny;
                             if (in && slab_local(gx, p.nx, P) >= 0) {
                                 const long si = slab_at(p, 0, gx, gy, z);
                                 const float ai = tabv(p, 0, 0, 0, gx), ci = tabv(p, 0, 0, 2, gx);
@@ -289,7 +418,6 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
                         const int bx = OX + i % TX, by = OY - 2 + i / TX;
                         const int q = by * BW + bx;
                         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        const bool in = gx < p.nx && gy >= 0 && gy < p.ny;
                         const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
                         const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
                         const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
@@ -300,7 +428,8 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
                         const float m23 = harm4f(m0[q], m0[qy1], m1[q], m1[qy1]);
                         float v12 = dt * m12 * sz[5 * BOXS + q];
                         float v23 = dt * m23 * sz[3 * BOXS + q];
-                        if constexpr (PM) {
+                        if constexpr (PML) {
+                            const bool in = gx < p.nx && gy >= 0 && gy < p.ny;
                             if (in && slab_local(gy, p.ny, P) >= 0) {
                                 const long si = slab_at(p, 1, gx, gy, z);
                                 const float ai = tabv(p, 1, 0, 0, gy), ci = tabv(p, 1, 0, 2, gy);
@@ -314,9 +443,7 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
                         Sxy[q] = v12;
                         Szy[q] = v23;
                     }
-                };
-                if (tpml) derive(std::true_type{});
-                else derive(std::false_type{});
+                }
                 __syncthreads();
                 XD0 = Qx;
                 XD1 = Syx;
@@ -325,65 +452,57 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
                 YD1 = Sxy;
                 YD2 = Szy;
             }
-            if (own) {
-                // divergence terms of the three components
-                float gx0 = dpx(XD0, o), gy0 = dmy(YD1, o), gz0 = dq(q13);   // u^x
-                float gx1 = dmx(XD1, o), gy1 = dpy(YD0, o), gz1 = dq(q23);   // u^y
-                float gx2 = dmx(XD2, o), gy2 = dmy(YD2, o), gz2 = dq(q33);   // u^z
+            if (ok && own) {
+                const float g[3][3] = {{dpx(XD0, o) * h, dmy(YD1, o) * h, dq(q13) * h},   // u^x
+                                       {dmx(XD1, o) * h, dpy(YD0, o) * h, dq(q23) * h},   // u^y
+                                       {dmx(XD2, o) * h, dmy(YD2, o) * h, dq(q33) * h}};  // u^z
                 const float* r0 = sz + 6 * BOXS;
                 const float* a0 = sz + 7 * BOXS;
                 const float rb[3] = {0.5f * (r0[o] + r0[o + xc1]), 0.5f * (r0[o] + r0[o + yc1]),
                                      0.5f * (r0[o] + sz1[6 * BOXS + o])};
                 const float ab[3] = {0.5f * (a0[o] + a0[o + xc1]), 0.5f * (a0[o] + a0[o + yc1]),
                                      0.5f * (a0[o] + sz1[7 * BOXS + o])};
-                float uo[3] = {u0, u1, u2};
-                float gsum[3][3] = {{gx0 * h, gy0 * h, gz0 * h}, {gx1 * h, gy1 * h, gz1 * h}, {gx2 * h, gy2 * h, gz2 * h}};
-                const int co[3] = {x, y, z};
-                const int nn[3] = {p.nx, p.ny, p.nz};
-                float res[3];
+                PmlZ pz{};
+                if constexpr (PML) pml_z_init(pz, p, z);
+                const unsigned gi = (unsigned)z * nxy + gxy;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
+                    float res;
                     if constexpr (!ADJ) {
-                        float acc = gsum[i][0] + gsum[i][1] + gsum[i][2];
-                        if (pml) {
+                        float acc = g[i][0] + g[i][1] + g[i][2];
+                        if constexpr (PML) {
 #pragma unroll
-                            for (int j = 0; j < 3; ++j) {
-                                const int l = slab_local(co[j], nn[j], P);
-                                if (l >= 0) {
+                            for (int j = 0; j < 3; ++j)
+                                if (in_axis(j, px, pz.lz)) {
                                     const int hh = (i == j);
-                                    const float a = tabv(p, j, hh, 0, co[j]), b = tabv(p, j, hh, 1, co[j]);
-                                    const float c = tabv(p, j, hh, 2, co[j]);
-                                    float* ph = p.phi[i][j] + slab_index(j, x, y, z, l, p);
-                                    const float v = b * (*ph) + a * gsum[i][j];
-                                    *ph = v;
-                                    acc += c * v;
+                                    const float v = coef(j, hh, 1, px, pz) * cph[i][j] + coef(j, hh, 0, px, pz) * g[i][j];
+                                    p.phi[i][j][own_slab(j, px, pz.lz, x, y, z, p)] = v;
+                                    acc += coef(j, hh, 2, px, pz) * v;
                                 }
-                            }
                         }
-                        res[i] = (1.0f - dt * ab[i]) * uo[i] + __fdividef(dt, rb[i]) * acc;
+                        res = (1.0f - dt * ab[i]) * cu[i] + __fdividef(dt, rb[i]) * acc;
                     } else {
-                        const float w = __fdividef(dt, rb[i]) * uo[i];
-                        if (pml) {
+                        if constexpr (PML) {
+                            const float w = __fdividef(dt, rb[i]) * cu[i];
 #pragma unroll
-                            for (int j = 0; j < 3; ++j) {
-                                const int l = slab_local(co[j], nn[j], P);
-                                if (l >= 0) {
+                            for (int j = 0; j < 3; ++j)
+                                if (in_axis(j, px, pz.lz)) {
                                     const int hh = (i == j);
-                                    const float b = tabv(p, j, hh, 1, co[j]), c = tabv(p, j, hh, 2, co[j]);
-                                    float* ph = p.phi[i][j] + slab_index(j, x, y, z, l, p);
-                                    *ph = b * (*ph + c * w);
+                                    p.phi[i][j][own_slab(j, px, pz.lz, x, y, z, p)] =
+                                        coef(j, hh, 1, px, pz) * (cph[i][j] + coef(j, hh, 2, px, pz) * w);
                                 }
-                            }
                         }
-                        res[i] = (1.0f - dt * ab[i]) * uo[i] - (gsum[i][0] + gsum[i][1] + gsum[i][2]);
+                        res = (1.0f - dt * ab[i]) * cu[i] - (g[i][0] + g[i][1] + g[i][2]);
                     }
+                    p.u[i][gi] = res;
                 }
-                p.u[0][g] = res[0];
-                p.u[1][g] = res[1];
-                p.u[2][g] = res[2];
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
+            return;
+        }
         if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
     }
 }
@@ -391,13 +510,15 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
 // ===========================================================================
 // stress family
 // ===========================================================================
-template <bool ADJ>
-__global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, int zc, int* err) {
-    using Cfg = StrCfg<ADJ>;
+template <bool ADJ, bool PML>
+__global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
+                                                  int* err) {
+    using Cfg = StrCfg<ADJ, PML>;
     extern __shared__ __align__(128) float sm[];
+    int tile_x, tile_y, zc0, zc1;
+    locate(rl, tile_x, tile_y, zc0, zc1);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, p.nz);
+    const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < p.nx && y < p.ny;
     const int pfirst = zc0 - 2, plast = zc1 + 1;
@@ -407,7 +528,9 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
     const int o = (ty + OY) * BW + tx + OX;
     const float dt = p.dt, h = p.inv_dx;
     const int P = p.P;
-    const bool tpml = P > 0 && (x0 - 2 < P || x0 + TX + 2 >= p.nx - P - 1 || y0 - 2 < P || y0 + TY + 2 >= p.ny - P - 1);
+    const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
+    PmlXY px{};
+    if constexpr (PML) pml_xy_init(px, p, x, y, own);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
@@ -419,7 +542,8 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
         const int k = pl - pfirst;
         float* dst = ring.stage(pl);
         mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
-        for (int b = 0; b < Cfg::NB; ++b) tma_load_3d(dst + b * BOXS, &tm.m[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+        for (int b = 0; b < Cfg::NB; ++b)
+            tma_load_3d(dst + b * BOXS, &tm.m[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
@@ -427,64 +551,110 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
     float qx[4] = {0, 0, 0, 0}, qy[4] = {0, 0, 0, 0}, qz[4] = {0, 0, 0, 0};
     const int xc1 = (x + 1 < p.nx) ? 1 : 0;
     const int yc1 = (y + 1 < p.ny) ? BW : 0;
+    const int oxy = o + xc1 + yc1;
+
+    // own stresses and psi of the next output plane, loaded one visit ahead
+    float ns[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float nps[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    auto prefetch = [&](int zn) {
+        if (!own || zn < zc0 || zn >= zc1) return;
+        const unsigned g = (unsigned)zn * nxy + gxy;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) ns[v] = p.s[v][g];
+        if constexpr (PML) {
+            const int lz = slab_local(zn, p.nz, P);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (in_axis(j, px, lz)) {
+                    const unsigned si = own_slab(j, px, lz, x, y, zn, p);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) nps[i][j] = p.psi[i][j][si];
+                }
+        }
+    };
+    // adjoint C-PML queue-head memory variables (phi^xz, phi^yz at plane pl,
+    // phi^zz at plane pl-1), loaded one visit ahead
+    float nhp[3] = {0.f, 0.f, 0.f};
+    auto prefetch_heads = [&](int pn) {
+        if constexpr (ADJ && PML) {
+            if (!own) return;
+            if (pn >= 0 && pn < p.nz) {
+                const int l = slab_local(pn, p.nz, P);
+                if (l >= 0) {
+                    const unsigned si = ((unsigned)l * p.ny + y) * p.nx + x;
+                    nhp[0] = p.phi[0][2][si];
+                    nhp[1] = p.phi[1][2][si];
+                }
+            }
+            const int pm = pn - 1;
+            if (pm >= 0 && pm < p.nz) {
+                const int l = slab_local(pm, p.nz, P);
+                if (l >= 0) nhp[2] = p.phi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
+            }
+        }
+    };
+    prefetch_heads(pfirst);
 
     for (int pl = pfirst; pl <= plast; ++pl) {
         const int z = pl - 2;
         const bool out = z >= zc0;
-        const unsigned g = own ? (unsigned)(((size_t)max(z, 0) * p.ny + y) * p.nx + x) : 0u;
-        float so[6] = {0, 0, 0, 0, 0, 0};
-        if (out && own) {
+        float so[6];
 #pragma unroll
-            for (int v = 0; v < 6; ++v) so[v] = p.s[v][g];
-        }
+        for (int v = 0; v < 6; ++v) so[v] = ns[v];
+        float cps[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) cps[i][j] = nps[i][j];
+        const float chp[3] = {nhp[0], nhp[1], nhp[2]};
+        prefetch(z + 1);
+        prefetch_heads(pl + 1);
         const int kk = pl - pfirst;
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1);
-            drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
-            return;
-        }
         const float* sp = ring.stage(pl);
         const float* spm = (pl - 1 >= pfirst) ? ring.stage(pl - 1) : nullptr;
         // ---- queue heads: d_z u^x, d_z u^y are integer->half (plane pl);
         //      d_z u^z is half->integer (plane pl-1)
-        if constexpr (!ADJ) {
-            push(qx, sp[o]);
-            push(qy, sp[BOXS + o]);
-            push(qz, spm ? spm[2 * BOXS + o] : 0.f);
-        } else {
-            float hx = 0.f, hy = 0.f, hz = 0.f;
-            if (pl >= 0 && pl < p.nz) {
-                const float* r = sp + 3 * BOXS;
-                hx = __fdividef(2.0f * dt, r[o] + r[o + xc1]) * sp[o];
-                hy = __fdividef(2.0f * dt, r[o] + r[o + yc1]) * sp[BOXS + o];
-                if (own && in_slab_plane(pl, p.nz, P)) {
-                    const long si = slab_at(p, 2, x, y, pl);
-                    const float a = tabv(p, 2, 0, 0, pl), c = tabv(p, 2, 0, 2, pl);
-                    hx += a * (p.phi[0][2][si] + c * hx);
-                    hy += a * (p.phi[1][2][si] + c * hy);
+        if (ok) {
+            if constexpr (!ADJ) {
+                push(qx, sp[o]);
+                push(qy, sp[BOXS + o]);
+                push(qz, spm ? spm[2 * BOXS + o] : 0.f);
+            } else {
+                float hx = 0.f, hy = 0.f, hz = 0.f;
+                if (pl >= 0 && pl < p.nz) {
+                    const float* r = sp + 3 * BOXS;
+                    hx = __fdividef(2.0f * dt, r[o] + r[o + xc1]) * sp[o];
+                    hy = __fdividef(2.0f * dt, r[o] + r[o + yc1]) * sp[BOXS + o];
+                    if constexpr (PML) {
+                        if (own && slab_local(pl, p.nz, P) >= 0) {
+                            const float a = tabv(p, 2, 0, 0, pl), c = tabv(p, 2, 0, 2, pl);
+                            hx += a * (chp[0] + c * hx);
+                            hy += a * (chp[1] + c * hy);
+                        }
+                    }
                 }
-            }
-            const int zm = pl - 1;
-            if (spm && zm >= 0 && zm < p.nz) {
-                const float* r = spm + 3 * BOXS;
-                const float* r1 = (pl < p.nz) ? sp + 3 * BOXS : r;
-                hz = __fdividef(2.0f * dt, r[o] + r1[o]) * spm[2 * BOXS + o];
-                if (own && in_slab_plane(zm, p.nz, P)) {
-                    const long si = slab_at(p, 2, x, y, zm);
-                    const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
-                    hz += a * (p.phi[2][2][si] + c * hz);
+                const int zm = pl - 1;
+                if (spm && zm >= 0 && zm < p.nz) {
+                    const float* r = spm + 3 * BOXS;
+                    const float* r1 = (pl < p.nz) ? sp + 3 * BOXS : r;
+                    hz = __fdividef(2.0f * dt, r[o] + r1[o]) * spm[2 * BOXS + o];
+                    if constexpr (PML) {
+                        if (own && slab_local(zm, p.nz, P) >= 0) {
+                            const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
+                            hz += a * (chp[2] + c * hz);
+                        }
+                    }
                 }
+                push(qx, hx);
+                push(qy, hy);
+                push(qz, hz);
             }
-            push(qx, hx);
-            push(qy, hy);
-            push(qz, hz);
         }
 
         if (out) {
             const float* sz = ring.stage(z);
             const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
-            const bool pml = tpml || in_slab_plane(z, p.nz, P);
             const float *XD0, *XD1, *XD2, *YD0, *YD1, *YD2;
             if constexpr (!ADJ) {
                 XD0 = sz;             // u^x  (D-x for s11)
@@ -502,8 +672,7 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
                 float* Rzy = der + 5 * BOXS;
                 const float* r0 = sz + 3 * BOXS;
                 const float* r1 = sz1 + 3 * BOXS;
-                auto derive = [&](auto PMLT) {
-                    constexpr bool PM = decltype(PMLT)::value;
+                if (ok) {
                     for (int i = tid; i < (TX + 4) * TY; i += NT) {
                         const int bx = OX - 2 + i % (TX + 4), by = OY + i / (TX + 4);
                         const int q = by * BW + bx;
@@ -515,7 +684,7 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
                             wx = __fdividef(2.0f * dt, r0[q] + r0[qx1]) * sz[q];
                             wy = __fdividef(2.0f * dt, r0[q] + r0[qy1]) * sz[BOXS + q];
                             wz = __fdividef(2.0f * dt, r0[q] + r1[q]) * sz[2 * BOXS + q];
-                            if constexpr (PM) {
+                            if constexpr (PML) {
                                 if (slab_local(gx, p.nx, P) >= 0) {
                                     const long si = slab_at(p, 0, gx, gy, z);
                                     const float ah = tabv(p, 0, 1, 0, gx), ch = tabv(p, 0, 1, 2, gx);
@@ -544,7 +713,7 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
                             wx = __fdividef(2.0f * dt, r0[q] + r0[qx1]) * sz[q];
                             wy = __fdividef(2.0f * dt, r0[q] + r0[qy1]) * sz[BOXS + q];
                             wz = __fdividef(2.0f * dt, r0[q] + r1[q]) * sz[2 * BOXS + q];
-                            if constexpr (PM) {
+                            if constexpr (PML) {
                                 if (slab_local(gy, p.ny, P) >= 0) {
                                     const long si = slab_at(p, 1, gx, gy, z);
                                     const float ah = tabv(p, 1, 1, 0, gy), ch = tabv(p, 1, 1, 2, gy);
@@ -562,9 +731,7 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
                         Rxy[q] = wx;
                         Rzy[q] = wz;
                     }
-                };
-                if (tpml) derive(std::true_type{});
-                else derive(std::false_type{});
+                }
                 __syncthreads();
                 XD0 = Rxx;
                 XD1 = Ryx;
@@ -573,175 +740,249 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
                 YD1 = Rxy;
                 YD2 = Rzy;
             }
-            if (own) {
-                const float exx = dmx(XD0, o) * h, eyy = dmy(YD0, o) * h, ezz = dq(qz) * h;
-                const float exy = dpy(YD1, o) * h;   // d_y of the u^x field
-                const float eyx = dpx(XD1, o) * h;   // d_x of the u^y field
-                const float exz = dq(qx) * h;        // d_z of the u^x field
-                const float ezx = dpx(XD2, o) * h;   // d_x of the u^z field
-                const float eyz = dq(qy) * h;        // d_z of the u^y field
-                const float ezy = dpy(YD2, o) * h;   // d_y of the u^z field
+            if (ok && own) {
+                // du[i][j] = d_j of the u^i-like field
+                const float du[3][3] = {{dmx(XD0, o) * h, dpy(YD1, o) * h, dq(qx) * h},
+                                        {dpx(XD1, o) * h, dmy(YD0, o) * h, dq(qy) * h},
+                                        {dpx(XD2, o) * h, dpy(YD2, o) * h, dq(qz) * h}};
+                const unsigned gi = (unsigned)z * nxy + gxy;
+                PmlZ pz{};
+                if constexpr (PML) pml_z_init(pz, p, z);
                 float res[6];
                 if constexpr (!ADJ) {
-                    const float* m0 = sz + 4 * BOXS;
-                    const float* m1 = sz1 + 4 * BOXS;
-                    const float lam = sz[3 * BOXS + o], mu2 = 2.0f * m0[o];
-                    const int oxy = (x + 1 < p.nx) ? ((y + 1 < p.ny) ? o + 1 + BW : o + 1) : (o + yc1);
+                    const float* m0 = sz + Cfg::BMU * BOXS;
+                    const float* m1 = sz1 + Cfg::BMU * BOXS;
+                    const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * m0[o];
                     const float m12 = harm4f(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
                     const float m13 = harm4f(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
                     const float m23 = harm4f(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);
-                    float e[3] = {exx, eyy, ezz};
-                    float ps[3] = {0.f, 0.f, 0.f}, cs[3] = {0.f, 0.f, 0.f};
-                    // shear memory terms: (xy, yx), (xz, zx), (yz, zy)
-                    float sh[6] = {exy, eyx, exz, ezx, eyz, ezy};
-                    float shp[6] = {0, 0, 0, 0, 0, 0};
-                    if (pml) {
-                        const int co[3] = {x, y, z};
-                        const int nn[3] = {p.nx, p.ny, p.nz};
+                    // memory variables psi^{ij} (lattice: integer if i == j, else half)
+                    float cp[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // chi * psi
+                    float pd[3] = {0.f, 0.f, 0.f};                                         // psi^{kk}
+                    if constexpr (PML) {
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const int l = slab_local(co[k], nn[k], P);
-                            if (l >= 0) {
-                                const float a = tabv(p, k, 0, 0, co[k]), b = tabv(p, k, 0, 1, co[k]);
-                                cs[k] = tabv(p, k, 0, 2, co[k]);
-                                float* ps_ = p.psi[k][k] + slab_index(k, x, y, z, l, p);
-                                const float v = b * (*ps_) + a * e[k];
-                                *ps_ = v;
-                                ps[k] = v;
-                            }
-                        }
-                        // psi^{ij} on the axis-j slab, half lattice along j
-                        const int pi_[6] = {0, 1, 0, 2, 1, 2};
-                        const int pj_[6] = {1, 0, 2, 0, 2, 1};
+                        for (int j = 0; j < 3; ++j)
+                            if (in_axis(j, px, pz.lz)) {
+                                const unsigned si = own_slab(j, px, pz.lz, x, y, z, p);
 #pragma unroll
-                        for (int t = 0; t < 6; ++t) {
-                            const int j = pj_[t];
-                            const int l = slab_local(co[j], nn[j], P);
-                            if (l >= 0) {
-                                const float a = tabv(p, j, 1, 0, co[j]), b = tabv(p, j, 1, 1, co[j]);
-                                const float c = tabv(p, j, 1, 2, co[j]);
-                                float* ps_ = p.psi[pi_[t]][j] + slab_index(j, x, y, z, l, p);
-                                const float v = b * (*ps_) + a * sh[t];
-                                *ps_ = v;
-                                shp[t] = c * v;
-                            }
-                        }
-                    }
-                    const float theta = exx + eyy + ezz + ps[0] + ps[1] + ps[2];
-                    const float lt = lam * theta;
-                    res[0] = so[0] + dt * (lt + mu2 * (exx + cs[0] * ps[0]));
-                    res[1] = so[1] + dt * (lt + mu2 * (eyy + cs[1] * ps[1]));
-                    res[2] = so[2] + dt * (lt + mu2 * (ezz + cs[2] * ps[2]));
-                    res[3] = so[3] + dt * m23 * (eyz + ezy + shp[4] + shp[5]);
-                    res[4] = so[4] + dt * m13 * (exz + ezx + shp[2] + shp[3]);
-                    res[5] = so[5] + dt * m12 * (exy + eyx + shp[0] + shp[1]);
-                } else {
-                    if (pml) {
-                        // psi <- B~ (psi + Delta^T sigma_old) at the own point
-                        const int co[3] = {x, y, z};
-                        const int nn[3] = {p.nx, p.ny, p.nz};
-                        const float lam = __ldg(p.lam + g), mu2 = 2.0f * __ldg(p.mu + g);
-                        const float ltr = lam * (so[0] + so[1] + so[2]);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const int l = slab_local(co[k], nn[k], P);
-                            if (l >= 0) {
-                                const float b = tabv(p, k, 0, 1, co[k]), c = tabv(p, k, 0, 2, co[k]);
-                                float* ps_ = p.psi[k][k] + slab_index(k, x, y, z, l, p);
-                                *ps_ = b * (*ps_ + dt * (ltr + mu2 * c * so[k]));
-                            }
-                        }
-                        const float msh[3] = {mu_shear<3>(x, y, z, p), mu_shear<4>(x, y, z, p), mu_shear<5>(x, y, z, p)};
-                        // Voigt 3: (y,z), 4: (x,z), 5: (x,y)
-                        const int vi[3] = {1, 0, 0}, vj[3] = {2, 2, 1};
-#pragma unroll
-                        for (int t = 0; t < 3; ++t) {
-                            const float dms = dt * msh[t] * so[3 + t];
-#pragma unroll
-                            for (int side = 0; side < 2; ++side) {
-                                const int i = side ? vj[t] : vi[t], j = side ? vi[t] : vj[t];
-                                const int l = slab_local(co[j], nn[j], P);
-                                if (l >= 0) {
-                                    const float b = tabv(p, j, 1, 1, co[j]), c = tabv(p, j, 1, 2, co[j]);
-                                    float* ps_ = p.psi[i][j] + slab_index(j, x, y, z, l, p);
-                                    *ps_ = b * (*ps_ + c * dms);
+                                for (int i = 0; i < 3; ++i) {
+                                    const int hh = (i != j);
+                                    const float v =
+                                        coef(j, hh, 1, px, pz) * cps[i][j] + coef(j, hh, 0, px, pz) * du[i][j];
+                                    p.psi[i][j][si] = v;
+                                    cp[i][j] = coef(j, hh, 2, px, pz) * v;
+                                    if (i == j) pd[j] = v;
                                 }
                             }
-                        }
                     }
-                    res[0] = so[0] - exx;
-                    res[1] = so[1] - eyy;
-                    res[2] = so[2] - ezz;
-                    res[3] = so[3] - (eyz + ezy);
-                    res[4] = so[4] - (exz + ezx);
-                    res[5] = so[5] - (exy + eyx);
+                    const float theta = du[0][0] + du[1][1] + du[2][2] + pd[0] + pd[1] + pd[2];
+                    const float lt = lam * theta;
+                    res[0] = so[0] + dt * (lt + mu2 * (du[0][0] + cp[0][0]));
+                    res[1] = so[1] + dt * (lt + mu2 * (du[1][1] + cp[1][1]));
+                    res[2] = so[2] + dt * (lt + mu2 * (du[2][2] + cp[2][2]));
+                    res[3] = so[3] + dt * m23 * (du[1][2] + du[2][1] + cp[1][2] + cp[2][1]);
+                    res[4] = so[4] + dt * m13 * (du[0][2] + du[2][0] + cp[0][2] + cp[2][0]);
+                    res[5] = so[5] + dt * m12 * (du[0][1] + du[1][0] + cp[0][1] + cp[1][0]);
+                } else {
+                    if constexpr (PML) {
+                        // psi <- B~ (psi + Delta^T sigma_old) at the own point
+                        const float* m0 = sz + Cfg::BMU * BOXS;
+                        const float* m1 = sz1 + Cfg::BMU * BOXS;
+                        const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * m0[o];
+                        const float ltr = lam * (so[0] + so[1] + so[2]);
+                        const float msh[3] = {harm4f(m0[o], m0[o + yc1], m1[o], m1[o + yc1]),   // 23
+                                              harm4f(m0[o], m0[o + xc1], m1[o], m1[o + xc1]),   // 13
+                                              harm4f(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy])};  // 12
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            if (in_axis(j, px, pz.lz)) {
+                                const unsigned si = own_slab(j, px, pz.lz, x, y, z, p);
+#pragma unroll
+                                for (int i = 0; i < 3; ++i) {
+                                    const int hh = (i != j);
+                                    const int v = voigt(i, j);
+                                    const float add = (i == j) ? dt * (ltr + mu2 * coef(j, 0, 2, px, pz) * so[j])
+                                                               : coef(j, 1, 2, px, pz) * dt * msh[v - 3] * so[v];
+                                    p.psi[i][j][si] = coef(j, hh, 1, px, pz) * (cps[i][j] + add);
+                                }
+                            }
+                    }
+                    res[0] = so[0] - du[0][0];
+                    res[1] = so[1] - du[1][1];
+                    res[2] = so[2] - du[2][2];
+                    res[3] = so[3] - (du[1][2] + du[2][1]);
+                    res[4] = so[4] - (du[0][2] + du[2][0]);
+                    res[5] = so[5] - (du[0][1] + du[1][0]);
                 }
 #pragma unroll
-                for (int v = 0; v < 6; ++v) p.s[v][g] = res[v];
+                for (int v = 0; v < 6; ++v) p.s[v][gi] = res[v];
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
+            return;
+        }
         if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
     }
 }
 
 // ---------------------------------------------------------------------------
-// host side
+// host side: work regions and launches
 // ---------------------------------------------------------------------------
-// z-chunk length: enough blocks for about two waves of resident blocks
-static int chunk_len(const StepParams& p, size_t smem, const void* fn) {
-    int dev = 0, sms = 148, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
-    const long tiles = (long)((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
-    const long want = 2L * sms * (per_sm > 0 ? per_sm : 1);
-    long chunks = (want + tiles - 1) / tiles;
-    chunks = std::max(1L, std::min(chunks, (long)std::max(1, p.nz / 16)));
-    return (int)((p.nz + chunks - 1) / chunks);
+namespace {
+
+// tiles whose halo region (x0-2 .. x0+TX+2, y0-2 .. y0+TY+2) stays off the
+// x and y layer slabs; returns false if there are none
+bool interior_tiles(const StepParams& p, int& txlo, int& txhi, int& tylo, int& tyhi) {
+    const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
+    const int P = p.P;
+    txlo = ntx;
+    txhi = -1;
+    for (int t = 0; t < ntx; ++t) {
+        const int a = t * TX;
+        if (a - 2 >= P && a + TX + 2 < p.nx - P - 1) {
+            txlo = std::min(txlo, t);
+            txhi = std::max(txhi, t);
+        }
+    }
+    tylo = nty;
+    tyhi = -1;
+    for (int t = 0; t < nty; ++t) {
+        const int a = t * TY;
+        if (a - 2 >= P && a + TY + 2 < p.ny - P - 1) {
+            tylo = std::min(tylo, t);
+            tyhi = std::max(tyhi, t);
+        }
+    }
+    return txlo <= txhi && tylo <= tyhi;
 }
 
-// per (device, kernel, grid) launch configuration, computed once
-struct LaunchCache {
-    int dev;
-    const void* fn;
-    int nx, ny, nz;
-    int zc;
+int add_region(RegionList& rl, int tx0, int tx1, int ty0, int ty1, int za, int zb, int zc, int& blocks) {
+    if (tx0 >= tx1 || ty0 >= ty1 || za >= zb) return 0;
+    zc = std::max(1, std::min(zc, zb - za));
+    Region& r = rl.r[rl.n++];
+    r = {tx0, tx1, ty0, ty1, za, zb, zc, blocks};
+    const int chunks = (zb - za + zc - 1) / zc;
+    blocks += (tx1 - tx0) * (ty1 - ty0) * chunks;
+    return 1;
+}
+
+// interior region (no C-PML code) and up to six C-PML regions
+void make_regions(const StepParams& p, int per_sm_int, int sms, RegionList& inner, int& inner_blocks,
+                  RegionList& outer, int& outer_blocks) {
+    inner.n = outer.n = 0;
+    inner_blocks = outer_blocks = 0;
+    const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
+    const int P = p.P;
+    const long want = 2L * sms * std::max(1, per_sm_int);  // about two waves
+    if (P == 0) {
+        const long tiles = (long)ntx * nty;
+        long chunks = std::max(1L, std::min((want + tiles - 1) / tiles, (long)std::max(1, p.nz / 16)));
+        add_region(inner, 0, ntx, 0, nty, 0, p.nz, (int)((p.nz + chunks - 1) / chunks), inner_blocks);
+        return;
+    }
+    const int za = P, zb = p.nz - P - 1;  // planes off the z slabs
+    int txlo, txhi, tylo, tyhi;
+    const bool has = za < zb && interior_tiles(p, txlo, txhi, tylo, tyhi);
+    // z slabs: every tile, one chunk each
+    add_region(outer, 0, ntx, 0, nty, 0, std::min(P, p.nz), P, outer_blocks);
+    add_region(outer, 0, ntx, 0, nty, std::max(zb, P), p.nz, p.nz, outer_blocks);
+    const int zcf = 64;
+    if (!has) {
+        add_region(outer, 0, ntx, 0, nty, za, zb, zcf, outer_blocks);
+        return;
+    }
+    add_region(outer, 0, txlo, 0, nty, za, zb, zcf, outer_blocks);
+    add_region(outer, txhi + 1, ntx, 0, nty, za, zb, zcf, outer_blocks);
+    add_region(outer, txlo, txhi + 1, 0, tylo, za, zb, zcf, outer_blocks);
+    add_region(outer, txlo, txhi + 1, tyhi + 1, nty, za, zb, zcf, outer_blocks);
+    const long tiles = (long)(txhi + 1 - txlo) * (tyhi + 1 - tylo);
+    long chunks = std::max(1L, std::min((want + tiles - 1) / tiles, (long)std::max(1, (zb - za) / 16)));
+    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, (int)((zb - za + chunks - 1) / chunks), inner_blocks);
+}
+
+struct LaunchPlan {
+    int dev, nx, ny, nz, P, family;
+    RegionList inner, outer;
+    int inner_blocks, outer_blocks;
 };
 
-template <class K>
-static void launch_tiled(K kernel, size_t smem, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
-    static LaunchCache cache[64];
-    static int ncache = 0;
+}  // namespace
+
+template <bool ADJ, bool PML>
+static const void* vel_fn() {
+    return (const void*)k_vel_tiled<ADJ, PML>;
+}
+template <bool ADJ, bool PML>
+static const void* str_fn() {
+    return (const void*)k_str_tiled<ADJ, PML>;
+}
+
+// family: 0 vel fwd, 1 vel adj, 2 str fwd, 3 str adj
+static LaunchPlan plan_for(int family, const StepParams& p) {
+    static LaunchPlan plans[32];
+    static int nplans = 0;
     static std::mutex mu;
     int dev = 0;
     cudaGetDevice(&dev);
-    int zc = 0;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        for (int i = 0; i < ncache; ++i)
-            if (cache[i].dev == dev && cache[i].fn == (const void*)kernel && cache[i].nx == p.nx &&
-                cache[i].ny == p.ny && cache[i].nz == p.nz)
-                zc = cache[i].zc;
-        if (!zc) {
-            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            zc = chunk_len(p, smem, (const void*)kernel);
-            cache[ncache % 64] = {dev, (const void*)kernel, p.nx, p.ny, p.nz, zc};
-            ncache = std::min(ncache + 1, 64);
-        }
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < nplans; ++i) {
+        const LaunchPlan& L = plans[i];
+        if (L.dev == dev && L.family == family && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz && L.P == p.P)
+            return L;
     }
-    dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + zc - 1) / zc);
-    kernel<<<grid, dim3(TX, TY, 1), smem, st>>>(p, tm, zc, err);
+    const void* fi = family == 0 ? vel_fn<false, false>() : family == 1 ? vel_fn<true, false>()
+                   : family == 2 ? str_fn<false, false>() : str_fn<true, false>();
+    const void* fo = family == 0 ? vel_fn<false, true>() : family == 1 ? vel_fn<true, true>()
+                   : family == 2 ? str_fn<false, true>() : str_fn<true, true>();
+    const size_t si = family == 0 ? VelCfg<false, false>::SMEM : family == 1 ? VelCfg<true, false>::SMEM
+                    : family == 2 ? StrCfg<false, false>::SMEM : StrCfg<true, false>::SMEM;
+    const size_t so = family == 0 ? VelCfg<false, true>::SMEM : family == 1 ? VelCfg<true, true>::SMEM
+                    : family == 2 ? StrCfg<false, true>::SMEM : StrCfg<true, true>::SMEM;
+    cudaFuncSetAttribute(fi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)si);
+    cudaFuncSetAttribute(fo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)so);
+    int sms = 148, per_sm = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fi, NT, si);
+    LaunchPlan& L = plans[nplans % 32];
+    L.dev = dev;
+    L.family = family;
+    L.nx = p.nx;
+    L.ny = p.ny;
+    L.nz = p.nz;
+    L.P = p.P;
+    make_regions(p, per_sm, sms, L.inner, L.inner_blocks, L.outer, L.outer_blocks);
+    nplans = std::min(nplans + 1, 32);
+    return L;
+}
+
+template <bool ADJ>
+static void launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
+    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p);
+    if (L.outer_blocks)
+        k_vel_tiled<ADJ, true><<<L.outer_blocks, dim3(TX, TY, 1), VelCfg<ADJ, true>::SMEM, st>>>(p, tm, L.outer, err);
+    if (L.inner_blocks)
+        k_vel_tiled<ADJ, false><<<L.inner_blocks, dim3(TX, TY, 1), VelCfg<ADJ, false>::SMEM, st>>>(p, tm, L.inner, err);
+}
+
+template <bool ADJ>
+static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
+    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p);
+    if (L.outer_blocks)
+        k_str_tiled<ADJ, true><<<L.outer_blocks, dim3(TX, TY, 1), StrCfg<ADJ, true>::SMEM, st>>>(p, tm, L.outer, err);
+    if (L.inner_blocks)
+        k_str_tiled<ADJ, false><<<L.inner_blocks, dim3(TX, TY, 1), StrCfg<ADJ, false>::SMEM, st>>>(p, tm, L.inner, err);
 }
 
 void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
-    if (adj) launch_tiled(k_vel_tiled<true>, VelCfg<true>::SMEM, p, tm, err, st);
-    else launch_tiled(k_vel_tiled<false>, VelCfg<false>::SMEM, p, tm, err, st);
+    if (adj) launch_vel_impl<true>(p, tm, err, st);
+    else launch_vel_impl<false>(p, tm, err, st);
 }
 
 void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
-    if (adj) launch_tiled(k_str_tiled<true>, StrCfg<true>::SMEM, p, tm, err, st);
-    else launch_tiled(k_str_tiled<false>, StrCfg<false>::SMEM, p, tm, err, st);
+    if (adj) launch_str_impl<true>(p, tm, err, st);
+    else launch_str_impl<false>(p, tm, err, st);
 }
 
 // Tensor maps: one 3-D float32 map per array, box 40 x 13 x 1, zero fill.
