@@ -127,6 +127,35 @@ int pact_query_bytes(const pact_grid_desc* desc, int L, int nsteps, size_t* byte
  * (Sec. 2.2 vectors u_bar, sigma_bar).  Synchronises the stream. */
 int pact_get_wavefield(pact_handle h, float* host_out);
 
+/* ---- serving: many solves advanced together ------------------------------
+ * A solve is prepared on its handle with pact_begin, then any set of prepared
+ * handles (forward and adjoint, any grid sizes) is advanced together by
+ * pact_advance: per time step, persistent multi-instance kernels walk a device
+ * table of the solves (the same step kernels as pact_forward / pact_adjoint, so
+ * a result is the same alone and in a mix).  Not part of the paper: this is how
+ * the operator pair is served to concurrent requests. */
+
+/* Prepare one solve on h (queued on the handle's stream).  is_adjoint = 0:
+ * forward, in = p0 (device, N floats), out = traces (device, (nsteps+1)*L),
+ * row 0 is written now; is_adjoint = 1: adjoint, in = traces (device,
+ * (nsteps+1)*L), out = image (device, N), written when the solve finishes.
+ * Needs nx % 4 == 0 (TMA-staged kernels).  Errors as pact_forward. */
+int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_xyz, int L, int nsteps, float* out);
+
+/* Advance every unfinished solve among hs[0..n-1] (n <= 64, one device) by
+ * min(ksteps, steps left) time steps, queued on `stream` (cudaStream_t) as one
+ * replay of a captured CUDA graph of ksteps multi-instance steps; a solve that
+ * finishes gets its read-out.  pact_begin of these handles must be ordered
+ * before it (use the same stream).  Errors: PACT_EINVAL, PACT_ECUDA,
+ * PACT_ETIMEOUT (an earlier advance on this device reported a timed-out
+ * wait); message via pact_last_error(NULL). */
+int pact_advance(pact_handle* hs, int n, int ksteps, void* stream);
+
+/* Steps done by the solve prepared on h (host bookkeeping; never touches the
+ * GPU).  Results are complete once steps_done == nsteps and the stream has
+ * reached that point. */
+int pact_poll(pact_handle h, int* steps_done);
+
 /* Forward operator H that allocates no device memory.  The paper has no
  * counterpart: this is a deployment variant of pact_forward for callers that
  * cannot call cudaMalloc -- code inside a host application that owns all device

@@ -79,8 +79,17 @@ struct pact_grid {
     // TMA-staged kernels (nx % 4 == 0) or the direct kernels
     bool tiled = false;
     TmaSet tm{};
+    // serving state (pact_begin / pact_advance / pact_poll)
+    bool sv_active = false;
+    int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
+    const float* sv_in = nullptr;
+    float* sv_out = nullptr;
+    RegionList sv_inner{}, sv_outer{};
+    int sv_ninner = 0, sv_nouter = 0;
     std::string err;
 };
+
+int serve_run(const MultiTable& T, int ksteps, cudaStream_t st, std::string& why);
 
 // message for pact_last_error(NULL) from calls that have no handle
 void pact_note_error(const std::string& msg) { g_err = msg; }
@@ -636,6 +645,93 @@ int pact_profile_read(pact_handle h, int kind, long long* launches, double* tota
     }
     *total_ms = ms;
     return device_status(h);
+}
+
+int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_xyz, int L, int nsteps, float* out) {
+    int rc = precheck(h, in, out, nsteps);
+    if (rc) return rc;
+    if (!h->tiled) return fail(h, PACT_EINVAL, "serving uses the TMA-staged kernels: nx must be a multiple of 4");
+    rc = set_receivers(h, rec_xyz, L);
+    if (rc) return rc;
+    rc = zero_state(h);
+    if (rc) return rc;
+    const StepParams p = make_params(h);
+    const RecTable r = make_rec(h);
+    h->sv_adj = is_adjoint ? 1 : 0;
+    h->sv_m = 0;
+    h->sv_nsteps = nsteps;
+    h->sv_in = in;
+    h->sv_out = out;
+    if (!is_adjoint) {
+        launch_source(in, p, h->stream);
+        launch_sample(p, r, out, h->stream);
+    } else {
+        launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
+        if (nsteps == 0) launch_readout(out, p, h->stream);
+    }
+    plan_instance_regions(p, 32, h->sv_inner, h->sv_ninner, h->sv_outer, h->sv_nouter);
+    h->sv_active = nsteps > 0;
+    CK(h, cudaGetLastError());
+    return PACT_OK;
+}
+
+int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
+    if (!hs || n < 0 || n > kMaxInst) return fail(nullptr, PACT_EINVAL, "pact_advance: 0 <= n <= 64 handles");
+    if (ksteps < 1) return fail(nullptr, PACT_EINVAL, "pact_advance: ksteps >= 1");
+    static thread_local MultiTable* T = nullptr;
+    if (!T) T = new (std::nothrow) MultiTable();
+    if (!T) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
+    int dev = -1, ni = 0;
+    T->pre_inner[0] = T->pre_outer[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        pact_handle h = hs[k];
+        if (!h) return fail(nullptr, PACT_EINVAL, "pact_advance: NULL handle");
+        if (!h->sv_active) continue;
+        if (dev < 0) dev = h->device;
+        if (h->device != dev) return fail(h, PACT_EINVAL, "pact_advance: handles on different devices");
+        InstDev& e = T->inst[ni];
+        e.tm = h->tm;
+        e.p = make_params(h);
+        e.inner = h->sv_inner;
+        e.outer = h->sv_outer;
+        e.rec = make_rec(h);
+        e.src = h->sv_adj ? h->sv_in : nullptr;
+        e.dst = h->sv_adj ? nullptr : h->sv_out;
+        e.adj = h->sv_adj;
+        e.m = h->sv_m;
+        e.nsteps = h->sv_nsteps;
+        e.L = h->L;
+        T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
+        T->pre_outer[ni + 1] = T->pre_outer[ni] + h->sv_nouter;
+        ++ni;
+    }
+    T->n_inst = ni;
+    if (ni == 0) return PACT_OK;
+    if (cudaSetDevice(dev) != cudaSuccess) return fail(nullptr, PACT_ECUDA, "cudaSetDevice failed");
+    std::string why;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = serve_run(*T, ksteps, st, why);
+    if (rc) return fail(nullptr, rc, why);
+    for (int k = 0; k < n; ++k) {
+        pact_handle h = hs[k];
+        if (!h->sv_active) continue;
+        h->sv_m = std::min(h->sv_nsteps, h->sv_m + ksteps);
+        if (h->sv_m == h->sv_nsteps) {
+            h->sv_active = false;
+            if (h->sv_adj) {
+                const StepParams p = make_params(h);
+                launch_readout(h->sv_out, p, st);
+            }
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(nullptr, PACT_ECUDA, "pact_advance: launch failed");
+    return PACT_OK;
+}
+
+int pact_poll(pact_handle h, int* steps_done) {
+    if (!h || !steps_done) return fail(h, PACT_EINVAL, "pact_poll: NULL argument");
+    *steps_done = h->sv_m;
+    return PACT_OK;
 }
 
 }  // extern "C"

@@ -68,19 +68,7 @@ template <bool ADJ, bool PML> struct StrCfg {
     }
 };
 
-// A rectangular block of work: tiles [tx0,tx1) x [ty0,ty1), planes [za,zb)
-// in chunks of zc planes; bstart = first block index of the region.
-struct Region {
-    int tx0, tx1, ty0, ty1, za, zb, zc, bstart;
-};
-constexpr int kMaxRegions = 7;
-struct RegionList {
-    int n;
-    Region r[kMaxRegions];
-};
-
-__device__ __forceinline__ void locate(const RegionList& rl, int& tile_x, int& tile_y, int& zc0, int& zc1) {
-    const int b = blockIdx.x;
+__device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1) {
     int r = 0;
     while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
     const Region& R = rl.r[r];
@@ -216,13 +204,11 @@ __device__ __forceinline__ float coef(int j, int hh, int w, const PmlXY& q, cons
 // ===========================================================================
 // velocity family
 // ===========================================================================
+// One (tile, z chunk) work item; false if a bounded wait timed out.
 template <bool ADJ, bool PML>
-__global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
-                                                  int* err) {
+__device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y, int zc0,
+                                         int zc1, int* err, float* sm) {
     using Cfg = VelCfg<ADJ, PML>;
-    extern __shared__ __align__(128) float sm[];
-    int tile_x, tile_y, zc0, zc1;
-    locate(rl, tile_x, tile_y, zc0, zc1);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -241,7 +227,7 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
         mbar_fence_init();
-        for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&tm.m[Cfg::tm(b)]);
+        for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
     auto issue = [&](int pl) {
@@ -249,7 +235,7 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
         float* dst = ring.stage(pl);
         mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
         for (int b = 0; b < Cfg::NB; ++b)
-            tma_load_3d(dst + b * BOXS, &tm.m[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+            tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
@@ -501,22 +487,25 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
             drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
-            return;
+            return false;
         }
         if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
     }
+    // every issued plane has been waited for: retire the barriers so that a
+    // persistent block can initialise them again for its next work item
+    if (tid == 0)
+        for (int s = 0; s < D; ++s) mbar_inval(&bar[s]);
+    return true;
 }
 
 // ===========================================================================
 // stress family
 // ===========================================================================
+// One (tile, z chunk) work item; false if a bounded wait timed out.
 template <bool ADJ, bool PML>
-__global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
-                                                  int* err) {
+__device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y, int zc0,
+                                         int zc1, int* err, float* sm) {
     using Cfg = StrCfg<ADJ, PML>;
-    extern __shared__ __align__(128) float sm[];
-    int tile_x, tile_y, zc0, zc1;
-    locate(rl, tile_x, tile_y, zc0, zc1);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -535,7 +524,7 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
         mbar_fence_init();
-        for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&tm.m[Cfg::tm(b)]);
+        for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
     auto issue = [&](int pl) {
@@ -543,7 +532,7 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
         float* dst = ring.stage(pl);
         mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
         for (int b = 0; b < Cfg::NB; ++b)
-            tma_load_3d(dst + b * BOXS, &tm.m[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+            tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
@@ -821,9 +810,66 @@ __global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_con
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
             drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
-            return;
+            return false;
         }
         if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
+    }
+    // every issued plane has been waited for: retire the barriers so that a
+    // persistent block can initialise them again for its next work item
+    if (tid == 0)
+        for (int s = 0; s < D; ++s) mbar_inval(&bar[s]);
+    return true;
+}
+
+// ===========================================================================
+// kernels: one grid (single instance) and persistent (many instances)
+// ===========================================================================
+template <bool ADJ, bool PML>
+__global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
+                                                  int* err) {
+    extern __shared__ __align__(128) float sm[];
+    int tile_x, tile_y, zc0, zc1;
+    locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
+    vel_body<ADJ, PML>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+}
+
+template <bool ADJ, bool PML>
+__global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
+                                                  int* err) {
+    extern __shared__ __align__(128) float sm[];
+    int tile_x, tile_y, zc0, zc1;
+    locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
+    str_body<ADJ, PML>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+}
+
+// Persistent multi-instance half steps: a fixed grid walks the work items of
+// every unfinished instance of the table (block b takes items b, b + grid,
+// ...), forward and adjoint instances alike.  STR selects the stress family.
+template <bool STR, bool PML>
+__global__ void __launch_bounds__(NT) k_multi(const MultiTable* __restrict__ T, int* err) {
+    extern __shared__ __align__(128) float sm[];
+    __shared__ StepParams sp;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int n = T->n_inst;
+    const int* pre = PML ? T->pre_outer : T->pre_inner;
+    const int total = pre[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int i = 0;
+        while (i + 1 < n && item >= pre[i + 1]) ++i;
+        const InstDev& I = T->inst[i];
+        if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
+        int tile_x, tile_y, zc0, zc1;
+        locate(PML ? I.outer : I.inner, item - pre[i], tile_x, tile_y, zc0, zc1);
+        __syncthreads();
+        for (int w = tid; w < (int)(sizeof(StepParams) / sizeof(int)); w += NT)
+            reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&I.p)[w];
+        __syncthreads();
+        bool ok;
+        if (STR) ok = I.adj ? str_body<true, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
+                            : str_body<false, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+        else ok = I.adj ? vel_body<true, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
+                        : vel_body<false, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+        if (!ok) return;
     }
 }
 
@@ -973,6 +1019,64 @@ static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cud
         k_str_tiled<ADJ, true><<<L.outer_blocks, dim3(TX, TY, 1), StrCfg<ADJ, true>::SMEM, st>>>(p, tm, L.outer, err);
     if (L.inner_blocks)
         k_str_tiled<ADJ, false><<<L.inner_blocks, dim3(TX, TY, 1), StrCfg<ADJ, false>::SMEM, st>>>(p, tm, L.inner, err);
+}
+
+// ---- multi-instance (persistent) launches --------------------------------
+template <bool STR, bool PML>
+static size_t multi_smem() {
+    return STR ? std::max(StrCfg<false, PML>::SMEM, StrCfg<true, PML>::SMEM)
+               : std::max(VelCfg<false, PML>::SMEM, VelCfg<true, PML>::SMEM);
+}
+
+template <bool STR, bool PML>
+static int multi_grid() {
+    static int grid[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!grid[dev]) {
+        const void* fn = (const void*)k_multi<STR, PML>;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)multi_smem<STR, PML>());
+        int sms = 148, per_sm = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, multi_smem<STR, PML>());
+        grid[dev] = sms * std::max(1, per_sm);
+    }
+    return grid[dev];
+}
+
+void launch_multi_step_half(bool str, const MultiTable* dT, int* err, cudaStream_t st) {
+    if (str) {
+        k_multi<true, true><<<multi_grid<true, true>(), dim3(TX, TY, 1), multi_smem<true, true>(), st>>>(dT, err);
+        k_multi<true, false><<<multi_grid<true, false>(), dim3(TX, TY, 1), multi_smem<true, false>(), st>>>(dT, err);
+    } else {
+        k_multi<false, true><<<multi_grid<false, true>(), dim3(TX, TY, 1), multi_smem<false, true>(), st>>>(dT, err);
+        k_multi<false, false><<<multi_grid<false, false>(), dim3(TX, TY, 1), multi_smem<false, false>(), st>>>(dT, err);
+    }
+}
+
+// Region plan of one instance for the persistent kernels: z chunks of about
+// `zc` planes so that work items of different instances are of similar size.
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
+                           int& nouter) {
+    const int sms = 148;
+    // a large "want" makes make_regions cap the interior chunking at zc
+    make_regions(p, 1, sms, inner, ninner, outer, nouter);
+    const int tiles_in = inner.n ? (inner.r[0].tx1 - inner.r[0].tx0) * (inner.r[0].ty1 - inner.r[0].ty0) : 0;
+    if (inner.n) {
+        Region& r = inner.r[0];
+        r.zc = std::max(1, std::min(zc, r.zb - r.za));
+        ninner = tiles_in * ((r.zb - r.za + r.zc - 1) / r.zc);
+    }
+    // outer frame regions (beyond the two z slabs) use the same chunk length
+    int blocks = 0;
+    for (int k = 0; k < outer.n; ++k) {
+        Region& r = outer.r[k];
+        if (k >= 2) r.zc = std::max(1, std::min(zc, r.zb - r.za));
+        r.bstart = blocks;
+        blocks += (r.tx1 - r.tx0) * (r.ty1 - r.ty0) * ((r.zb - r.za + r.zc - 1) / r.zc);
+    }
+    nouter = blocks;
 }
 
 void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {

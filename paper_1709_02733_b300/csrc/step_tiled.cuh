@@ -11,7 +11,46 @@ struct TmaSet {
     CUtensorMap m[TM_N];
 };
 
+// A rectangular block of work: tiles [tx0,tx1) x [ty0,ty1), planes [za,zb)
+// in chunks of zc planes; bstart = first block (work item) of the region.
+struct Region {
+    int tx0, tx1, ty0, ty1, za, zb, zc, bstart;
+};
+constexpr int kMaxRegions = 7;
+struct RegionList {
+    int n;
+    Region r[kMaxRegions];
+};
+
+// One instance (a forward or adjoint solve on its own grid) of the
+// persistent multi-instance step kernels.
+struct alignas(128) InstDev {
+    TmaSet tm;            // tensor maps of this instance's arrays
+    StepParams p;
+    RegionList inner;     // work items without C-PML code
+    RegionList outer;     // work items with C-PML code
+    RecTable rec;
+    const float* src;     // adjoint: traces to inject
+    float* dst;           // forward: traces to sample into
+    int adj;              // 0 forward, 1 adjoint
+    int m;                // steps done (advanced on the device)
+    int nsteps;
+    int L;
+};
+
+constexpr int kMaxInst = 64;
+struct MultiTable {
+    int n_inst;
+    int pre_inner[kMaxInst + 1];   // first work item of each instance
+    int pre_outer[kMaxInst + 1];
+    InstDev inst[kMaxInst];
+};
+
 // 0 on success; arrays[i] is the device base address of array i (order above)
 int make_tma_set(TmaSet* out, float* const* arrays, int nx, int ny, int nz);
 void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st);
 void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st);
+// persistent multi-instance half step (str = stress family) over a device table
+void launch_multi_step_half(bool str, const MultiTable* dT, int* err, cudaStream_t st);
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
+                           int& nouter);

@@ -27,7 +27,7 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 # every symbol include/pact.h declares
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
-           "pact_profile", "pact_profile_read", "pact_forward_noalloc"]
+           "pact_profile", "pact_profile_read", "pact_forward_noalloc", "pact_begin", "pact_advance", "pact_poll"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout"]
@@ -76,6 +76,9 @@ def load(path: str = SO_PATH):
     lib.pact_last_error.restype = ctypes.c_char_p
     lib.pact_query_bytes.argtypes = [D, i, i, ctypes.POINTER(ctypes.c_size_t)]
     lib.pact_get_wavefield.argtypes = [vp, fp]
+    lib.pact_begin.argtypes = [vp, i, fp, fp, i, i, fp]
+    lib.pact_advance.argtypes = [ctypes.POINTER(vp), i, i, vp]
+    lib.pact_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.pact_forward_noalloc.argtypes = [D, fp, fp, fp, fp, fp, fp, i, i, fp, vp]
     lib.pact_profile.argtypes = [vp, i]
     lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
@@ -97,6 +100,15 @@ def pact_query_bytes(desc: GridDesc, L: int = 0, nsteps: int = -1) -> int:
     _check(load().pact_query_bytes(ctypes.byref(pact_grid_desc.from_desc(desc)), int(L), int(nsteps),
                                    ctypes.byref(out)))
     return int(out.value)
+
+
+def pact_advance(grids, ksteps: int, stream=None):
+    """Advance the solves prepared on ``grids`` together by up to ksteps steps."""
+    import torch
+    lib = load()
+    arr = (ctypes.c_void_p * max(1, len(grids)))(*[g._h.value for g in grids])
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(lib.pact_advance(arr, len(grids), int(ksteps), ctypes.c_void_p(st)))
 
 
 def pact_forward_noalloc(desc: GridDesc, medium, p0, rec, nsteps: int, out=None, stream=None):
@@ -226,6 +238,23 @@ class Grid:
         return out
 
     get_wavefield = pact_get_wavefield
+
+    def pact_begin(self, is_adjoint: bool, inp, rec, nsteps: int, out):
+        """Prepare a solve for pact_advance (buffers must stay alive until done)."""
+        r, L = _rec_host(rec)
+        n_in = (nsteps + 1) * L if is_adjoint else self.N
+        n_out = self.N if is_adjoint else (nsteps + 1) * L
+        _check(self.lib.pact_begin(self._h, int(bool(is_adjoint)), _dev_ptr(inp, n_in),
+                                   r.ctypes.data_as(ctypes.c_void_p), L, int(nsteps), _dev_ptr(out, n_out)), self._h)
+
+    begin = pact_begin
+
+    def pact_poll(self) -> int:
+        n = ctypes.c_int(0)
+        _check(self.lib.pact_poll(self._h, ctypes.byref(n)), self._h)
+        return int(n.value)
+
+    poll = pact_poll
 
     def pact_profile(self, enable: bool = True):
         _check(self.lib.pact_profile(self._h, int(bool(enable))), self._h)

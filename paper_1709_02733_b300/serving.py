@@ -1,0 +1,287 @@
+"""Continuous-batching server for forward (H) and adjoint (H^T) solves.
+
+Requests of different grid sizes arrive over time.  The server keeps each
+admitted solve's medium, wavefield and buffers resident on the GPU, admits
+queued requests first-come-first-served while an HBM budget (and a slot limit)
+allows, and advances all admitted solves together: every ``pact_advance`` call
+replays a CUDA graph of k multi-instance steps (persistent step kernels that
+walk a device table of the admitted solves).  Solves finish independently;
+their memory is released and waiting requests are admitted in the same loop.
+
+The one-at-a-time baseline (``run_one_at_a_time``) solves the same requests in
+arrival order with ``pact_forward`` / ``pact_adjoint`` alone on the GPU.
+
+Host-side pieces (``Admission``) have no GPU dependency and are tested on CPU.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+from . import synth
+from .synth import GridDesc
+
+MAX_SLOTS = 64  # pact_advance takes at most 64 handles
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float           # seconds after the start of the stream
+    adjoint: bool
+    n: int                   # cubic grid side
+    nsteps: int
+    L: int
+    seed: int
+    # filled by the server
+    admitted: Optional[float] = None
+    done: Optional[float] = None
+    result: Optional[object] = field(default=None, repr=False)
+
+    @property
+    def updates(self) -> float:
+        return float(self.n) ** 3 * self.nsteps
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def make_stream(nreq=200, rate=40.0, seed=5, n_range=(96, 320), n_step=8, steps_range=(800, 2500),
+                L_range=(64, 512)) -> List[Request]:
+    """Seeded Poisson stream: exponential gaps (mean 1/rate), side uniform over
+    multiples of n_step in n_range, nsteps and L uniform, forward/adjoint 50/50."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    sides = np.arange(n_range[0], n_range[1] + 1, n_step)
+    out = []
+    for k in range(nreq):
+        t += rng.exponential(1.0 / rate)
+        out.append(Request(rid=k, arrival=t, adjoint=bool(rng.random() < 0.5), n=int(rng.choice(sides)),
+                           nsteps=int(rng.integers(steps_range[0], steps_range[1] + 1)),
+                           L=int(rng.integers(L_range[0], L_range[1] + 1)), seed=int(seed * 1000 + k)))
+    return out
+
+
+class Admission:
+    """First-come-first-served admission under a byte budget and a slot limit."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = MAX_SLOTS):
+        self.budget = int(budget_bytes)
+        self.max_slots = int(max_slots)
+        self.used = 0
+        self.slots = 0
+
+    def fits(self, nbytes: int) -> bool:
+        return self.slots < self.max_slots and self.used + nbytes <= self.budget
+
+    def take(self, nbytes: int) -> None:
+        assert self.fits(nbytes)
+        self.used += nbytes
+        self.slots += 1
+
+    def release(self, nbytes: int) -> None:
+        self.used -= nbytes
+        self.slots -= 1
+        assert self.used >= 0 and self.slots >= 0
+
+    def admit(self, queue: List, size_of: Callable[[object], int]) -> List:
+        """Pop and return the longest prefix of the queue that fits (FIFO: a
+        request that does not fit blocks the ones behind it)."""
+        out = []
+        while queue and self.fits(size_of(queue[0])):
+            r = queue.pop(0)
+            self.take(size_of(r))
+            out.append(r)
+        return out
+
+
+# ---------------------------------------------------------------------------
+# inputs (cached per grid side: the media are generated once)
+# ---------------------------------------------------------------------------
+SERVE_DX = 0.4e-3
+SERVE_NPML = 10
+
+
+class InputCache:
+    def __init__(self):
+        self._med: Dict[int, tuple] = {}
+
+    def workload(self, n: int):
+        if n not in self._med:
+            d = GridDesc(n, n, n, SERVE_DX, synth.CFL * SERVE_DX / synth.SKULL_VMAX, npml=SERVE_NPML,
+                         pml_vmax=synth.SKULL_VMAX)
+            med = synth.skull_medium(n, SERVE_DX, SERVE_NPML, seed=n)
+            p0 = synth.tubes_p0(n, SERVE_DX, SERVE_NPML, seed=n)
+            self._med[n] = (d, med, p0)
+        return self._med[n]
+
+    def device_workload(self, n: int):
+        """(desc, medium on the GPU, p0 on the GPU), uploaded once per grid side."""
+        import torch
+        if not hasattr(self, "_dev"):
+            self._dev = {}
+        if n not in self._dev:
+            d, med, p0 = self.workload(n)
+            self._dev[n] = (d, [torch.from_numpy(m).cuda() for m in med], torch.from_numpy(p0).cuda())
+        return self._dev[n]
+
+    def receivers(self, n: int, L: int):
+        geo = synth.skull_geometry(n, SERVE_DX, SERVE_NPML)
+        c = (n - 1) / 2.0
+        return synth.fibonacci_hemisphere(L, geo.R_rec / SERVE_DX, (c, c, c))
+
+    def traces(self, r: Request, dt: float):
+        return synth.band_limited_traces(r.nsteps, r.L, r.seed, dt)
+
+
+def request_bytes(r: Request, cache: InputCache) -> int:
+    """Device bytes a request holds while admitted: the handle (pact_query_bytes)
+    plus its medium copy, input and output buffers."""
+    from .pact import pact_query_bytes
+    d = cache.workload(r.n)[0]
+    N = r.n ** 3
+    io = (N + (r.nsteps + 1) * r.L) * 4
+    return pact_query_bytes(d, r.L, -1) + 4 * N * 4 + io
+
+
+# ---------------------------------------------------------------------------
+# the server
+# ---------------------------------------------------------------------------
+class _Active:
+    __slots__ = ("req", "grid", "bufs", "nbytes", "ev")
+
+    def __init__(self, req, grid, bufs, nbytes):
+        self.req, self.grid, self.bufs, self.nbytes, self.ev = req, grid, bufs, nbytes, None
+
+
+def _prepare(r: Request, cache: InputCache, stream):
+    """Handle + input/output buffers of one request, set up on `stream`
+    (pact_set_medium synchronises only that stream)."""
+    import torch
+    from .pact import Grid
+    d, dmed, p0 = cache.device_workload(r.n)
+    rec = cache.receivers(r.n, r.L)
+    with torch.cuda.stream(stream):
+        g = Grid(d, stream=stream)
+        g.set_medium(*dmed)
+        if r.adjoint:
+            inp = torch.from_numpy(cache.traces(r, d.dt)).to("cuda", non_blocking=False)
+            out = torch.empty(d.shape, device="cuda")
+        else:
+            inp = p0
+            out = torch.empty((r.nsteps + 1, r.L), device="cuda")
+    return g, rec, inp, out
+
+
+def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16, max_slots: int = 32,
+                   cache: Optional[InputCache] = None, realtime: bool = True) -> Dict:
+    """Serve the stream with continuous batching; returns statistics.
+
+    Loop: move arrived requests to the queue; admit FIFO under the budget
+    (each admission is prepared on a side stream that the serving stream then
+    waits for); replay one k-step multi-instance graph over all admitted
+    solves; retire solves whose last step has executed.  At most two graph
+    replays are in flight, so admissions and completions are seen within one
+    chunk.  realtime=False skips idle waits (arrivals are then virtual)."""
+    import collections
+
+    import torch
+    from .pact import pact_advance
+    cache = cache or InputCache()
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    adm = Admission(budget_bytes, min(max_slots, MAX_SLOTS))
+    pending = sorted(requests, key=lambda r: r.arrival)
+    queue: List[Request] = []
+    active: List[_Active] = []
+    finished: List[Request] = []
+    sizes = {r.rid: request_bytes(r, cache) for r in requests}
+    for n in sorted({r.n for r in requests}):
+        cache.device_workload(n)
+    torch.cuda.synchronize()
+    clock = {"t0": time.perf_counter()}
+    now = lambda: time.perf_counter() - clock["t0"]
+    inflight = collections.deque()
+    while pending or queue or active:
+        if not realtime and not active and not queue and pending and pending[0].arrival > now():
+            clock["t0"] -= pending[0].arrival - now()  # idle: jump to the next arrival
+        while pending and pending[0].arrival <= now():
+            queue.append(pending.pop(0))
+        admitted = adm.admit(queue, lambda q: sizes[q.rid])
+        for r in admitted:
+            r.admitted = now()
+            g, rec, inp, out = _prepare(r, cache, side)
+            g.begin(r.adjoint, inp, rec, r.nsteps, out)
+            active.append(_Active(r, g, (inp, out), sizes[r.rid]))
+        if admitted:
+            stream.wait_stream(side)
+        if not active:
+            if pending:
+                time.sleep(max(0.0, min(pending[0].arrival - now(), 0.005)))
+            continue
+        pact_advance([a.grid for a in active], ksteps, stream)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        inflight.append(ev)
+        for a in active:
+            if a.ev is None and a.grid.poll() >= a.req.nsteps:
+                a.ev = ev
+        while len(inflight) > 1:
+            inflight.popleft().synchronize()
+        still = []
+        for a in active:
+            if a.ev is not None and a.ev.query():
+                a.req.done = now()
+                a.req.result = a.bufs[1]
+                adm.release(a.nbytes)
+                a.grid.close()
+                finished.append(a.req)
+            else:
+                still.append(a)
+        active = still
+    torch.cuda.synchronize()
+    return summarize(finished, now())
+
+
+def run_one_at_a_time(requests: List[Request], cache: Optional[InputCache] = None, realtime: bool = True) -> Dict:
+    """Baseline: each request alone on the GPU, in arrival order."""
+    import torch
+    cache = cache or InputCache()
+    stream = torch.cuda.current_stream()
+    for n in sorted({r.n for r in requests}):
+        cache.device_workload(n)
+    torch.cuda.synchronize()
+    clock = {"t0": time.perf_counter()}
+    now = lambda: time.perf_counter() - clock["t0"]
+    done = []
+    for r in sorted(requests, key=lambda q: q.arrival):
+        if now() < r.arrival:
+            if realtime:
+                time.sleep(r.arrival - now())
+            else:
+                clock["t0"] -= r.arrival - now()
+        r.admitted = now()
+        g, rec, inp, out = _prepare(r, cache, stream)
+        if r.adjoint:
+            g.adjoint(inp, rec, out=out)
+        else:
+            g.forward(inp, rec, r.nsteps, out=out)
+        torch.cuda.synchronize()
+        r.done = now()
+        r.result = out
+        g.close()
+        done.append(r)
+    return summarize(done, now())
+
+
+def summarize(done: List[Request], wall: float) -> Dict:
+    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+    upd = sum(r.updates for r in done)
+    return {"requests": len(done), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "wall_s": wall, "updates": upd,
+            "updates_per_s": upd / wall if wall > 0 else math.nan}

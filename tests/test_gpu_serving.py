@@ -1,0 +1,98 @@
+"""Serving on the GPU: solves advanced together by the persistent
+multi-instance kernels give the same results as the same solves alone, and a
+queued stream served with continuous batching completes with correct results."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1709_02733_b300 import pact, synth  # noqa: E402
+from paper_1709_02733_b300.serving import InputCache, make_stream, run_continuous, run_one_at_a_time  # noqa: E402
+from paper_1709_02733_b300.synth import GridDesc  # noqa: E402
+
+TOL_MIX = 1e-6
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1709_02733_b300 import build
+    build.build()
+
+
+def _random(shape, npml, seed, L):
+    rho, lam, mu, al, vmax = synth.random_medium(shape, seed)
+    nz, ny, nx = shape
+    d = GridDesc(nx, ny, nz, 1e-3, 0.3e-3 / vmax, npml=npml, pml_vmax=vmax)
+    rng = np.random.default_rng(seed)
+    return d, (rho, lam, mu, al), rng.standard_normal(shape).astype(np.float32), synth.random_receivers(L, shape, seed)
+
+
+def test_mixed_solves_match_solo():
+    w = synth.skull(48, 1.2e-3, 6, 60, 40, seed=21)
+    cases = [("fwd", w.desc, w.medium, w.p0, w.rec, 60)]
+    d, med, p0, rec = _random((36, 44, 40), 3, 22, 17)
+    cases.append(("fwd", d, med, p0, rec, 45))
+    d, med, p0, rec = _random((48, 56, 64), 4, 23, 21)
+    cases.append(("adj", d, med, p0, rec, 38))
+    wp = synth.plain_fluid_64(npml=3, nsteps=50)
+    cases.append(("adj", wp.desc, wp.medium, wp.p0, wp.rec, 50))
+    grids, bufs, solo = [], [], []
+    rng = np.random.default_rng(3)
+    for kind, d, med, p0, rec, ns in cases:
+        g = pact.Grid(d)
+        g.set_medium(*[cuda(m) for m in med])
+        if kind == "fwd":
+            inp = cuda(p0)
+            ref = g.forward(inp, rec, ns).cpu().numpy()
+            out = torch.full((ns + 1, rec.shape[0]), float("nan"), device="cuda")
+        else:
+            inp = cuda(rng.standard_normal((ns + 1, rec.shape[0])))
+            ref = g.adjoint(inp, rec).cpu().numpy()
+            out = torch.full(d.shape, float("nan"), device="cuda")
+        g.begin(kind == "adj", inp, rec, ns, out)
+        grids.append(g)
+        bufs.append((inp, out))
+        solo.append(ref)
+    k = 7
+    for _ in range(100):
+        if all(g.poll() >= c[5] for g, c in zip(grids, cases)):
+            break
+        pact.pact_advance(grids, k)
+    torch.cuda.synchronize()
+    for (kind, *_rest), (inp, out), ref in zip(cases, bufs, solo):
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got)), kind
+        assert rel_l2(got, ref) <= TOL_MIX, kind
+
+
+def test_continuous_batching_stream():
+    """A small seeded stream under a budget that admits only part of it at a
+    time: every request completes and equals its one-at-a-time result."""
+    reqs = make_stream(10, rate=200.0, seed=7, n_range=(64, 112), n_step=16, steps_range=(60, 160),
+                       L_range=(32, 96))
+    reqs2 = make_stream(10, rate=200.0, seed=7, n_range=(64, 112), n_step=16, steps_range=(60, 160),
+                        L_range=(32, 96))
+    cache = InputCache()
+    from paper_1709_02733_b300.serving import request_bytes
+    budget = 3 * max(request_bytes(r, cache) for r in reqs)
+    st = run_continuous(reqs, budget, ksteps=8, max_slots=8, cache=cache, realtime=False)
+    assert st["requests"] == 10
+    base = run_one_at_a_time(reqs2, cache=cache, realtime=False)
+    assert base["requests"] == 10
+    by = {r.rid: r for r in reqs2}
+    for r in reqs:
+        a = r.result.cpu().numpy()
+        b = by[r.rid].result.cpu().numpy()
+        assert rel_l2(a, b) <= TOL_MIX, r.rid
+        assert r.done >= r.arrival
