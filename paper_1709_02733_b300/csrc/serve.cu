@@ -95,8 +95,9 @@ int serve_run(const MultiTable& T, int ksteps, cudaStream_t st, std::string& why
         SCK(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
     }
     if (*S.host_err) {
-        why = "serve: a multi-instance step kernel gave up waiting for its TMA loads";
-        return PACT_ETIMEOUT;
+        why = *S.host_err == 2 ? "serve: a multi-instance work item fell outside its grid (skipped)"
+                               : "serve: a multi-instance step kernel gave up waiting for its TMA loads";
+        return *S.host_err == 2 ? PACT_EINVAL : PACT_ETIMEOUT;
     }
     auto it = S.graphs.find(ksteps);
     if (it == S.graphs.end()) {

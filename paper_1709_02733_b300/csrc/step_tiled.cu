@@ -860,9 +860,18 @@ __global__ void __launch_bounds__(NT) k_multi(const MultiTable* __restrict__ T, 
         if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
         int tile_x, tile_y, zc0, zc1;
         locate(PML ? I.outer : I.inner, item - pre[i], tile_x, tile_y, zc0, zc1);
+        // a work item must lie inside its instance's grid; otherwise record
+        // the inconsistency and touch nothing
+        if (tile_x < 0 || tile_x * TX >= I.p.nx || tile_y < 0 || tile_y * TY >= I.p.ny || zc0 < 0 || zc0 >= zc1 ||
+            zc1 > I.p.nz) {
+            if (tid == 0) atomicExch(err, 2);
+            continue;
+        }
         __syncthreads();
         for (int w = tid; w < (int)(sizeof(StepParams) / sizeof(int)); w += NT)
             reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&I.p)[w];
+        if (tid == 0)
+            for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
         __syncthreads();
         bool ok;
         if (STR) ok = I.adj ? str_body<true, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)

@@ -79,10 +79,9 @@ def test_mixed_solves_match_solo():
 def test_continuous_batching_stream():
     """A small seeded stream under a budget that admits only part of it at a
     time: every request completes and equals its one-at-a-time result."""
-    reqs = make_stream(10, rate=200.0, seed=7, n_range=(64, 112), n_step=16, steps_range=(60, 160),
-                       L_range=(32, 96))
-    reqs2 = make_stream(10, rate=200.0, seed=7, n_range=(64, 112), n_step=16, steps_range=(60, 160),
-                        L_range=(32, 96))
+    kw = dict(rate=200.0, seed=7, n_range=(96, 128), n_step=16, steps_range=(60, 160), L_range=(32, 96))
+    reqs = make_stream(10, **kw)
+    reqs2 = make_stream(10, **kw)
     cache = InputCache()
     from paper_1709_02733_b300.serving import request_bytes
     budget = 3 * max(request_bytes(r, cache) for r in reqs)
@@ -92,7 +91,8 @@ def test_continuous_batching_stream():
     assert base["requests"] == 10
     by = {r.rid: r for r in reqs2}
     for r in reqs:
-        a = r.result.cpu().numpy()
-        b = by[r.rid].result.cpu().numpy()
-        assert rel_l2(a, b) <= TOL_MIX, r.rid
+        a = r.result.cpu().numpy().astype(np.float64)
+        b = by[r.rid].result.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(a)) and np.linalg.norm(b) > 0, r.rid
+        assert np.linalg.norm(a - b) <= TOL_MIX * np.linalg.norm(b), r.rid
         assert r.done >= r.arrival
