@@ -27,6 +27,7 @@ void launch_source(const float* p0, const StepParams& p, cudaStream_t st);
 void launch_readout(float* img, const StepParams& p, cudaStream_t st);
 void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStream_t st);
 void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st);
+void launch_inv_mu(const float* mu, float* inv, size_t n, cudaStream_t st);
 void launch_medium_check(const float* rho, const float* lam, const float* mu, const float* alpha, size_t n,
                          unsigned int* out, cudaStream_t st);
 
@@ -47,7 +48,7 @@ struct pact_grid {
     int device = 0;
     size_t N = 0;
     float* fields = nullptr;      // 9N
-    float* medium = nullptr;      // 4N
+    float* medium = nullptr;      // 5N: rho, lambda, mu, alpha, 1/mu
     float* tables = nullptr;      // 3 axes x 2 lattices x 3 (a,b,chi) x nmax
     int nmax = 0;
     float* slabs[3] = {nullptr, nullptr, nullptr};  // 6 x slab size per axis
@@ -159,7 +160,7 @@ int check_desc(const pact_grid_desc* d, std::string& why) {
 
 static size_t desc_bytes(const pact_grid_desc& d, int L, int nsteps) {
     const size_t N = (size_t)d.nx * d.ny * d.nz;
-    size_t b = 13 * N * sizeof(float);  // fields + medium
+    size_t b = 14 * N * sizeof(float);  // fields + medium (incl. 1/mu)
     for (int a = 0; a < 3; ++a) b += 6 * slab_points(d, a) * sizeof(float);
     const int nmax = std::max(d.nx, std::max(d.ny, d.nz));
     b += 18 * (size_t)nmax * sizeof(float) + 16;
@@ -452,7 +453,7 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
         return bail(PACT_ECUDA);
     }
     cudaError_t e = cudaMalloc(&h->fields, 9 * h->N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->medium, 4 * h->N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->medium, 5 * h->N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->tables, 18 * (size_t)h->nmax * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch_u32, 4 * sizeof(unsigned int));
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
@@ -475,7 +476,7 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
         for (int i = 0; i < 9; ++i) arrays[i] = h->fields + i * h->N;
         arrays[TM_RHO] = h->medium;
         arrays[TM_LAM] = h->medium + h->N;
-        arrays[TM_MU] = h->medium + 2 * h->N;
+        arrays[TM_MU] = h->medium + 4 * h->N;  // the TMA-staged kernels read 1/mu
         arrays[TM_ALPHA] = h->medium + 3 * h->N;
         h->tiled = make_tma_set(&h->tm, arrays, desc->nx, desc->ny, desc->nz) == 0;
     }
@@ -495,6 +496,7 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     CK(h, cudaMemcpyAsync(h->medium + 3 * N, alpha, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemsetAsync(h->scratch_u32, 0, 4 * sizeof(unsigned int), s));
     launch_medium_check(h->medium, h->medium + N, h->medium + 2 * N, h->medium + 3 * N, N, h->scratch_u32, s);
+    launch_inv_mu(h->medium + 2 * N, h->medium + 4 * N, N, s);
     CK(h, cudaGetLastError());
     unsigned int red[4];
     CK(h, cudaMemcpyAsync(red, h->scratch_u32, sizeof red, cudaMemcpyDeviceToHost, s));

@@ -371,6 +371,14 @@ __global__ void k_inject(float* s0, float* s1, float* s2, RecTable r, const floa
     s2[q] -= acc;
 }
 
+// 1/mu for the TMA-staged kernels (+inf at fluid nodes, where mu = 0)
+__global__ void k_inv_mu(const float* __restrict__ mu, float* inv, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float m = mu[i];
+        inv[i] = m > 0.0f ? 1.0f / m : __int_as_float(0x7f800000);
+    }
+}
+
 // medium reduction: [0] max (lambda+2mu)/rho, [1] max alpha, as float bits
 // (all values checked >= 0 before use); [2] count of invalid nodes
 __global__ void k_medium_check(const float* __restrict__ rho, const float* __restrict__ lam,
@@ -450,6 +458,10 @@ void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStrea
 
 void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st) {
     if (r.ncorner > 0) k_inject<<<(r.ncorner + 127) / 128, 128, 0, st>>>(p.s[0], p.s[1], p.s[2], r, ph);
+}
+
+void launch_inv_mu(const float* mu, float* inv, size_t n, cudaStream_t st) {
+    k_inv_mu<<<ew_blocks(n), 256, 0, st>>>(mu, inv, n);
 }
 
 void launch_medium_check(const float* rho, const float* lam, const float* mu, const float* alpha, size_t n,

@@ -47,20 +47,31 @@ constexpr int OX = 4, OY = 2;   // own point offset inside the box
 constexpr int D = 4;            // stage ring depth (planes)
 
 template <bool ADJ, bool PML> struct VelCfg {
-    // stage boxes: 0..5 sigma (Voigt), 6 rho, 7 alpha, [adjoint: 8 lambda, 9 mu]
-    static constexpr int NB = ADJ ? 10 : 8;
-    static constexpr int NDER = ADJ ? 6 : 0;
+    // stage boxes 0..5: sigma (Voigt); then
+    //   forward:            6 rho, 7 alpha
+    //   adjoint, C-PML:     6 rho, 7 alpha, 8 lambda, 9 1/mu
+    //   adjoint, interior:  6 lambda, 7 1/mu (alpha is read through the cache)
+    // The interior adjoint computes its material-weighted fields in place in
+    // the stage of the output plane; the C-PML adjoint uses NDER extra boxes.
+    static constexpr int NB = ADJ ? (PML ? 10 : 8) : 8;
+    static constexpr int BRHO = (ADJ && !PML) ? -1 : 6;
+    static constexpr int BALPHA = (ADJ && !PML) ? -1 : 7;
+    static constexpr int BLAM = ADJ ? (PML ? 8 : 6) : -1;
+    static constexpr int BMU = ADJ ? (PML ? 9 : 7) : -1;
+    static constexpr int NDER = (ADJ && PML) ? 6 : 0;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) {
-        return b < 6 ? TM_S0 + b : (b == 6 ? TM_RHO : (b == 7 ? TM_ALPHA : (b == 8 ? TM_LAM : TM_MU)));
+        return b < 6 ? TM_S0 + b
+                     : (b == BRHO ? TM_RHO : (b == BALPHA ? TM_ALPHA : (b == BLAM ? TM_LAM : TM_MU)));
     }
 };
 
 template <bool ADJ, bool PML> struct StrCfg {
-    // stage boxes: 0..2 u, then forward: 3 lambda, 4 mu;
-    // adjoint: 3 rho [C-PML variant: 4 lambda, 5 mu, for the psi tails]
+    // stage boxes 0..2: u; then forward: 3 lambda, 4 1/mu; adjoint: 3 rho
+    // [C-PML adjoint: 4 lambda, 5 1/mu, for the psi tails].  The interior
+    // adjoint forms w = dt u / rho in place; the C-PML adjoint uses NDER boxes.
     static constexpr int NB = ADJ ? (PML ? 6 : 4) : 5;
-    static constexpr int NDER = ADJ ? 6 : 0;
+    static constexpr int NDER = (ADJ && PML) ? 6 : 0;
     static constexpr int BLAM = ADJ ? 4 : 3, BMU = ADJ ? 5 : 4;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) {
@@ -108,9 +119,12 @@ __device__ __forceinline__ void push(float* q, float h) {
 
 __device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
 
-// harmonic mean of four values; 0 if any is 0 (1/0 = inf makes the sum inf)
-__device__ __forceinline__ float harm4f(float a, float b, float c, float d) {
-    return __fdividef(4.0f, frcp(a) + frcp(b) + frcp(c) + frcp(d));
+// The TMA-staged kernels read r = 1/mu (+inf at fluid nodes).
+// mu = 1/r (0 at fluid nodes); the harmonic mean of four mu is 4 / (r1+r2+r3+r4),
+// which is 0 as soon as one node is fluid (the sum is +inf).
+__device__ __forceinline__ float mu_of(float r) { return frcp(r); }
+__device__ __forceinline__ float harm_inv(float a, float b, float c, float d) {
+    return __fdividef(4.0f, a + b + c + d);
 }
 
 __device__ __forceinline__ bool in_slab_plane(int k, int n, int P) {
@@ -247,12 +261,20 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     // own-point values of the next output plane, loaded one visit ahead
     float nu[3] = {0.f, 0.f, 0.f};
     float nph[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float na[4] = {0.f, 0.f, 0.f, 0.f};  // interior adjoint: alpha at p, +x, +y, +z (clamped)
+    const unsigned dx1 = (x + 1 < p.nx) ? 1u : 0u, dy1 = (y + 1 < p.ny) ? (unsigned)p.nx : 0u;
     auto prefetch = [&](int zn) {
         if (!own || zn < zc0 || zn >= zc1) return;
         const unsigned g = (unsigned)zn * nxy + gxy;
         nu[0] = p.u[0][g];
         nu[1] = p.u[1][g];
         nu[2] = p.u[2][g];
+        if constexpr (Cfg::BALPHA < 0) {
+            na[0] = __ldg(p.alpha + g);
+            na[1] = __ldg(p.alpha + g + dx1);
+            na[2] = __ldg(p.alpha + g + dy1);
+            na[3] = __ldg(p.alpha + g + ((zn + 1 < p.nz) ? nxy : 0u));
+        }
         if constexpr (PML) {
             const int lz = slab_local(zn, p.nz, P);
 #pragma unroll
@@ -291,6 +313,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const int z = pl - 2;
         const bool out = z >= zc0;
         float cu[3] = {nu[0], nu[1], nu[2]};
+        const float ca[4] = {na[0], na[1], na[2], na[3]};
         float cph[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -311,30 +334,30 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                 push(q23, spm ? spm[3 * BOXS + o] : 0.f);
             } else {
                 float h33 = 0.f, h13 = 0.f, h23 = 0.f;
-                if (pl >= 0 && pl < p.nz) {
+                if (own && pl >= 0 && pl < p.nz) {
                     const float s11 = sp[o], s22 = sp[BOXS + o], s33 = sp[2 * BOXS + o];
-                    const float lam = sp[8 * BOXS + o], mu2 = 2.0f * sp[9 * BOXS + o];
+                    const float lam = sp[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(sp[Cfg::BMU * BOXS + o]);
                     const float ltr = lam * (s11 + s22 + s33);
                     h33 = dt * (ltr + mu2 * s33);
                     if constexpr (PML) {
                         const int l = slab_local(pl, p.nz, P);
-                        if (own && l >= 0) {
+                        if (l >= 0) {
                             const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
                             h33 += a * (chp[0] + dt * (ltr + mu2 * chi * s33));
                         }
                     }
                 }
                 const int zm = pl - 1;
-                if (spm && zm >= 0 && zm < p.nz) {
-                    const float* mz = spm + 9 * BOXS;                    // mu at plane pl-1
-                    const float* mz1 = (pl < p.nz) ? sp + 9 * BOXS : mz;  // mu at plane pl (clamped)
-                    const float m13 = harm4f(mz[o], mz[o + xc1], mz1[o], mz1[o + xc1]);
-                    const float m23 = harm4f(mz[o], mz[o + yc1], mz1[o], mz1[o + yc1]);
+                if (own && spm && zm >= 0 && zm < p.nz) {
+                    const float* mz = spm + Cfg::BMU * BOXS;                    // 1/mu at plane pl-1
+                    const float* mz1 = (pl < p.nz) ? sp + Cfg::BMU * BOXS : mz;  // 1/mu at plane pl (clamped)
+                    const float m13 = harm_inv(mz[o], mz[o + xc1], mz1[o], mz1[o + xc1]);
+                    const float m23 = harm_inv(mz[o], mz[o + yc1], mz1[o], mz1[o + yc1]);
                     h13 = dt * m13 * spm[4 * BOXS + o];
                     h23 = dt * m23 * spm[3 * BOXS + o];
                     if constexpr (PML) {
                         const int l = slab_local(zm, p.nz, P);
-                        if (own && l >= 0) {
+                        if (l >= 0) {
                             const float a = tabv(p, 2, 1, 0, zm), chi = tabv(p, 2, 1, 2, zm);
                             h13 += a * (chp[1] + chi * h13);
                             h23 += a * (chp[2] + chi * h23);
@@ -348,7 +371,8 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         }
 
         if (out) {
-            const float* sz = ring.stage(z);
+            float* szw = ring.stage(z);
+            const float* sz = szw;
             const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
             const float *XD0, *XD1, *XD2, *YD0, *YD1, *YD2;
             if constexpr (!ADJ) {
@@ -358,35 +382,103 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                 YD0 = sz + 1 * BOXS;  // s22
                 YD1 = sz + 5 * BOXS;  // s12
                 YD2 = sz + 3 * BOXS;  // s23
+            } else if constexpr (!PML) {
+                // Material-weighted stress fields of plane z, in place over the
+                // cross-shaped region the differences read: the x band (rows
+                // OY..OY+TY-1, columns OX-2..OX+TX+1) and four y rows (OY-2, OY-1,
+                // OY+TY, OY+TY+1; columns OX..OX+TX-1).  Off the layers the shear
+                // field is the same for both difference directions.
+                //   s11 <- Q_x, s22 <- Q_y, s12 <- dt mu12 s12, s13 <- dt mu13 s13,
+                //   s23 <- dt mu23 s23; zero outside the grid.
+                const float* lm = sz + Cfg::BLAM * BOXS;
+                const float* i0 = sz + Cfg::BMU * BOXS;
+                const float* i1 = sz1 + Cfg::BMU * BOXS;
+                constexpr int XB = (TX + 4) * TY, YE = 4 * TX;
+                if (ok) {
+                    for (int i = tid; i < XB + YE; i += NT) {
+                        int bx, by;
+                        bool inx, iny;
+                        if (i < XB) {
+                            bx = OX - 2 + i % (TX + 4);
+                            by = OY + i / (TX + 4);
+                            inx = true;
+                            iny = bx >= OX && bx < OX + TX;
+                        } else {
+                            const int j = i - XB, r = j / TX;
+                            bx = OX + j % TX;
+                            by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
+                            inx = false;
+                            iny = true;
+                        }
+                        const int q = by * BW + bx;
+                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+                        float vqx = 0.f, vqy = 0.f, v12 = 0.f, v13 = 0.f, v23 = 0.f;
+                        if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny) {
+                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
+                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
+                            const int qxy = (gx + 1 < p.nx) ? qy1 + 1 : qy1;
+                            const float a11 = sz[q], a22 = sz[BOXS + q], a33 = sz[2 * BOXS + q];
+                            const float r0 = i0[q];
+                            const float ltr = dt * lm[q] * (a11 + a22 + a33);
+                            const float mu2 = 2.0f * dt * mu_of(r0);
+                            v12 = dt * harm_inv(r0, i0[qx1], i0[qy1], i0[qxy]) * sz[5 * BOXS + q];
+                            if (inx) {
+                                vqx = ltr + mu2 * a11;
+                                v13 = dt * harm_inv(r0, i0[qx1], i1[q], i1[qx1]) * sz[4 * BOXS + q];
+                            }
+                            if (iny) {
+                                vqy = ltr + mu2 * a22;
+                                v23 = dt * harm_inv(r0, i0[qy1], i1[q], i1[qy1]) * sz[3 * BOXS + q];
+                            }
+                        }
+                        szw[5 * BOXS + q] = v12;
+                        if (inx) {
+                            szw[q] = vqx;
+                            szw[4 * BOXS + q] = v13;
+                        }
+                        if (iny) {
+                            szw[BOXS + q] = vqy;
+                            szw[3 * BOXS + q] = v23;
+                        }
+                    }
+                }
+                __syncthreads();
+                XD0 = sz;             // Q_x
+                XD1 = sz + 5 * BOXS;  // S_12
+                XD2 = sz + 4 * BOXS;  // S_13
+                YD0 = sz + BOXS;      // Q_y
+                YD1 = sz + 5 * BOXS;  // S_12
+                YD2 = sz + 3 * BOXS;  // S_23
             } else {
-                // material-weighted stress fields of plane z into shared memory
+                // C-PML blocks: the x- and y-differenced shear fields differ by
+                // their memory-variable terms, so they get separate boxes
                 float* Qx = der;
                 float* Syx = der + BOXS;
                 float* Szx = der + 2 * BOXS;
                 float* Qy = der + 3 * BOXS;
                 float* Sxy = der + 4 * BOXS;
                 float* Szy = der + 5 * BOXS;
-                const float* m0 = sz + 9 * BOXS;
-                const float* m1 = sz1 + 9 * BOXS;
+                const float* m0 = sz + Cfg::BMU * BOXS;
+                const float* m1 = sz1 + Cfg::BMU * BOXS;
                 if (ok) {
                     // x-differenced: columns OX-2..OX+TX+1, rows OY..OY+TY-1
                     for (int i = tid; i < (TX + 4) * TY; i += NT) {
                         const int bx = OX - 2 + i % (TX + 4), by = OY + i / (TX + 4);
                         const int q = by * BW + bx;
                         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                        const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                        const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
-                        const float lam = sz[8 * BOXS + q], mu2 = 2.0f * m0[q];
-                        const float ltr = lam * (s11 + s22 + s33);
-                        float vq = dt * (ltr + mu2 * s11);
-                        const float m12 = harm4f(m0[q], m0[qx1], m0[qy1], m0[(gy + 1 < p.ny) ? qx1 + BW : qx1]);
-                        const float m13 = harm4f(m0[q], m0[qx1], m1[q], m1[qx1]);
-                        float v12 = dt * m12 * sz[5 * BOXS + q];
-                        float v13 = dt * m13 * sz[4 * BOXS + q];
-                        if constexpr (PML) {
-                            const bool in = gx >= 0 && gx < p.nx && gy < p.ny;
-                            if (in && slab_local(gx, p.nx, P) >= 0) {
+                        float vq = 0.f, v12 = 0.f, v13 = 0.f;
+                        if (gx >= 0 && gx < p.nx && gy < p.ny) {
+                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
+                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
+                            const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
+                            const float lam = sz[Cfg::BLAM * BOXS + q], mu2 = 2.0f * mu_of(m0[q]);
+                            const float ltr = lam * (s11 + s22 + s33);
+                            vq = dt * (ltr + mu2 * s11);
+                            const float m12 = harm_inv(m0[q], m0[qx1], m0[qy1], m0[(gy + 1 < p.ny) ? qx1 + BW : qx1]);
+                            const float m13 = harm_inv(m0[q], m0[qx1], m1[q], m1[qx1]);
+                            v12 = dt * m12 * sz[5 * BOXS + q];
+                            v13 = dt * m13 * sz[4 * BOXS + q];
+                            if (slab_local(gx, p.nx, P) >= 0) {
                                 const long si = slab_at(p, 0, gx, gy, z);
                                 const float ai = tabv(p, 0, 0, 0, gx), ci = tabv(p, 0, 0, 2, gx);
                                 const float ah = tabv(p, 0, 1, 0, gx), ch = tabv(p, 0, 1, 2, gx);
@@ -404,19 +496,19 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                         const int bx = OX + i % TX, by = OY - 2 + i / TX;
                         const int q = by * BW + bx;
                         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                        const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                        const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
-                        const float lam = sz[8 * BOXS + q], mu2 = 2.0f * m0[q];
-                        const float ltr = lam * (s11 + s22 + s33);
-                        float vq = dt * (ltr + mu2 * s22);
-                        const float m12 = harm4f(m0[q], m0[qx1], m0[qy1], m0[(gx + 1 < p.nx) ? qy1 + 1 : qy1]);
-                        const float m23 = harm4f(m0[q], m0[qy1], m1[q], m1[qy1]);
-                        float v12 = dt * m12 * sz[5 * BOXS + q];
-                        float v23 = dt * m23 * sz[3 * BOXS + q];
-                        if constexpr (PML) {
-                            const bool in = gx < p.nx && gy >= 0 && gy < p.ny;
-                            if (in && slab_local(gy, p.ny, P) >= 0) {
+                        float vq = 0.f, v12 = 0.f, v23 = 0.f;
+                        if (gx < p.nx && gy >= 0 && gy < p.ny) {
+                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
+                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
+                            const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
+                            const float lam = sz[Cfg::BLAM * BOXS + q], mu2 = 2.0f * mu_of(m0[q]);
+                            const float ltr = lam * (s11 + s22 + s33);
+                            vq = dt * (ltr + mu2 * s22);
+                            const float m12 = harm_inv(m0[q], m0[qx1], m0[qy1], m0[(gx + 1 < p.nx) ? qy1 + 1 : qy1]);
+                            const float m23 = harm_inv(m0[q], m0[qy1], m1[q], m1[qy1]);
+                            v12 = dt * m12 * sz[5 * BOXS + q];
+                            v23 = dt * m23 * sz[3 * BOXS + q];
+                            if (slab_local(gy, p.ny, P) >= 0) {
                                 const long si = slab_at(p, 1, gx, gy, z);
                                 const float ai = tabv(p, 1, 0, 0, gy), ci = tabv(p, 1, 0, 2, gy);
                                 const float ah = tabv(p, 1, 1, 0, gy), ch = tabv(p, 1, 1, 2, gy);
@@ -442,12 +534,21 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                 const float g[3][3] = {{dpx(XD0, o) * h, dmy(YD1, o) * h, dq(q13) * h},   // u^x
                                        {dmx(XD1, o) * h, dpy(YD0, o) * h, dq(q23) * h},   // u^y
                                        {dmx(XD2, o) * h, dmy(YD2, o) * h, dq(q33) * h}};  // u^z
-                const float* r0 = sz + 6 * BOXS;
-                const float* a0 = sz + 7 * BOXS;
-                const float rb[3] = {0.5f * (r0[o] + r0[o + xc1]), 0.5f * (r0[o] + r0[o + yc1]),
-                                     0.5f * (r0[o] + sz1[6 * BOXS + o])};
-                const float ab[3] = {0.5f * (a0[o] + a0[o + xc1]), 0.5f * (a0[o] + a0[o + yc1]),
-                                     0.5f * (a0[o] + sz1[7 * BOXS + o])};
+                float rb[3] = {1.f, 1.f, 1.f}, ab[3];
+                if constexpr (Cfg::BALPHA >= 0) {
+                    const float* r0 = sz + Cfg::BRHO * BOXS;
+                    const float* a0 = sz + Cfg::BALPHA * BOXS;
+                    rb[0] = 0.5f * (r0[o] + r0[o + xc1]);
+                    rb[1] = 0.5f * (r0[o] + r0[o + yc1]);
+                    rb[2] = 0.5f * (r0[o] + sz1[Cfg::BRHO * BOXS + o]);
+                    ab[0] = 0.5f * (a0[o] + a0[o + xc1]);
+                    ab[1] = 0.5f * (a0[o] + a0[o + yc1]);
+                    ab[2] = 0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o]);
+                } else {
+                    ab[0] = 0.5f * (ca[0] + ca[1]);
+                    ab[1] = 0.5f * (ca[0] + ca[2]);
+                    ab[2] = 0.5f * (ca[0] + ca[3]);
+                }
                 PmlZ pz{};
                 if constexpr (PML) pml_z_init(pz, p, z);
                 const unsigned gi = (unsigned)z * nxy + gxy;
@@ -642,7 +743,8 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         }
 
         if (out) {
-            const float* sz = ring.stage(z);
+            float* szw = ring.stage(z);
+            const float* sz = szw;
             const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
             const float *XD0, *XD1, *XD2, *YD0, *YD1, *YD2;
             if constexpr (!ADJ) {
@@ -652,6 +754,51 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 YD0 = sz + BOXS;      // u^y  (D-y for s22)
                 YD1 = sz;             // u^x  (D+y for s12)
                 YD2 = sz + 2 * BOXS;  // u^z  (D+y for s23)
+            } else if constexpr (!PML) {
+                // w = dt u / rho on the velocity nodes, in place over the
+                // cross-shaped region the differences read (x band and four y
+                // rows, as in the velocity family); zero outside the grid.  Off
+                // the layers R_ij = w_i for every difference direction j.
+                float* U0 = szw;
+                float* U1 = szw + BOXS;
+                float* U2 = szw + 2 * BOXS;
+                const float* r0 = sz + 3 * BOXS;
+                const float* r1 = sz1 + 3 * BOXS;
+                constexpr int XB = (TX + 4) * TY, YE = 4 * TX;
+                if (ok) {
+                    for (int i = tid; i < XB + YE; i += NT) {
+                        int bx, by;
+                        if (i < XB) {
+                            bx = OX - 2 + i % (TX + 4);
+                            by = OY + i / (TX + 4);
+                        } else {
+                            const int j = i - XB, r = j / TX;
+                            bx = OX + j % TX;
+                            by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
+                        }
+                        const int q = by * BW + bx;
+                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+                        float wx = 0.f, wy = 0.f, wz = 0.f;
+                        if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny) {
+                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
+                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
+                            const float rr = r0[q];
+                            wx = __fdividef(2.0f * dt, rr + r0[qx1]) * U0[q];
+                            wy = __fdividef(2.0f * dt, rr + r0[qy1]) * U1[q];
+                            wz = __fdividef(2.0f * dt, rr + r1[q]) * U2[q];
+                        }
+                        U0[q] = wx;
+                        U1[q] = wy;
+                        U2[q] = wz;
+                    }
+                }
+                __syncthreads();
+                XD0 = U0;
+                XD1 = U1;
+                XD2 = U2;
+                YD0 = U1;
+                YD1 = U0;
+                YD2 = U2;
             } else {
                 float* Rxx = der;
                 float* Ryx = der + BOXS;
@@ -741,10 +888,10 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 if constexpr (!ADJ) {
                     const float* m0 = sz + Cfg::BMU * BOXS;
                     const float* m1 = sz1 + Cfg::BMU * BOXS;
-                    const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * m0[o];
-                    const float m12 = harm4f(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
-                    const float m13 = harm4f(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
-                    const float m23 = harm4f(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);
+                    const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(m0[o]);
+                    const float m12 = harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
+                    const float m13 = harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
+                    const float m23 = harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);
                     // memory variables psi^{ij} (lattice: integer if i == j, else half)
                     float cp[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // chi * psi
                     float pd[3] = {0.f, 0.f, 0.f};                                         // psi^{kk}
@@ -777,11 +924,11 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                         // psi <- B~ (psi + Delta^T sigma_old) at the own point
                         const float* m0 = sz + Cfg::BMU * BOXS;
                         const float* m1 = sz1 + Cfg::BMU * BOXS;
-                        const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * m0[o];
+                        const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(m0[o]);
                         const float ltr = lam * (so[0] + so[1] + so[2]);
-                        const float msh[3] = {harm4f(m0[o], m0[o + yc1], m1[o], m1[o + yc1]),   // 23
-                                              harm4f(m0[o], m0[o + xc1], m1[o], m1[o + xc1]),   // 13
-                                              harm4f(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy])};  // 12
+                        const float msh[3] = {harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]),   // 23
+                                              harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]),   // 13
+                                              harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy])};  // 12
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
                             if (in_axis(j, px, pz.lz)) {
