@@ -48,17 +48,17 @@ constexpr int D = 4;            // stage ring depth (planes)
 
 template <bool ADJ, bool PML> struct VelCfg {
     // stage boxes 0..5: sigma (Voigt); then
-    //   forward:            6 rho, 7 alpha
-    //   adjoint, C-PML:     6 rho, 7 alpha, 8 lambda, 9 1/mu
-    //   adjoint, interior:  6 lambda, 7 1/mu (alpha is read through the cache)
-    // The interior adjoint computes its material-weighted fields in place in
-    // the stage of the output plane; the C-PML adjoint uses NDER extra boxes.
-    static constexpr int NB = ADJ ? (PML ? 10 : 8) : 8;
-    static constexpr int BRHO = (ADJ && !PML) ? -1 : 6;
-    static constexpr int BALPHA = (ADJ && !PML) ? -1 : 7;
-    static constexpr int BLAM = ADJ ? (PML ? 8 : 6) : -1;
-    static constexpr int BMU = ADJ ? (PML ? 9 : 7) : -1;
-    static constexpr int NDER = (ADJ && PML) ? 6 : 0;
+    //   forward: 6 rho, 7 alpha
+    //   adjoint: 6 lambda, 7 1/mu (rho and alpha are read through the cache)
+    // The adjoint computes its material-weighted fields in place in the stage
+    // of the output plane; C-PML blocks keep the x-differenced sigma12 field,
+    // which differs from the y-differenced one inside the layers, in one extra box.
+    static constexpr int NB = 8;
+    static constexpr int BRHO = ADJ ? -1 : 6;
+    static constexpr int BALPHA = ADJ ? -1 : 7;
+    static constexpr int BLAM = ADJ ? 6 : -1;
+    static constexpr int BMU = ADJ ? 7 : -1;
+    static constexpr int NDER = (ADJ && PML) ? 1 : 0;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) {
         return b < 6 ? TM_S0 + b
@@ -68,10 +68,11 @@ template <bool ADJ, bool PML> struct VelCfg {
 
 template <bool ADJ, bool PML> struct StrCfg {
     // stage boxes 0..2: u; then forward: 3 lambda, 4 1/mu; adjoint: 3 rho
-    // [C-PML adjoint: 4 lambda, 5 1/mu, for the psi tails].  The interior
-    // adjoint forms w = dt u / rho in place; the C-PML adjoint uses NDER boxes.
+    // [C-PML adjoint: 4 lambda, 5 1/mu, for the psi tails].  The adjoint forms
+    // w = dt u / rho in place; C-PML blocks keep the y-differenced fields, which
+    // differ from the x-differenced ones inside the layers, in three extra boxes.
     static constexpr int NB = ADJ ? (PML ? 6 : 4) : 5;
-    static constexpr int NDER = (ADJ && PML) ? 6 : 0;
+    static constexpr int NDER = (ADJ && PML) ? 3 : 0;
     static constexpr int BLAM = ADJ ? 4 : 3, BMU = ADJ ? 5 : 4;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) {
@@ -125,6 +126,85 @@ __device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
 __device__ __forceinline__ float mu_of(float r) { return frcp(r); }
 __device__ __forceinline__ float harm_inv(float a, float b, float c, float d) {
     return __fdividef(4.0f, a + b + c + d);
+}
+
+// The cross-shaped region the x and y differences read: the x band (rows
+// OY..OY+TY-1, columns OX-2..OX+TX+1) and four y rows (OY-2, OY-1, OY+TY,
+// OY+TY+1; columns OX..OX+TX-1): 416 positions, at most two per thread.  The
+// positions a thread owns are the same on every plane, so their box index,
+// clamped +x / +y neighbour offsets and band flags are computed once.
+constexpr int NCROSS = (TX + 4) * TY + 4 * TX;
+constexpr unsigned char CP_EXISTS = 1, CP_IN = 2, CP_XB = 4, CP_YB = 8;
+struct CrossPos {
+    int q[2];
+    short dx[2], dy[2];
+    unsigned char f[2];
+};
+
+__device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0, int nx, int ny) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * NT;
+        c.q[k] = 0;
+        c.dx[k] = c.dy[k] = 0;
+        c.f[k] = 0;
+        if (i >= NCROSS) continue;
+        int bx, by;
+        bool inx, iny;
+        if (i < (TX + 4) * TY) {
+            bx = OX - 2 + i % (TX + 4);
+            by = OY + i / (TX + 4);
+            inx = true;
+            iny = bx >= OX && bx < OX + TX;
+        } else {
+            const int j = i - (TX + 4) * TY, r = j / TX;
+            bx = OX + j % TX;
+            by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
+            inx = false;
+            iny = true;
+        }
+        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        c.q[k] = by * BW + bx;
+        c.dx[k] = (gx + 1 < nx) ? 1 : 0;
+        c.dy[k] = (gy + 1 < ny) ? BW : 0;
+        c.f[k] = CP_EXISTS | (in ? CP_IN : 0) | (inx ? CP_XB : 0) | (iny ? CP_YB : 0);
+    }
+}
+
+// C-PML data of the cross positions: per box column / row the layer
+// coefficients (a and chi on the integer and half lattice) and, per position,
+// the slab index base of the x slab (x-band positions) and y slab (y-band
+// positions), -1 off the layer.
+struct CrossPml {
+    int sx[2], sy[2];
+};
+
+__device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy, const CrossPos& cp, int tid,
+                                               int x0, int y0, const StepParams& p) {
+    const int W = 2 * p.P + 1;
+    for (int i = tid; i < BW + BH; i += NT) {
+        float* t = i < BW ? cx + 4 * i : cy + 4 * (i - BW);
+        const int axis = i < BW ? 0 : 1;
+        const int g = i < BW ? x0 - 4 + i : y0 - 2 + (i - BW);
+        const int n = axis == 0 ? p.nx : p.ny;
+        const bool in = g >= 0 && g < n && slab_local(g, n, p.P) >= 0;
+        t[0] = in ? __ldg(p.tab[axis][0][0] + g) : 0.f;  // a, integer lattice
+        t[1] = in ? __ldg(p.tab[axis][0][2] + g) : 0.f;  // chi, integer lattice
+        t[2] = in ? __ldg(p.tab[axis][1][0] + g) : 0.f;  // a, half lattice
+        t[3] = in ? __ldg(p.tab[axis][1][2] + g) : 0.f;  // chi, half lattice
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        c.sx[k] = c.sy[k] = -1;
+        const unsigned char f = cp.f[k];
+        if (!(f & CP_IN)) continue;
+        const int bx = cp.q[k] % BW, by = cp.q[k] / BW;
+        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+        const int lx = slab_local(gx, p.nx, p.P), ly = slab_local(gy, p.ny, p.P);
+        if ((f & CP_XB) && lx >= 0) c.sx[k] = gy * W + lx;
+        if ((f & CP_YB) && ly >= 0) c.sy[k] = ly * p.nx + gx;
+    }
 }
 
 __device__ __forceinline__ bool in_slab_plane(int k, int n, int P) {
@@ -257,11 +337,21 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     float q33[4] = {0, 0, 0, 0}, q13[4] = {0, 0, 0, 0}, q23[4] = {0, 0, 0, 0};
     const int xc1 = (x + 1 < p.nx) ? 1 : 0;   // clamped +x neighbour offset
     const int yc1 = (y + 1 < p.ny) ? BW : 0;  // clamped +y neighbour offset
+    CrossPos cross{};
+    CrossPml cpm{};
+    __shared__ float cxt[(ADJ && PML) ? 4 * BW : 1], cyt[(ADJ && PML) ? 4 * BH : 1];
+    if constexpr (ADJ) cross_init(cross, tid, x0, y0, p.nx, p.ny);
+    if constexpr (ADJ && PML) {
+        __syncthreads();  // a persistent block may still read the tables of its previous item
+        cross_pml_init(cpm, cxt, cyt, cross, tid, x0, y0, p);
+        __syncthreads();
+    }
 
     // own-point values of the next output plane, loaded one visit ahead
     float nu[3] = {0.f, 0.f, 0.f};
     float nph[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float na[4] = {0.f, 0.f, 0.f, 0.f};  // interior adjoint: alpha at p, +x, +y, +z (clamped)
+    float na[4] = {0.f, 0.f, 0.f, 0.f};  // adjoint: alpha at p, +x, +y, +z (clamped)
+    float nr[4] = {0.f, 0.f, 0.f, 0.f};  // C-PML adjoint: rho at the same points
     const unsigned dx1 = (x + 1 < p.nx) ? 1u : 0u, dy1 = (y + 1 < p.ny) ? (unsigned)p.nx : 0u;
     auto prefetch = [&](int zn) {
         if (!own || zn < zc0 || zn >= zc1) return;
@@ -270,10 +360,17 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         nu[1] = p.u[1][g];
         nu[2] = p.u[2][g];
         if constexpr (Cfg::BALPHA < 0) {
+            const unsigned dz1 = (zn + 1 < p.nz) ? nxy : 0u;
             na[0] = __ldg(p.alpha + g);
             na[1] = __ldg(p.alpha + g + dx1);
             na[2] = __ldg(p.alpha + g + dy1);
-            na[3] = __ldg(p.alpha + g + ((zn + 1 < p.nz) ? nxy : 0u));
+            na[3] = __ldg(p.alpha + g + dz1);
+            if constexpr (PML) {
+                nr[0] = __ldg(p.rho + g);
+                nr[1] = __ldg(p.rho + g + dx1);
+                nr[2] = __ldg(p.rho + g + dy1);
+                nr[3] = __ldg(p.rho + g + dz1);
+            }
         }
         if constexpr (PML) {
             const int lz = slab_local(zn, p.nz, P);
@@ -314,6 +411,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const bool out = z >= zc0;
         float cu[3] = {nu[0], nu[1], nu[2]};
         const float ca[4] = {na[0], na[1], na[2], na[3]};
+        const float cr[4] = {nr[0], nr[1], nr[2], nr[3]};
         float cph[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -322,6 +420,28 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const float chp[3] = {nhp[0], nhp[1], nhp[2]};
         prefetch(z + 1);
         prefetch_heads(pl + 1);
+        // C-PML adjoint: memory variables at the cross positions of plane z
+        float dps[2][6];
+        if constexpr (ADJ && PML) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+#pragma unroll
+                for (int t = 0; t < 6; ++t) dps[k][t] = 0.f;
+                if (!out) continue;
+                if (cpm.sx[k] >= 0) {
+                    const unsigned si = (unsigned)z * p.ny * (2 * P + 1) + cpm.sx[k];
+                    dps[k][0] = p.psi[0][0][si];
+                    dps[k][1] = p.psi[1][0][si];
+                    dps[k][2] = p.psi[2][0][si];
+                }
+                if (cpm.sy[k] >= 0) {
+                    const unsigned si = (unsigned)z * (2 * P + 1) * p.nx + cpm.sy[k];
+                    dps[k][3] = p.psi[1][1][si];
+                    dps[k][4] = p.psi[0][1][si];
+                    dps[k][5] = p.psi[2][1][si];
+                }
+            }
+        }
         const int kk = pl - pfirst;
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
         const float* sp = ring.stage(pl);
@@ -393,50 +513,35 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                 const float* lm = sz + Cfg::BLAM * BOXS;
                 const float* i0 = sz + Cfg::BMU * BOXS;
                 const float* i1 = sz1 + Cfg::BMU * BOXS;
-                constexpr int XB = (TX + 4) * TY, YE = 4 * TX;
                 if (ok) {
-                    for (int i = tid; i < XB + YE; i += NT) {
-                        int bx, by;
-                        bool inx, iny;
-                        if (i < XB) {
-                            bx = OX - 2 + i % (TX + 4);
-                            by = OY + i / (TX + 4);
-                            inx = true;
-                            iny = bx >= OX && bx < OX + TX;
-                        } else {
-                            const int j = i - XB, r = j / TX;
-                            bx = OX + j % TX;
-                            by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
-                            inx = false;
-                            iny = true;
-                        }
-                        const int q = by * BW + bx;
-                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const unsigned char f = cross.f[k];
+                        if (!(f & CP_EXISTS)) continue;
+                        const int q = cross.q[k];
                         float vqx = 0.f, vqy = 0.f, v12 = 0.f, v13 = 0.f, v23 = 0.f;
-                        if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny) {
-                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                            const int qxy = (gx + 1 < p.nx) ? qy1 + 1 : qy1;
+                        if (f & CP_IN) {
+                            const int qx1 = q + cross.dx[k], qy1 = q + cross.dy[k];
                             const float a11 = sz[q], a22 = sz[BOXS + q], a33 = sz[2 * BOXS + q];
                             const float r0 = i0[q];
                             const float ltr = dt * lm[q] * (a11 + a22 + a33);
                             const float mu2 = 2.0f * dt * mu_of(r0);
-                            v12 = dt * harm_inv(r0, i0[qx1], i0[qy1], i0[qxy]) * sz[5 * BOXS + q];
-                            if (inx) {
+                            v12 = dt * harm_inv(r0, i0[qx1], i0[qy1], i0[qy1 + cross.dx[k]]) * sz[5 * BOXS + q];
+                            if (f & CP_XB) {
                                 vqx = ltr + mu2 * a11;
                                 v13 = dt * harm_inv(r0, i0[qx1], i1[q], i1[qx1]) * sz[4 * BOXS + q];
                             }
-                            if (iny) {
+                            if (f & CP_YB) {
                                 vqy = ltr + mu2 * a22;
                                 v23 = dt * harm_inv(r0, i0[qy1], i1[q], i1[qy1]) * sz[3 * BOXS + q];
                             }
                         }
                         szw[5 * BOXS + q] = v12;
-                        if (inx) {
+                        if (f & CP_XB) {
                             szw[q] = vqx;
                             szw[4 * BOXS + q] = v13;
                         }
-                        if (iny) {
+                        if (f & CP_YB) {
                             szw[BOXS + q] = vqy;
                             szw[3 * BOXS + q] = v23;
                         }
@@ -450,85 +555,69 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                 YD1 = sz + 5 * BOXS;  // S_12
                 YD2 = sz + 3 * BOXS;  // S_23
             } else {
-                // C-PML blocks: the x- and y-differenced shear fields differ by
-                // their memory-variable terms, so they get separate boxes
-                float* Qx = der;
-                float* Syx = der + BOXS;
-                float* Szx = der + 2 * BOXS;
-                float* Qy = der + 3 * BOXS;
-                float* Sxy = der + 4 * BOXS;
-                float* Szy = der + 5 * BOXS;
-                const float* m0 = sz + Cfg::BMU * BOXS;
-                const float* m1 = sz1 + Cfg::BMU * BOXS;
+                // C-PML blocks: as in the interior, plus the memory-variable
+                // terms of the x and y layers (adjoint of Delta and E~): Q_x, S_zx
+                // and the x-differenced S_yx take the x-layer terms, Q_y, S_zy and
+                // the y-differenced S_xy the y-layer terms; S_yx goes to box E.
+                float* E = der;
+                const float* lm = sz + Cfg::BLAM * BOXS;
+                const float* i0 = sz + Cfg::BMU * BOXS;
+                const float* i1 = sz1 + Cfg::BMU * BOXS;
                 if (ok) {
-                    // x-differenced: columns OX-2..OX+TX+1, rows OY..OY+TY-1
-                    for (int i = tid; i < (TX + 4) * TY; i += NT) {
-                        const int bx = OX - 2 + i % (TX + 4), by = OY + i / (TX + 4);
-                        const int q = by * BW + bx;
-                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        float vq = 0.f, v12 = 0.f, v13 = 0.f;
-                        if (gx >= 0 && gx < p.nx && gy < p.ny) {
-                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                            const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
-                            const float lam = sz[Cfg::BLAM * BOXS + q], mu2 = 2.0f * mu_of(m0[q]);
-                            const float ltr = lam * (s11 + s22 + s33);
-                            vq = dt * (ltr + mu2 * s11);
-                            const float m12 = harm_inv(m0[q], m0[qx1], m0[qy1], m0[(gy + 1 < p.ny) ? qx1 + BW : qx1]);
-                            const float m13 = harm_inv(m0[q], m0[qx1], m1[q], m1[qx1]);
-                            v12 = dt * m12 * sz[5 * BOXS + q];
-                            v13 = dt * m13 * sz[4 * BOXS + q];
-                            if (slab_local(gx, p.nx, P) >= 0) {
-                                const long si = slab_at(p, 0, gx, gy, z);
-                                const float ai = tabv(p, 0, 0, 0, gx), ci = tabv(p, 0, 0, 2, gx);
-                                const float ah = tabv(p, 0, 1, 0, gx), ch = tabv(p, 0, 1, 2, gx);
-                                vq += ai * (p.psi[0][0][si] + dt * (ltr + mu2 * ci * s11));
-                                v12 += ah * (p.psi[1][0][si] + ch * v12);
-                                v13 += ah * (p.psi[2][0][si] + ch * v13);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const unsigned char f = cross.f[k];
+                        if (!(f & CP_EXISTS)) continue;
+                        const int q = cross.q[k];
+                        float vqx = 0.f, vqy = 0.f, v12 = 0.f, e12 = 0.f, v13 = 0.f, v23 = 0.f;
+                        if (f & CP_IN) {
+                            const int qx1 = q + cross.dx[k], qy1 = q + cross.dy[k];
+                            const float a11 = sz[q], a22 = sz[BOXS + q], a33 = sz[2 * BOXS + q];
+                            const float r0 = i0[q];
+                            const float ltr = dt * lm[q] * (a11 + a22 + a33);
+                            const float mu2 = 2.0f * dt * mu_of(r0);
+                            const float b12 = dt * harm_inv(r0, i0[qx1], i0[qy1], i0[qy1 + cross.dx[k]]) * sz[5 * BOXS + q];
+                            v12 = e12 = b12;
+                            if (f & CP_XB) {
+                                vqx = ltr + mu2 * a11;
+                                v13 = dt * harm_inv(r0, i0[qx1], i1[q], i1[qx1]) * sz[4 * BOXS + q];
+                                if (cpm.sx[k] >= 0) {
+                                    const float* t = cxt + 4 * (q % BW);
+                                    vqx += t[0] * (dps[k][0] + ltr + mu2 * t[1] * a11);
+                                    e12 = b12 + t[2] * (dps[k][1] + t[3] * b12);
+                                    v13 += t[2] * (dps[k][2] + t[3] * v13);
+                                }
+                            }
+                            if (f & CP_YB) {
+                                vqy = ltr + mu2 * a22;
+                                v23 = dt * harm_inv(r0, i0[qy1], i1[q], i1[qy1]) * sz[3 * BOXS + q];
+                                if (cpm.sy[k] >= 0) {
+                                    const float* t = cyt + 4 * (q / BW);
+                                    vqy += t[0] * (dps[k][3] + ltr + mu2 * t[1] * a22);
+                                    v12 = b12 + t[2] * (dps[k][4] + t[3] * b12);
+                                    v23 += t[2] * (dps[k][5] + t[3] * v23);
+                                }
                             }
                         }
-                        Qx[q] = vq;
-                        Syx[q] = v12;
-                        Szx[q] = v13;
-                    }
-                    // y-differenced: columns OX..OX+TX-1, rows OY-2..OY+TY+1
-                    for (int i = tid; i < TX * (TY + 4); i += NT) {
-                        const int bx = OX + i % TX, by = OY - 2 + i / TX;
-                        const int q = by * BW + bx;
-                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        float vq = 0.f, v12 = 0.f, v23 = 0.f;
-                        if (gx < p.nx && gy >= 0 && gy < p.ny) {
-                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                            const float s11 = sz[q], s22 = sz[BOXS + q], s33 = sz[2 * BOXS + q];
-                            const float lam = sz[Cfg::BLAM * BOXS + q], mu2 = 2.0f * mu_of(m0[q]);
-                            const float ltr = lam * (s11 + s22 + s33);
-                            vq = dt * (ltr + mu2 * s22);
-                            const float m12 = harm_inv(m0[q], m0[qx1], m0[qy1], m0[(gx + 1 < p.nx) ? qy1 + 1 : qy1]);
-                            const float m23 = harm_inv(m0[q], m0[qy1], m1[q], m1[qy1]);
-                            v12 = dt * m12 * sz[5 * BOXS + q];
-                            v23 = dt * m23 * sz[3 * BOXS + q];
-                            if (slab_local(gy, p.ny, P) >= 0) {
-                                const long si = slab_at(p, 1, gx, gy, z);
-                                const float ai = tabv(p, 1, 0, 0, gy), ci = tabv(p, 1, 0, 2, gy);
-                                const float ah = tabv(p, 1, 1, 0, gy), ch = tabv(p, 1, 1, 2, gy);
-                                vq += ai * (p.psi[1][1][si] + dt * (ltr + mu2 * ci * s22));
-                                v12 += ah * (p.psi[0][1][si] + ch * v12);
-                                v23 += ah * (p.psi[2][1][si] + ch * v23);
-                            }
+                        szw[5 * BOXS + q] = v12;
+                        E[q] = e12;
+                        if (f & CP_XB) {
+                            szw[q] = vqx;
+                            szw[4 * BOXS + q] = v13;
                         }
-                        Qy[q] = vq;
-                        Sxy[q] = v12;
-                        Szy[q] = v23;
+                        if (f & CP_YB) {
+                            szw[BOXS + q] = vqy;
+                            szw[3 * BOXS + q] = v23;
+                        }
                     }
                 }
                 __syncthreads();
-                XD0 = Qx;
-                XD1 = Syx;
-                XD2 = Szx;
-                YD0 = Qy;
-                YD1 = Sxy;
-                YD2 = Szy;
+                XD0 = sz;             // Q_x
+                XD1 = E;              // S_yx
+                XD2 = sz + 4 * BOXS;  // S_zx
+                YD0 = sz + BOXS;      // Q_y
+                YD1 = sz + 5 * BOXS;  // S_xy
+                YD2 = sz + 3 * BOXS;  // S_zy
             }
             if (ok && own) {
                 const float g[3][3] = {{dpx(XD0, o) * h, dmy(YD1, o) * h, dq(q13) * h},   // u^x
@@ -548,6 +637,11 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                     ab[0] = 0.5f * (ca[0] + ca[1]);
                     ab[1] = 0.5f * (ca[0] + ca[2]);
                     ab[2] = 0.5f * (ca[0] + ca[3]);
+                    if constexpr (PML) {
+                        rb[0] = 0.5f * (cr[0] + cr[1]);
+                        rb[1] = 0.5f * (cr[0] + cr[2]);
+                        rb[2] = 0.5f * (cr[0] + cr[3]);
+                    }
                 }
                 PmlZ pz{};
                 if constexpr (PML) pml_z_init(pz, p, z);
@@ -642,6 +736,15 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     const int xc1 = (x + 1 < p.nx) ? 1 : 0;
     const int yc1 = (y + 1 < p.ny) ? BW : 0;
     const int oxy = o + xc1 + yc1;
+    CrossPos cross{};
+    CrossPml cpm{};
+    __shared__ float cxt[(ADJ && PML) ? 4 * BW : 1], cyt[(ADJ && PML) ? 4 * BH : 1];
+    if constexpr (ADJ) cross_init(cross, tid, x0, y0, p.nx, p.ny);
+    if constexpr (ADJ && PML) {
+        __syncthreads();  // a persistent block may still read the tables of its previous item
+        cross_pml_init(cpm, cxt, cyt, cross, tid, x0, y0, p);
+        __syncthreads();
+    }
 
     // own stresses and psi of the next output plane, loaded one visit ahead
     float ns[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -699,6 +802,28 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         const float chp[3] = {nhp[0], nhp[1], nhp[2]};
         prefetch(z + 1);
         prefetch_heads(pl + 1);
+        // C-PML adjoint: memory variables phi at the cross positions of plane z
+        float dph[2][6];
+        if constexpr (ADJ && PML) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+#pragma unroll
+                for (int t = 0; t < 6; ++t) dph[k][t] = 0.f;
+                if (!out) continue;
+                if (cpm.sx[k] >= 0) {
+                    const unsigned si = (unsigned)z * p.ny * (2 * P + 1) + cpm.sx[k];
+                    dph[k][0] = p.phi[0][0][si];
+                    dph[k][1] = p.phi[1][0][si];
+                    dph[k][2] = p.phi[2][0][si];
+                }
+                if (cpm.sy[k] >= 0) {
+                    const unsigned si = (unsigned)z * (2 * P + 1) * p.nx + cpm.sy[k];
+                    dph[k][3] = p.phi[1][1][si];
+                    dph[k][4] = p.phi[0][1][si];
+                    dph[k][5] = p.phi[2][1][si];
+                }
+            }
+        }
         const int kk = pl - pfirst;
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
         const float* sp = ring.stage(pl);
@@ -764,27 +889,17 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 float* U2 = szw + 2 * BOXS;
                 const float* r0 = sz + 3 * BOXS;
                 const float* r1 = sz1 + 3 * BOXS;
-                constexpr int XB = (TX + 4) * TY, YE = 4 * TX;
                 if (ok) {
-                    for (int i = tid; i < XB + YE; i += NT) {
-                        int bx, by;
-                        if (i < XB) {
-                            bx = OX - 2 + i % (TX + 4);
-                            by = OY + i / (TX + 4);
-                        } else {
-                            const int j = i - XB, r = j / TX;
-                            bx = OX + j % TX;
-                            by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
-                        }
-                        const int q = by * BW + bx;
-                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const unsigned char f = cross.f[k];
+                        if (!(f & CP_EXISTS)) continue;
+                        const int q = cross.q[k];
                         float wx = 0.f, wy = 0.f, wz = 0.f;
-                        if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny) {
-                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
+                        if (f & CP_IN) {
                             const float rr = r0[q];
-                            wx = __fdividef(2.0f * dt, rr + r0[qx1]) * U0[q];
-                            wy = __fdividef(2.0f * dt, rr + r0[qy1]) * U1[q];
+                            wx = __fdividef(2.0f * dt, rr + r0[q + cross.dx[k]]) * U0[q];
+                            wy = __fdividef(2.0f * dt, rr + r0[q + cross.dy[k]]) * U1[q];
                             wz = __fdividef(2.0f * dt, rr + r1[q]) * U2[q];
                         }
                         U0[q] = wx;
@@ -800,81 +915,61 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 YD1 = U0;
                 YD2 = U2;
             } else {
-                float* Rxx = der;
-                float* Ryx = der + BOXS;
-                float* Rzx = der + 2 * BOXS;
-                float* Ryy = der + 3 * BOXS;
-                float* Rxy = der + 4 * BOXS;
-                float* Rzy = der + 5 * BOXS;
+                // C-PML blocks: w as in the interior, plus the memory-variable
+                // terms of the x and y layers (adjoint of Gamma and E): the
+                // x-differenced fields R_xx, R_yx, R_zx stay in place, the
+                // y-differenced R_yy, R_xy, R_zy go to boxes E0, E1, E2.
+                float* U0 = szw;
+                float* U1 = szw + BOXS;
+                float* U2 = szw + 2 * BOXS;
+                float* E0 = der;
+                float* E1 = der + BOXS;
+                float* E2 = der + 2 * BOXS;
                 const float* r0 = sz + 3 * BOXS;
                 const float* r1 = sz1 + 3 * BOXS;
                 if (ok) {
-                    for (int i = tid; i < (TX + 4) * TY; i += NT) {
-                        const int bx = OX - 2 + i % (TX + 4), by = OY + i / (TX + 4);
-                        const int q = by * BW + bx;
-                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const unsigned char f = cross.f[k];
+                        if (!(f & CP_EXISTS)) continue;
+                        const int q = cross.q[k];
                         float wx = 0.f, wy = 0.f, wz = 0.f;
-                        if (gx >= 0 && gx < p.nx && gy < p.ny) {
-                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                            wx = __fdividef(2.0f * dt, r0[q] + r0[qx1]) * sz[q];
-                            wy = __fdividef(2.0f * dt, r0[q] + r0[qy1]) * sz[BOXS + q];
-                            wz = __fdividef(2.0f * dt, r0[q] + r1[q]) * sz[2 * BOXS + q];
-                            if constexpr (PML) {
-                                if (slab_local(gx, p.nx, P) >= 0) {
-                                    const long si = slab_at(p, 0, gx, gy, z);
-                                    const float ah = tabv(p, 0, 1, 0, gx), ch = tabv(p, 0, 1, 2, gx);
-                                    const float ai = tabv(p, 0, 0, 0, gx), ci = tabv(p, 0, 0, 2, gx);
-                                    const float vx = wx + ah * (p.phi[0][0][si] + ch * wx);
-                                    const float vy = wy + ai * (p.phi[1][0][si] + ci * wy);
-                                    const float vz = wz + ai * (p.phi[2][0][si] + ci * wz);
-                                    wx = vx;
-                                    wy = vy;
-                                    wz = vz;
-                                }
-                            }
+                        if (f & CP_IN) {
+                            const float rr = r0[q];
+                            wx = __fdividef(2.0f * dt, rr + r0[q + cross.dx[k]]) * U0[q];
+                            wy = __fdividef(2.0f * dt, rr + r0[q + cross.dy[k]]) * U1[q];
+                            wz = __fdividef(2.0f * dt, rr + r1[q]) * U2[q];
                         }
-                        Rxx[q] = wx;
-                        Ryx[q] = wy;
-                        Rzx[q] = wz;
-                    }
-                    for (int i = tid; i < TX * (TY + 4); i += NT) {
-                        const int bx = OX + i % TX, by = OY - 2 + i / TX;
-                        const int q = by * BW + bx;
-                        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-                        float wx = 0.f, wy = 0.f, wz = 0.f;
-                        if (gx < p.nx && gy >= 0 && gy < p.ny) {
-                            const int qx1 = (gx + 1 < p.nx) ? q + 1 : q;
-                            const int qy1 = (gy + 1 < p.ny) ? q + BW : q;
-                            wx = __fdividef(2.0f * dt, r0[q] + r0[qx1]) * sz[q];
-                            wy = __fdividef(2.0f * dt, r0[q] + r0[qy1]) * sz[BOXS + q];
-                            wz = __fdividef(2.0f * dt, r0[q] + r1[q]) * sz[2 * BOXS + q];
-                            if constexpr (PML) {
-                                if (slab_local(gy, p.ny, P) >= 0) {
-                                    const long si = slab_at(p, 1, gx, gy, z);
-                                    const float ah = tabv(p, 1, 1, 0, gy), ch = tabv(p, 1, 1, 2, gy);
-                                    const float ai = tabv(p, 1, 0, 0, gy), ci = tabv(p, 1, 0, 2, gy);
-                                    const float vy = wy + ah * (p.phi[1][1][si] + ch * wy);
-                                    const float vx = wx + ai * (p.phi[0][1][si] + ci * wx);
-                                    const float vz = wz + ai * (p.phi[2][1][si] + ci * wz);
-                                    wx = vx;
-                                    wy = vy;
-                                    wz = vz;
-                                }
-                            }
+                        float rxx = wx, ryx = wy, rzx = wz, ryy = wy, rxy = wx, rzy = wz;
+                        if (cpm.sx[k] >= 0) {
+                            const float* t = cxt + 4 * (q % BW);
+                            rxx = wx + t[2] * (dph[k][0] + t[3] * wx);
+                            ryx = wy + t[0] * (dph[k][1] + t[1] * wy);
+                            rzx = wz + t[0] * (dph[k][2] + t[1] * wz);
                         }
-                        Ryy[q] = wy;
-                        Rxy[q] = wx;
-                        Rzy[q] = wz;
+                        if (cpm.sy[k] >= 0) {
+                            const float* t = cyt + 4 * (q / BW);
+                            ryy = wy + t[2] * (dph[k][3] + t[3] * wy);
+                            rxy = wx + t[0] * (dph[k][4] + t[1] * wx);
+                            rzy = wz + t[0] * (dph[k][5] + t[1] * wz);
+                        }
+                        U0[q] = rxx;
+                        U1[q] = ryx;
+                        U2[q] = rzx;
+                        if (f & CP_YB) {
+                            E0[q] = ryy;
+                            E1[q] = rxy;
+                            E2[q] = rzy;
+                        }
                     }
                 }
                 __syncthreads();
-                XD0 = Rxx;
-                XD1 = Ryx;
-                XD2 = Rzx;
-                YD0 = Ryy;
-                YD1 = Rxy;
-                YD2 = Rzy;
+                XD0 = U0;  // R_xx
+                XD1 = U1;  // R_yx
+                XD2 = U2;  // R_zx
+                YD0 = E0;  // R_yy
+                YD1 = E1;  // R_xy
+                YD2 = E2;  // R_zy
             }
             if (ok && own) {
                 // du[i][j] = d_j of the u^i-like field
@@ -981,7 +1076,7 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
 }
 
 template <bool ADJ, bool PML>
-__global__ void __launch_bounds__(NT) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
+__global__ void __launch_bounds__(NT, PML ? 3 : 1) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
                                                   int* err) {
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1;
