@@ -22,7 +22,6 @@ path); value = updates of all ranks / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -154,12 +153,8 @@ def algorithmic_bytes(kind, d, L):
 
 
 def source_sha():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1709_02733_b300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
-    return h.hexdigest()[:16]
+    from paper_1709_02733_b300.profiling import source_sha as sha
+    return sha()
 
 
 def traffic_for(kind):
