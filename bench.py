@@ -141,14 +141,14 @@ def algorithmic_bytes(kind, d, L):
         return f * (11 * N + 3 * N) + 2 * f * 3 * S
     if kind == "fwd_stress":     # read 3 u, 6 sigma, lambda, mu; write 6 sigma; psi^{ij} r+w on slabs
         return f * (11 * N + 6 * N) + 2 * f * 3 * S
-    if kind == "adj_a":          # read 6 sigma, lambda, mu, 3 u, rho, alpha; write 3 u; psi read, phi r+w
-        return f * (13 * N + 3 * N) + f * 3 * S + 2 * f * 3 * S
-    if kind == "adj_b":          # read 3 u, rho, 6 sigma; write 6 sigma; lambda, mu, phi read, psi r+w on slabs
-        return f * (10 * N + 6 * N) + f * 2 * S + f * 3 * S + 2 * f * 3 * S
+    if kind == "adj_a":          # read 6 Q, 3 w, rho, alpha; write 3 w; psi^ read, phi~ r+w on slabs
+        return f * (11 * N + 3 * N) + f * 3 * S + 2 * f * 3 * S
+    if kind == "adj_b":          # read 3 w, 6 Q, lambda, mu; write 6 Q; phi~ read, psi^ r+w on slabs
+        return f * (11 * N + 6 * N) + f * 3 * S + 2 * f * 3 * S
     if kind == "sample":
         return f * (3 * 8 * L + L) + 8 * 8 * L
-    if kind == "inject":
-        return f * (2 * 3 * 8 * L + L) + 8 * 8 * L
+    if kind == "inject":         # 3 normal Q r+w and lambda, mu at the 8 corners of each receiver
+        return f * (2 * 3 * 8 * L + 2 * 8 * L + L) + 8 * 8 * L
     return 0
 
 

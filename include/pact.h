@@ -79,7 +79,8 @@ typedef struct {
 int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out);
 
 /* Copy the medium into the handle: density rho [kg/m^3] > 0, Lame lambda and
- * mu [Pa] (mu >= 0, lambda + 2 mu > 0), absorption alpha [1/s] >= 0, all
+ * mu [Pa] (mu >= 0, lambda + 2 mu > 0, bulk modulus 3 lambda + 2 mu > 0, which
+ * the adjoint's read-out divides by), absorption alpha [1/s] >= 0, all
  * device arrays of N floats at the integer nodes (Sec. 2.1, Eq. (Elastic)).
  * Builds the C-PML profile tables.  Synchronises the stream (it reduces the
  * medium to check it).  Errors: PACT_EINVAL (NULL pointer or a value out of
@@ -124,7 +125,10 @@ int pact_query_bytes(const pact_grid_desc* desc, int L, int nsteps, size_t* byte
 
 /* Diagnostics: copy the current wavefield to HOST memory, 9*N floats in the
  * order u^1, u^2, u^3, sigma^11, sigma^22, sigma^33, sigma^23, sigma^13, sigma^12
- * (Sec. 2.2 vectors u_bar, sigma_bar).  Synchronises the stream. */
+ * (Sec. 2.2 vectors u_bar, sigma_bar) after pact_forward.  After pact_adjoint
+ * the same slots hold the adjoint state in the library's weighted variables
+ * w = dt u~ / rho_bar and Q = C sigma~ (C: the stiffness of the stress update).
+ * Synchronises the stream. */
 int pact_get_wavefield(pact_handle h, float* host_out);
 
 /* ---- serving: many solves advanced together ------------------------------

@@ -80,13 +80,16 @@ struct pact_grid {
     // TMA-staged kernels (nx % 4 == 0) or the direct kernels
     bool tiled = false;
     TmaSet tm{};
+    // the C-PML frame launches overlap the interior launches on this stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // serving state (pact_begin / pact_advance / pact_poll)
     bool sv_active = false;
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
     const float* sv_in = nullptr;
     float* sv_out = nullptr;
-    RegionList sv_inner{}, sv_outer{};
-    int sv_ninner = 0, sv_nouter = 0;
+    RegionList sv_inner{}, sv_zslab{}, sv_outer{};
+    int sv_ninner = 0, sv_nzslab = 0, sv_nouter = 0;
     std::string err;
 };
 
@@ -353,9 +356,10 @@ static int device_status(pact_handle h) {
 static void fwd_step(pact_handle h, const StepParams& p) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
     if (h->tiled) {
-        launch_vel_tiled(false, p, h->tm, err, h->stream);
+        const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join};
+        launch_vel_tiled(false, p, h->tm, err, ss);
         mark(h, PACT_K_FWD_VELOCITY);
-        launch_str_tiled(false, p, h->tm, err, h->stream);
+        launch_str_tiled(false, p, h->tm, err, ss);
         mark(h, PACT_K_FWD_STRESS);
     } else {
         launch_fwd_velocity(p, h->stream);
@@ -368,9 +372,10 @@ static void fwd_step(pact_handle h, const StepParams& p) {
 static void adj_step(pact_handle h, const StepParams& p) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
     if (h->tiled) {
-        launch_vel_tiled(true, p, h->tm, err, h->stream);
+        const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join};
+        launch_vel_tiled(true, p, h->tm, err, ss);
         mark(h, PACT_K_ADJ_A);
-        launch_str_tiled(true, p, h->tm, err, h->stream);
+        launch_str_tiled(true, p, h->tm, err, ss);
         mark(h, PACT_K_ADJ_B);
     } else {
         launch_adj_a(p, h->stream);
@@ -479,6 +484,16 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
         arrays[TM_MU] = h->medium + 4 * h->N;  // the TMA-staged kernels read 1/mu
         arrays[TM_ALPHA] = h->medium + 3 * h->N;
         h->tiled = make_tma_set(&h->tm, arrays, desc->nx, desc->ny, desc->nz) == 0;
+        // PACT_OVERLAP=0 runs the frame and interior launches one after the other
+        const char* oenv = getenv("PACT_OVERLAP");
+        if (h->tiled && !(oenv && std::strcmp(oenv, "0") == 0)) {
+            if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+                h->err = "creating the frame stream and its events failed";
+                return bail(PACT_ECUDA);
+            }
+        }
     }
     *out = h;
     return PACT_OK;
@@ -503,8 +518,9 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     CK(h, cudaStreamSynchronize(s));
     h->medium_set = false;
     if (red[2] != 0) {
-        char buf[160];
-        snprintf(buf, sizeof buf, "medium: %u nodes violate rho > 0, mu >= 0, lambda + 2 mu > 0, alpha >= 0",
+        char buf[192];
+        snprintf(buf, sizeof buf,
+                 "medium: %u nodes violate rho > 0, mu >= 0, lambda + 2 mu > 0, 3 lambda + 2 mu > 0, alpha >= 0",
                  red[2]);
         return fail(h, PACT_EINVAL, buf);
     }
@@ -597,6 +613,9 @@ int pact_destroy(pact_handle h) {
     for (int a = 0; a < 3; ++a) cudaFree(h->slabs[a]);
     free_rec(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     cudaFree(h->stage_a);
     cudaFree(h->stage_b);
     delete h;
@@ -671,7 +690,7 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
         if (nsteps == 0) launch_readout(out, p, h->stream);
     }
-    plan_instance_regions(p, 32, h->sv_inner, h->sv_ninner, h->sv_outer, h->sv_nouter);
+    plan_instance_regions(p, 32, h->sv_inner, h->sv_ninner, h->sv_zslab, h->sv_nzslab, h->sv_outer, h->sv_nouter);
     h->sv_active = nsteps > 0;
     CK(h, cudaGetLastError());
     return PACT_OK;
@@ -684,7 +703,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
     if (!T) T = new (std::nothrow) MultiTable();
     if (!T) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
     int dev = -1, ni = 0;
-    T->pre_inner[0] = T->pre_outer[0] = 0;
+    T->pre_inner[0] = T->pre_zslab[0] = T->pre_outer[0] = 0;
     for (int k = 0; k < n; ++k) {
         pact_handle h = hs[k];
         if (!h) return fail(nullptr, PACT_EINVAL, "pact_advance: NULL handle");
@@ -695,6 +714,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
         e.tm = h->tm;
         e.p = make_params(h);
         e.inner = h->sv_inner;
+        e.zslab = h->sv_zslab;
         e.outer = h->sv_outer;
         e.rec = make_rec(h);
         e.src = h->sv_adj ? h->sv_in : nullptr;
@@ -704,6 +724,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
         e.nsteps = h->sv_nsteps;
         e.L = h->L;
         T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
+        T->pre_zslab[ni + 1] = T->pre_zslab[ni] + h->sv_nzslab;
         T->pre_outer[ni + 1] = T->pre_outer[ni] + h->sv_nouter;
         ++ni;
     }

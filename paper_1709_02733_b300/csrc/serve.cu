@@ -19,7 +19,8 @@
 
 // After one step of every unfinished instance: forward instances sample
 // row m+1 of their traces (Theta), adjoint instances inject row nsteps-(m+1)
-// (Theta^T, owner-computes as in k_inject); then the step counter advances.
+// (Theta^T into the weighted normal stresses Q, owner-computes as in
+// k_inject); then the step counter advances.
 __global__ void k_multi_receivers(MultiTable* T) {
     const int i = blockIdx.x;
     if (i >= T->n_inst) return;
@@ -45,6 +46,7 @@ __global__ void k_multi_receivers(MultiTable* T) {
             float acc = 0.0f;
             for (int e = r.inj_off[c]; e < r.inj_off[c + 1]; ++e) acc += r.inj_w[e] * ph[r.inj_rec[e]];
             const int q = r.inj_point[c];
+            acc *= 3.0f * p.lam[q] + 2.0f * p.mu[q];  // Q = C sigma~ (see step_direct.cu)
             p.s[0][q] -= acc;
             p.s[1][q] -= acc;
             p.s[2][q] -= acc;

@@ -6,15 +6,26 @@
 //   k_fwd_stress   : psi <- B~ psi + E~ u   ; sigma <- sigma + Psi u + Delta psi
 // Adjoint step W'^T = S1^T S2^T S3^T S4^T (Sec. 4, Eq. (backwardstep); Appendix
 // A.3, Eq. (AdjupPML)) in gather form.  With zero padding (D+)^T = -(D-) and
-// (D-)^T = -(D+), so every transposed difference becomes a difference of the
-// complementary kind applied to a material-weighted field:
-//   k_adj_a : finishes the previous step's S2^T / S1^T tails at its own point
-//             (u <- J u, phi <- B (phi + Gamma^T u)), then
-//             u <- u + Psi^T sigma + E~^T (psi + Delta^T sigma)
-//   k_adj_b : sigma <- sigma + Phi^T u + E^T (phi + Gamma^T u)
-//             psi   <- B~ (psi + Delta^T sigma_old)   (own point, old sigma)
-// The J and B factors of S2^T / S1^T are applied one kernel later because
-// k_adj_b still reads u and phi at neighbouring points.
+// (D-)^T = -(D+), so every transposed difference is a difference of the
+// complementary kind.  The adjoint state is kept in weighted variables
+//   w = dt u~ / rho_bar   (velocity nodes),   Q = C sigma~   (stress nodes),
+//   psi^ = psi~ / dt,     phi~ as is,
+// where C is the stiffness of the stress update (lambda, mu at the normal
+// nodes, the harmonic mean of mu at the shear nodes).  In these variables the
+// transposed step has the form of the forward step with negated differences,
+// so no material-weighted field has to be formed at neighbouring points:
+//   k_adj_a : phi~ <- b (phi~ + chi w)      (tail of the previous S2^T / S1^T, own point)
+//             w    <- J w - dt^2/rho_bar D F,   F = Q + a (psi^ + chi Q)   [S4^T, S3^T]
+//   k_adj_b : psi^ <- b (psi^ + chi Q)      (tail of S4^T / S3^T, own point, old Q)
+//             Q    <- Q - C e(E),           E = w + a (phi~ + chi w)      [S2^T, S1^T]
+// with D, e(.) the difference patterns of the forward velocity and stress
+// updates and a, b, chi the C-PML tables (the a-terms vanish off the slabs).
+// The J and b factors are applied one kernel later because the next kernel
+// still reads w, Q and the memory variables at neighbouring points.
+// Source and read-out in these variables: the injection Theta^T p adds
+// -(3 lambda + 2 mu) p to each normal Q (it adds -p to each normal sigma~), and
+// tau^T sigma~ = -tr(sigma~)/3 = -tr(Q) / (3 (3 lambda + 2 mu)), which needs a
+// positive bulk modulus 3 lambda + 2 mu at every node (checked with the medium).
 #include "pact_internal.cuh"
 
 // ---------------------------------------------------------------------------
@@ -163,48 +174,33 @@ __global__ void k_fwd_stress(StepParams p) {
 // adjoint
 // ===========================================================================
 
-// Material-weighted normal-stress field for u^K (integer node q):
-//   dt (lambda tr sigma + 2 mu sigma^KK) + a_K (psi^KK + dt (lambda tr sigma + 2 mu chi_K sigma^KK))
-// i.e. the part of Psi^T sigma + E~^T psi~ that is differenced along K.
+// F for u^K differenced along K (normal node q): Q^KK + a_K (psi^KK + chi_K Q^KK)
 template <int K>
 __device__ __forceinline__ float adj_normal(int x, int y, int z, const StepParams& p) {
     if (!inside(x, y, z, p)) return 0.0f;
     const size_t q = lin3(x, y, z, p.nx, p.ny);
-    const float s0 = __ldg(p.s[0] + q), s1 = __ldg(p.s[1] + q), s2 = __ldg(p.s[2] + q);
-    const float sk = K == 0 ? s0 : (K == 1 ? s1 : s2);
-    const float ltr = __ldg(p.lam + q) * (s0 + s1 + s2);
-    const float mu2 = 2.0f * __ldg(p.mu + q);
-    float v = p.dt * (ltr + mu2 * sk);
+    const float qk = __ldg(p.s[K] + q);
     const int k = coord<K>(x, y, z);
     const int l = slab_local(k, extent<K>(p), p.P);
-    if (l >= 0) {
-        const float a = ptab<K>(p, 0, 0, k), chi = ptab<K>(p, 0, 2, k);
-        const float ps = __ldg(p.psi[K][K] + slab_index(K, x, y, z, l, p));
-        v += a * (ps + p.dt * (ltr + mu2 * chi * sk));
-    }
-    return v;
+    if (l < 0) return qk;
+    const float a = ptab<K>(p, 0, 0, k), chi = ptab<K>(p, 0, 2, k);
+    return qk + a * (__ldg(p.psi[K][K] + slab_index(K, x, y, z, l, p)) + chi * qk);
 }
 
-// Material-weighted shear field for u^K differenced along J (shear node q):
-//   dt mu sigma^KJ + a_J (psi^KJ + dt mu chi_J sigma^KJ)
+// F for u^K differenced along J (shear node q): Q^KJ + a_J (psi^KJ + chi_J Q^KJ)
 template <int K, int J>
 __device__ __forceinline__ float adj_shear(int x, int y, int z, const StepParams& p) {
     if (!inside(x, y, z, p)) return 0.0f;
-    constexpr int V = voigt(K, J);
     const size_t q = lin3(x, y, z, p.nx, p.ny);
-    const float dms = p.dt * mu_shear<V>(x, y, z, p) * __ldg(p.s[V] + q);
-    float v = dms;
+    const float qs = __ldg(p.s[voigt(K, J)] + q);
     const int k = coord<J>(x, y, z);
     const int l = slab_local(k, extent<J>(p), p.P);
-    if (l >= 0) {
-        const float a = ptab<J>(p, 1, 0, k), chi = ptab<J>(p, 1, 2, k);
-        const float ps = __ldg(p.psi[K][J] + slab_index(J, x, y, z, l, p));
-        v += a * (ps + chi * dms);
-    }
-    return v;
+    if (l < 0) return qs;
+    const float a = ptab<J>(p, 1, 0, k), chi = ptab<J>(p, 1, 2, k);
+    return qs + a * (__ldg(p.psi[K][J] + slab_index(J, x, y, z, l, p)) + chi * qs);
 }
 
-// deferred tail of S2^T / S1^T for phi^{KJ}: phi <- b (phi + chi w), w = dt/rho u
+// deferred tail of S2^T / S1^T for phi^{KJ}: phi <- b (phi + chi w)
 template <int K, int J>
 __device__ __forceinline__ void phi_tail(float w, int x, int y, int z, const StepParams& p) {
     const int k = coord<J>(x, y, z);
@@ -219,16 +215,14 @@ __device__ __forceinline__ void phi_tail(float w, int x, int y, int z, const Ste
 template <int K>
 __device__ __forceinline__ void adj_a_update(int x, int y, int z, size_t idx, const StepParams& p) {
     constexpr int J1 = (K + 1) % 3, J2 = (K + 2) % 3;
-    const float ut = p.u[K][idx];
-    const float w = p.dt / med_avg<K>(p.rho, x, y, z, p) * ut;
+    const float w = p.u[K][idx];
     phi_tail<K, 0>(w, x, y, z, p);
     phi_tail<K, 1>(w, x, y, z, p);
     phi_tail<K, 2>(w, x, y, z, p);
-    const float uj = (1.0f - p.dt * med_avg<K>(p.alpha, x, y, z, p)) * ut;
     const float g = DplusF<K>([&](int a, int b, int c) { return adj_normal<K>(a, b, c, p); }, x, y, z, p) +
                     DminusF<J1>([&](int a, int b, int c) { return adj_shear<K, J1>(a, b, c, p); }, x, y, z, p) +
                     DminusF<J2>([&](int a, int b, int c) { return adj_shear<K, J2>(a, b, c, p); }, x, y, z, p);
-    p.u[K][idx] = uj - g;
+    p.u[K][idx] = (1.0f - p.dt * med_avg<K>(p.alpha, x, y, z, p)) * w - p.dt * p.dt / med_avg<K>(p.rho, x, y, z, p) * g;
 }
 
 __global__ void k_adj_a(StepParams p) {
@@ -242,62 +236,41 @@ __global__ void k_adj_a(StepParams p) {
     adj_a_update<2>(x, y, z, idx, p);
 }
 
-// Velocity-weighted field at the u^I node differenced along J:
-//   dt/rho_I u^I + a_J (phi^IJ + dt/rho_I chi_J u^I)
+// E for the u^I node differenced along J: w^I + a_J (phi^IJ + chi_J w^I)
 template <int I, int J>
 __device__ __forceinline__ float adj_vel(int x, int y, int z, const StepParams& p) {
     if (!inside(x, y, z, p)) return 0.0f;
     const size_t q = lin3(x, y, z, p.nx, p.ny);
-    const float w = p.dt / med_avg<I>(p.rho, x, y, z, p) * __ldg(p.u[I] + q);
-    float v = w;
+    const float w = __ldg(p.u[I] + q);
     const int k = coord<J>(x, y, z);
     const int l = slab_local(k, extent<J>(p), p.P);
-    if (l >= 0) {
-        constexpr int h = (I == J);
-        const float a = ptab<J>(p, h, 0, k), chi = ptab<J>(p, h, 2, k);
-        const float ph = __ldg(p.phi[I][J] + slab_index(J, x, y, z, l, p));
-        v += a * (ph + chi * w);
-    }
-    return v;
+    if (l < 0) return w;
+    constexpr int h = (I == J);
+    const float a = ptab<J>(p, h, 0, k), chi = ptab<J>(p, h, 2, k);
+    return w + a * (__ldg(p.phi[I][J] + slab_index(J, x, y, z, l, p)) + chi * w);
 }
 
-// psi^{IJ} <- b (psi^{IJ} + c) on the axis-J slab at the own point
+// deferred tail of S4^T / S3^T for psi^{IJ}: psi^ <- b (psi^ + chi Q)
 template <int I, int J>
-__device__ __forceinline__ void psi_tail(float dmc, int x, int y, int z, const StepParams& p) {
+__device__ __forceinline__ void psi_tail(float qv, int x, int y, int z, const StepParams& p) {
     const int k = coord<J>(x, y, z);
     const int l = slab_local(k, extent<J>(p), p.P);
     if (l < 0) return;
     constexpr int h = (I != J);
     const float b = ptab<J>(p, h, 1, k), chi = ptab<J>(p, h, 2, k);
     float* ps = p.psi[I][J] + slab_index(J, x, y, z, l, p);
-    *ps = b * (*ps + chi * dmc);
-}
-
-// normal psi tail: psi^KK <- b (psi^KK + dt (lambda tr + 2 mu chi sigma^KK))
-template <int K>
-__device__ __forceinline__ void psi_tail_normal(float ltr, float mu2, float sk, int x, int y, int z,
-                                                const StepParams& p) {
-    const int k = coord<K>(x, y, z);
-    const int l = slab_local(k, extent<K>(p), p.P);
-    if (l < 0) return;
-    const float b = ptab<K>(p, 0, 1, k), chi = ptab<K>(p, 0, 2, k);
-    float* ps = p.psi[K][K] + slab_index(K, x, y, z, l, p);
-    *ps = b * (*ps + p.dt * (ltr + mu2 * chi * sk));
+    *ps = b * (*ps + chi * qv);
 }
 
 template <int V>
 __device__ __forceinline__ void adj_b_shear(int x, int y, int z, size_t idx, const StepParams& p) {
     constexpr int I = ShearAxes<V>::I, J = ShearAxes<V>::J;
-    const float so = p.s[V][idx];
-    if (slab_local(coord<I>(x, y, z), extent<I>(p), p.P) >= 0 ||
-        slab_local(coord<J>(x, y, z), extent<J>(p), p.P) >= 0) {
-        const float dms = p.dt * mu_shear<V>(x, y, z, p) * so;
-        psi_tail<I, J>(dms, x, y, z, p);
-        psi_tail<J, I>(dms, x, y, z, p);
-    }
+    const float qo = p.s[V][idx];
+    psi_tail<I, J>(qo, x, y, z, p);
+    psi_tail<J, I>(qo, x, y, z, p);
     const float g = DplusF<J>([&](int a, int b, int c) { return adj_vel<I, J>(a, b, c, p); }, x, y, z, p) +
                     DplusF<I>([&](int a, int b, int c) { return adj_vel<J, I>(a, b, c, p); }, x, y, z, p);
-    p.s[V][idx] = so - g;
+    p.s[V][idx] = qo - mu_shear<V>(x, y, z, p) * g;
 }
 
 __global__ void k_adj_b(StepParams p) {
@@ -306,17 +279,17 @@ __global__ void k_adj_b(StepParams p) {
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const size_t idx = lin3(x, y, z, p.nx, p.ny);
-    const float s0 = p.s[0][idx], s1 = p.s[1][idx], s2 = p.s[2][idx];
-    if (slab_local(x, p.nx, p.P) >= 0 || slab_local(y, p.ny, p.P) >= 0 || slab_local(z, p.nz, p.P) >= 0) {
-        const float ltr = __ldg(p.lam + idx) * (s0 + s1 + s2);
-        const float mu2 = 2.0f * __ldg(p.mu + idx);
-        psi_tail_normal<0>(ltr, mu2, s0, x, y, z, p);
-        psi_tail_normal<1>(ltr, mu2, s1, x, y, z, p);
-        psi_tail_normal<2>(ltr, mu2, s2, x, y, z, p);
-    }
-    p.s[0][idx] = s0 - DminusF<0>([&](int a, int b, int c) { return adj_vel<0, 0>(a, b, c, p); }, x, y, z, p);
-    p.s[1][idx] = s1 - DminusF<1>([&](int a, int b, int c) { return adj_vel<1, 1>(a, b, c, p); }, x, y, z, p);
-    p.s[2][idx] = s2 - DminusF<2>([&](int a, int b, int c) { return adj_vel<2, 2>(a, b, c, p); }, x, y, z, p);
+    const float q0 = p.s[0][idx], q1 = p.s[1][idx], q2 = p.s[2][idx];
+    psi_tail<0, 0>(q0, x, y, z, p);
+    psi_tail<1, 1>(q1, x, y, z, p);
+    psi_tail<2, 2>(q2, x, y, z, p);
+    const float e0 = DminusF<0>([&](int a, int b, int c) { return adj_vel<0, 0>(a, b, c, p); }, x, y, z, p);
+    const float e1 = DminusF<1>([&](int a, int b, int c) { return adj_vel<1, 1>(a, b, c, p); }, x, y, z, p);
+    const float e2 = DminusF<2>([&](int a, int b, int c) { return adj_vel<2, 2>(a, b, c, p); }, x, y, z, p);
+    const float lt = __ldg(p.lam + idx) * (e0 + e1 + e2), mu2 = 2.0f * __ldg(p.mu + idx);
+    p.s[0][idx] = q0 - (lt + mu2 * e0);
+    p.s[1][idx] = q1 - (lt + mu2 * e1);
+    p.s[2][idx] = q2 - (lt + mu2 * e2);
     adj_b_shear<3>(x, y, z, idx, p);
     adj_b_shear<4>(x, y, z, idx, p);
     adj_b_shear<5>(x, y, z, idx, p);
@@ -336,11 +309,13 @@ __global__ void k_source(const float* __restrict__ p0, float* s0, float* s1, flo
     }
 }
 
-// tau^T: image = -(sigma^11 + sigma^22 + sigma^33) / 3
+// tau^T: image = -(sigma~11 + sigma~22 + sigma~33) / 3 = -tr(Q) / (3 (3 lambda + 2 mu))
 __global__ void k_readout(const float* __restrict__ s0, const float* __restrict__ s1, const float* __restrict__ s2,
-                          float* img, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        img[i] = -(__ldg(s0 + i) + __ldg(s1 + i) + __ldg(s2 + i)) * (1.0f / 3.0f);
+                          const float* __restrict__ lam, const float* __restrict__ mu, float* img, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float k3 = 3.0f * (3.0f * __ldg(lam + i) + 2.0f * __ldg(mu + i));
+        img[i] = -__fdividef(__ldg(s0 + i) + __ldg(s1 + i) + __ldg(s2 + i), k3);
+    }
 }
 
 // Theta (Eq. (interpgrid)): out[l] = -sum_c w_c (s11 + s22 + s33)(c)
@@ -357,15 +332,18 @@ __global__ void k_sample(const float* __restrict__ s0, const float* __restrict__
     out[l] = -acc;
 }
 
-// Theta^T: sigma^ii(point) -= sum over contributions w * p_hat[l]; one thread
-// per distinct corner point, contributions in a fixed order (deterministic)
-__global__ void k_inject(float* s0, float* s1, float* s2, RecTable r, const float* __restrict__ ph) {
+// Theta^T: sigma~^ii(point) -= sum over contributions w * p_hat[l], i.e.
+// Q^ii(point) -= (3 lambda + 2 mu) * that sum; one thread per distinct corner
+// point, contributions in a fixed order (deterministic)
+__global__ void k_inject(float* s0, float* s1, float* s2, const float* __restrict__ lam, const float* __restrict__ mu,
+                         RecTable r, const float* __restrict__ ph) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= r.ncorner) return;
     float acc = 0.0f;
     for (int e = __ldg(r.inj_off + c); e < __ldg(r.inj_off + c + 1); ++e)
         acc += __ldg(r.inj_w + e) * __ldg(ph + __ldg(r.inj_rec + e));
     const int q = __ldg(r.inj_point + c);
+    acc *= 3.0f * __ldg(lam + q) + 2.0f * __ldg(mu + q);
     s0[q] -= acc;
     s1[q] -= acc;
     s2[q] -= acc;
@@ -389,8 +367,8 @@ __global__ void k_medium_check(const float* __restrict__ rho, const float* __res
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float r = rho[i], l = lam[i], m = mu[i], a = alpha[i];
         const float m2 = l + 2.0f * m;
-        const bool ok = (r > 0.0f) && (m >= 0.0f) && (m2 > 0.0f) && (a >= 0.0f) && isfinite(r) && isfinite(l) &&
-                        isfinite(m) && isfinite(a);
+        const bool ok = (r > 0.0f) && (m >= 0.0f) && (m2 > 0.0f) && (3.0f * l + 2.0f * m > 0.0f) && (a >= 0.0f) &&
+                        isfinite(r) && isfinite(l) && isfinite(m) && isfinite(a);
         if (!ok) {
             ++bad;
             continue;
@@ -449,7 +427,7 @@ void launch_source(const float* p0, const StepParams& p, cudaStream_t st) {
 
 void launch_readout(float* img, const StepParams& p, cudaStream_t st) {
     const size_t n = (size_t)p.nx * p.ny * p.nz;
-    k_readout<<<ew_blocks(n), 256, 0, st>>>(p.s[0], p.s[1], p.s[2], img, n);
+    k_readout<<<ew_blocks(n), 256, 0, st>>>(p.s[0], p.s[1], p.s[2], p.lam, p.mu, img, n);
 }
 
 void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStream_t st) {
@@ -457,7 +435,7 @@ void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStrea
 }
 
 void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st) {
-    if (r.ncorner > 0) k_inject<<<(r.ncorner + 127) / 128, 128, 0, st>>>(p.s[0], p.s[1], p.s[2], r, ph);
+    if (r.ncorner > 0) k_inject<<<(r.ncorner + 127) / 128, 128, 0, st>>>(p.s[0], p.s[1], p.s[2], p.lam, p.mu, r, ph);
 }
 
 void launch_inv_mu(const float* mu, float* inv, size_t n, cudaStream_t st) {

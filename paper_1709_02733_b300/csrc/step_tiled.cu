@@ -9,23 +9,27 @@
 // x and y differences read shared memory; z differences read per-thread
 // register queues holding the thread's own column over four planes.
 //
-// The two kernel families share their stencils:
+// The two kernel families share their stencils, forward and adjoint alike:
 //   velocity family (3 outputs from 6 stress-like fields):
-//     forward  u  <- J u + dt/rho (D+x s11 + D-y s12 + D-z s13, ...)     (Eq. (it) + C-PML)
-//     adjoint  u  <- J u - (D+x Q_x + D-y S_xy + D-z S_xz, ...)           (Eq. (backwardstep))
+//     forward  u <- J u + dt/rho (D+x s11 + D-y s12 + D-z s13, ...)        (Eq. (it) + C-PML)
+//     adjoint  w <- J w - dt^2/rho (D+x F11 + D-y F12 + D-z F13, ...)      (Eq. (backwardstep))
 //   stress family (6 outputs from 3 velocity-like fields):
-//     forward  s  <- s + dt (lambda tr(e) I + 2 mu e)                     (Eq. (it) + C-PML)
-//     adjoint  s  <- s - (D-x R_xx, D+y R_xy + D+x R_yx, ...)             (Eq. (backwardstep))
-// where the adjoint fields Q, S (stress side) and R (velocity side) are the
-// material-weighted fields of the gather form of the transposed operators
-// (see step_direct.cu), computed once per point into shared memory.  The
-// deferred J and B tails of the adjoint are as in step_direct.cu.
+//     forward  s <- s + dt C e(u)                                          (Eq. (it) + C-PML)
+//     adjoint  Q <- Q - C e(E)                                             (Eq. (backwardstep))
+// The adjoint runs on the weighted variables w = dt u~/rho and Q = C s~
+// (step_direct.cu derives them); F and E are Q and w plus the C-PML memory
+// terms, which are nonzero only on the slabs, so off the x / y layers the
+// adjoint reads its boxes exactly as the forward does.  The deferred J and
+// B tails of the adjoint are as in step_direct.cu.
 //
-// Every half-step is two launches over disjoint regions of (tile, plane)
-// work: blocks whose tile halo and planes stay off the C-PML slabs run an
-// instantiation without any C-PML code; the rest run the C-PML instantiation,
-// which keeps the per-thread x / y layer coefficients in registers and loads
-// the own-point memory variables one plane ahead with the wavefield values.
+// Every half-step is three launches over disjoint (tile, plane) regions: the
+// frame of tiles whose halo touches an x or y C-PML slab (all planes; full
+// C-PML code, per-thread x / y layer coefficients in registers), the z-slab
+// planes of the other tiles (z-layer code only) and the rest (no layer code).
+// Layer blocks load the own-point memory variables one plane ahead with the
+// wavefield values.  The launches write disjoint points and read only the
+// other family's fields, so the frame and z-slab launches may run on a second
+// stream, concurrently with the interior one.
 //
 // Requirements: nx % 4 == 0 (TMA global strides are multiples of 16 bytes).
 #include <algorithm>
@@ -46,38 +50,36 @@ constexpr int BOXS = 544;       // box stride in floats (2176 B, 128-B aligned)
 constexpr int OX = 4, OY = 2;   // own point offset inside the box
 constexpr int D = 4;            // stage ring depth (planes)
 
-template <bool ADJ, bool PML> struct VelCfg {
-    // stage boxes 0..5: sigma (Voigt); then
-    //   forward: 6 rho, 7 alpha
-    //   adjoint: 6 lambda, 7 1/mu (rho and alpha are read through the cache)
-    // The adjoint computes its material-weighted fields in place in the stage
-    // of the output plane; C-PML blocks keep the x-differenced sigma12 field,
-    // which differs from the y-differenced one inside the layers, in one extra box.
+// C-PML code compiled into a kernel instantiation:
+//   PM_NONE  no layer (tiles and planes whose reach stays off every slab, or P = 0)
+//   PM_FULL  x, y and z layers (tiles whose halo touches an x or y slab)
+//   PM_Z     z layer only (tiles whose halo stays off the x and y slabs, all planes)
+constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2;
+
+template <bool ADJ, int PM> struct VelCfg {
+    static constexpr bool PML = PM != PM_NONE, PXY = PM == PM_FULL;
+    // stage boxes 0..5: sigma (forward) or Q (adjoint), Voigt order; 6 rho,
+    // 7 alpha.  Full C-PML adjoint blocks form the layer-augmented fields F in
+    // place and keep the x-differenced F^21, which differs from the
+    // y-differenced F^12 inside the layers, in one extra box.
     static constexpr int NB = 8;
-    static constexpr int BRHO = ADJ ? -1 : 6;
-    static constexpr int BALPHA = ADJ ? -1 : 7;
-    static constexpr int BLAM = ADJ ? 6 : -1;
-    static constexpr int BMU = ADJ ? 7 : -1;
-    static constexpr int NDER = (ADJ && PML) ? 1 : 0;
+    static constexpr int BRHO = 6, BALPHA = 7;
+    static constexpr int NDER = (ADJ && PXY) ? 1 : 0;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
-    __host__ __device__ static constexpr int tm(int b) {
-        return b < 6 ? TM_S0 + b
-                     : (b == BRHO ? TM_RHO : (b == BALPHA ? TM_ALPHA : (b == BLAM ? TM_LAM : TM_MU)));
-    }
+    __host__ __device__ static constexpr int tm(int b) { return b < 6 ? TM_S0 + b : (b == BRHO ? TM_RHO : TM_ALPHA); }
 };
 
-template <bool ADJ, bool PML> struct StrCfg {
-    // stage boxes 0..2: u; then forward: 3 lambda, 4 1/mu; adjoint: 3 rho
-    // [C-PML adjoint: 4 lambda, 5 1/mu, for the psi tails].  The adjoint forms
-    // w = dt u / rho in place; C-PML blocks keep the y-differenced fields, which
-    // differ from the x-differenced ones inside the layers, in three extra boxes.
-    static constexpr int NB = ADJ ? (PML ? 6 : 4) : 5;
-    static constexpr int NDER = (ADJ && PML) ? 3 : 0;
-    static constexpr int BLAM = ADJ ? 4 : 3, BMU = ADJ ? 5 : 4;
+template <bool ADJ, int PM> struct StrCfg {
+    static constexpr bool PML = PM != PM_NONE, PXY = PM == PM_FULL;
+    // stage boxes 0..2: u (forward) or w (adjoint); 3 lambda, 4 1/mu.  Full
+    // C-PML adjoint blocks form the layer-augmented fields E in place (the
+    // x-differenced ones) and keep the y-differenced ones, which differ inside
+    // the layers, in three extra boxes.
+    static constexpr int NB = 5;
+    static constexpr int NDER = (ADJ && PXY) ? 3 : 0;
+    static constexpr int BLAM = 3, BMU = 4;
     static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
-    __host__ __device__ static constexpr int tm(int b) {
-        return b < 3 ? TM_U0 + b : (ADJ ? (b == 3 ? TM_RHO : (b == 4 ? TM_LAM : TM_MU)) : (b == 3 ? TM_LAM : TM_MU));
-    }
+    __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : (b == 3 ? TM_LAM : TM_MU); }
 };
 
 __device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1) {
@@ -287,8 +289,11 @@ __device__ __forceinline__ unsigned own_slab(int axis, const PmlXY& q, int lz, i
     return ((unsigned)lz * p.ny + y) * p.nx + x;
 }
 
+// own point on the layer of axis j?  Without x / y layer code (PXY false)
+// only the z layer exists, which the compiler sees for an unrolled j.
+template <bool PXY>
 __device__ __forceinline__ bool in_axis(int j, const PmlXY& q, int lz) {
-    return j == 0 ? q.lx >= 0 : (j == 1 ? q.ly >= 0 : lz >= 0);
+    return j == 2 ? lz >= 0 : (PXY && (j == 0 ? q.lx >= 0 : q.ly >= 0));
 }
 
 __device__ __forceinline__ float coef(int j, int hh, int w, const PmlXY& q, const PmlZ& qz) {
@@ -299,10 +304,15 @@ __device__ __forceinline__ float coef(int j, int hh, int w, const PmlXY& q, cons
 // velocity family
 // ===========================================================================
 // One (tile, z chunk) work item; false if a bounded wait timed out.
-template <bool ADJ, bool PML>
+//   forward: u <- J u + dt/rho (D sigma + chi phi),  phi <- b phi + a D sigma
+//   adjoint: phi~ <- b (phi~ + chi w)  (the deferred tail of the previous
+//            stress-family half, own point, old w), then
+//            w <- J w - dt^2/rho D F,  F = Q + a (psi^ + chi Q) on the slabs
+template <bool ADJ, int PM>
 __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y, int zc0,
                                          int zc1, int* err, float* sm) {
-    using Cfg = VelCfg<ADJ, PML>;
+    using Cfg = VelCfg<ADJ, PM>;
+    constexpr bool PML = Cfg::PML, PXY = Cfg::PXY;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -316,7 +326,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     const int P = p.P;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
     PmlXY px{};
-    if constexpr (PML) pml_xy_init(px, p, x, y, own);
+    if constexpr (PXY) pml_xy_init(px, p, x, y, own);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
@@ -339,9 +349,9 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     const int yc1 = (y + 1 < p.ny) ? BW : 0;  // clamped +y neighbour offset
     CrossPos cross{};
     CrossPml cpm{};
-    __shared__ float cxt[(ADJ && PML) ? 4 * BW : 1], cyt[(ADJ && PML) ? 4 * BH : 1];
-    if constexpr (ADJ) cross_init(cross, tid, x0, y0, p.nx, p.ny);
-    if constexpr (ADJ && PML) {
+    __shared__ float cxt[(ADJ && PXY) ? 4 * BW : 1], cyt[(ADJ && PXY) ? 4 * BH : 1];
+    if constexpr (ADJ && PXY) {
+        cross_init(cross, tid, x0, y0, p.nx, p.ny);
         __syncthreads();  // a persistent block may still read the tables of its previous item
         cross_pml_init(cpm, cxt, cyt, cross, tid, x0, y0, p);
         __syncthreads();
@@ -350,33 +360,17 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     // own-point values of the next output plane, loaded one visit ahead
     float nu[3] = {0.f, 0.f, 0.f};
     float nph[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float na[4] = {0.f, 0.f, 0.f, 0.f};  // adjoint: alpha at p, +x, +y, +z (clamped)
-    float nr[4] = {0.f, 0.f, 0.f, 0.f};  // C-PML adjoint: rho at the same points
-    const unsigned dx1 = (x + 1 < p.nx) ? 1u : 0u, dy1 = (y + 1 < p.ny) ? (unsigned)p.nx : 0u;
     auto prefetch = [&](int zn) {
         if (!own || zn < zc0 || zn >= zc1) return;
         const unsigned g = (unsigned)zn * nxy + gxy;
         nu[0] = p.u[0][g];
         nu[1] = p.u[1][g];
         nu[2] = p.u[2][g];
-        if constexpr (Cfg::BALPHA < 0) {
-            const unsigned dz1 = (zn + 1 < p.nz) ? nxy : 0u;
-            na[0] = __ldg(p.alpha + g);
-            na[1] = __ldg(p.alpha + g + dx1);
-            na[2] = __ldg(p.alpha + g + dy1);
-            na[3] = __ldg(p.alpha + g + dz1);
-            if constexpr (PML) {
-                nr[0] = __ldg(p.rho + g);
-                nr[1] = __ldg(p.rho + g + dx1);
-                nr[2] = __ldg(p.rho + g + dy1);
-                nr[3] = __ldg(p.rho + g + dz1);
-            }
-        }
         if constexpr (PML) {
             const int lz = slab_local(zn, p.nz, P);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (in_axis(j, px, lz)) {
+                if (in_axis<PXY>(j, px, lz)) {
                     const unsigned si = own_slab(j, px, lz, x, y, zn, p);
 #pragma unroll
                     for (int i = 0; i < 3; ++i) nph[i][j] = p.phi[i][j][si];
@@ -409,9 +403,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     for (int pl = pfirst; pl <= plast; ++pl) {
         const int z = pl - 2;
         const bool out = z >= zc0;
-        float cu[3] = {nu[0], nu[1], nu[2]};
-        const float ca[4] = {na[0], na[1], na[2], na[3]};
-        const float cr[4] = {nr[0], nr[1], nr[2], nr[3]};
+        const float cu[3] = {nu[0], nu[1], nu[2]};
         float cph[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -420,9 +412,9 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const float chp[3] = {nhp[0], nhp[1], nhp[2]};
         prefetch(z + 1);
         prefetch_heads(pl + 1);
-        // C-PML adjoint: memory variables at the cross positions of plane z
+        // full C-PML adjoint: memory variables psi^ at the cross positions of plane z
         float dps[2][6];
-        if constexpr (ADJ && PML) {
+        if constexpr (ADJ && PXY) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
 #pragma unroll
@@ -446,235 +438,115 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
         const float* sp = ring.stage(pl);
         const float* spm = (pl - 1 >= pfirst) ? ring.stage(pl - 1) : nullptr;
-        // ---- queue heads: integer->half field at plane pl, half->integer at pl-1
+        // ---- queue heads: integer->half field at plane pl, half->integer at
+        //      pl-1 (zero outside the grid: the boxes are zero-filled there)
         if (ok) {
-            if constexpr (!ADJ) {
-                push(q33, sp[2 * BOXS + o]);
-                push(q13, spm ? spm[4 * BOXS + o] : 0.f);
-                push(q23, spm ? spm[3 * BOXS + o] : 0.f);
-            } else {
-                float h33 = 0.f, h13 = 0.f, h23 = 0.f;
-                if (own && pl >= 0 && pl < p.nz) {
-                    const float s11 = sp[o], s22 = sp[BOXS + o], s33 = sp[2 * BOXS + o];
-                    const float lam = sp[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(sp[Cfg::BMU * BOXS + o]);
-                    const float ltr = lam * (s11 + s22 + s33);
-                    h33 = dt * (ltr + mu2 * s33);
-                    if constexpr (PML) {
-                        const int l = slab_local(pl, p.nz, P);
-                        if (l >= 0) {
-                            const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
-                            h33 += a * (chp[0] + dt * (ltr + mu2 * chi * s33));
-                        }
-                    }
+            float h33 = sp[2 * BOXS + o];
+            float h13 = spm ? spm[4 * BOXS + o] : 0.f;
+            float h23 = spm ? spm[3 * BOXS + o] : 0.f;
+            if constexpr (ADJ && PML) {
+                // z-layer terms of F33 (integer lattice, plane pl) and of F13,
+                // F23 (half lattice, plane pl-1)
+                if (own && pl >= 0 && pl < p.nz && slab_local(pl, p.nz, P) >= 0) {
+                    const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
+                    h33 += a * (chp[0] + chi * h33);
                 }
                 const int zm = pl - 1;
-                if (own && spm && zm >= 0 && zm < p.nz) {
-                    const float* mz = spm + Cfg::BMU * BOXS;                    // 1/mu at plane pl-1
-                    const float* mz1 = (pl < p.nz) ? sp + Cfg::BMU * BOXS : mz;  // 1/mu at plane pl (clamped)
-                    const float m13 = harm_inv(mz[o], mz[o + xc1], mz1[o], mz1[o + xc1]);
-                    const float m23 = harm_inv(mz[o], mz[o + yc1], mz1[o], mz1[o + yc1]);
-                    h13 = dt * m13 * spm[4 * BOXS + o];
-                    h23 = dt * m23 * spm[3 * BOXS + o];
-                    if constexpr (PML) {
-                        const int l = slab_local(zm, p.nz, P);
-                        if (l >= 0) {
-                            const float a = tabv(p, 2, 1, 0, zm), chi = tabv(p, 2, 1, 2, zm);
-                            h13 += a * (chp[1] + chi * h13);
-                            h23 += a * (chp[2] + chi * h23);
-                        }
-                    }
+                if (own && spm && zm >= 0 && zm < p.nz && slab_local(zm, p.nz, P) >= 0) {
+                    const float a = tabv(p, 2, 1, 0, zm), chi = tabv(p, 2, 1, 2, zm);
+                    h13 += a * (chp[1] + chi * h13);
+                    h23 += a * (chp[2] + chi * h23);
                 }
-                push(q33, h33);
-                push(q13, h13);
-                push(q23, h23);
             }
+            push(q33, h33);
+            push(q13, h13);
+            push(q23, h23);
         }
 
         if (out) {
             float* szw = ring.stage(z);
             const float* sz = szw;
             const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
-            const float *XD0, *XD1, *XD2, *YD0, *YD1, *YD2;
-            if constexpr (!ADJ) {
-                XD0 = sz;             // s11
-                XD1 = sz + 5 * BOXS;  // s12
-                XD2 = sz + 4 * BOXS;  // s13
-                YD0 = sz + 1 * BOXS;  // s22
-                YD1 = sz + 5 * BOXS;  // s12
-                YD2 = sz + 3 * BOXS;  // s23
-            } else if constexpr (!PML) {
-                // Material-weighted stress fields of plane z, in place over the
-                // cross-shaped region the differences read: the x band (rows
-                // OY..OY+TY-1, columns OX-2..OX+TX+1) and four y rows (OY-2, OY-1,
-                // OY+TY, OY+TY+1; columns OX..OX+TX-1).  Off the layers the shear
-                // field is the same for both difference directions.
-                //   s11 <- Q_x, s22 <- Q_y, s12 <- dt mu12 s12, s13 <- dt mu13 s13,
-                //   s23 <- dt mu23 s23; zero outside the grid.
-                const float* lm = sz + Cfg::BLAM * BOXS;
-                const float* i0 = sz + Cfg::BMU * BOXS;
-                const float* i1 = sz1 + Cfg::BMU * BOXS;
-                if (ok) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const unsigned char f = cross.f[k];
-                        if (!(f & CP_EXISTS)) continue;
-                        const int q = cross.q[k];
-                        float vqx = 0.f, vqy = 0.f, v12 = 0.f, v13 = 0.f, v23 = 0.f;
-                        if (f & CP_IN) {
-                            const int qx1 = q + cross.dx[k], qy1 = q + cross.dy[k];
-                            const float a11 = sz[q], a22 = sz[BOXS + q], a33 = sz[2 * BOXS + q];
-                            const float r0 = i0[q];
-                            const float ltr = dt * lm[q] * (a11 + a22 + a33);
-                            const float mu2 = 2.0f * dt * mu_of(r0);
-                            v12 = dt * harm_inv(r0, i0[qx1], i0[qy1], i0[qy1 + cross.dx[k]]) * sz[5 * BOXS + q];
-                            if (f & CP_XB) {
-                                vqx = ltr + mu2 * a11;
-                                v13 = dt * harm_inv(r0, i0[qx1], i1[q], i1[qx1]) * sz[4 * BOXS + q];
-                            }
-                            if (f & CP_YB) {
-                                vqy = ltr + mu2 * a22;
-                                v23 = dt * harm_inv(r0, i0[qy1], i1[q], i1[qy1]) * sz[3 * BOXS + q];
-                            }
-                        }
-                        szw[5 * BOXS + q] = v12;
-                        if (f & CP_XB) {
-                            szw[q] = vqx;
-                            szw[4 * BOXS + q] = v13;
-                        }
-                        if (f & CP_YB) {
-                            szw[BOXS + q] = vqy;
-                            szw[3 * BOXS + q] = v23;
-                        }
-                    }
-                }
-                __syncthreads();
-                XD0 = sz;             // Q_x
-                XD1 = sz + 5 * BOXS;  // S_12
-                XD2 = sz + 4 * BOXS;  // S_13
-                YD0 = sz + BOXS;      // Q_y
-                YD1 = sz + 5 * BOXS;  // S_12
-                YD2 = sz + 3 * BOXS;  // S_23
-            } else {
-                // C-PML blocks: as in the interior, plus the memory-variable
-                // terms of the x and y layers (adjoint of Delta and E~): Q_x, S_zx
-                // and the x-differenced S_yx take the x-layer terms, Q_y, S_zy and
-                // the y-differenced S_xy the y-layer terms; S_yx goes to box E.
+            // x-differenced fields (for u^x, u^y, u^z) and y-differenced ones
+            const float* XD0 = sz;             // s11 / F11
+            const float* XD1 = sz + 5 * BOXS;  // s12 / F21
+            const float* XD2 = sz + 4 * BOXS;  // s13 / F31
+            const float* YD0 = sz + 1 * BOXS;  // s22 / F22
+            const float* YD1 = sz + 5 * BOXS;  // s12 / F12
+            const float* YD2 = sz + 3 * BOXS;  // s23 / F32
+            if constexpr (ADJ && PXY) {
+                // F = Q + a (psi^ + chi Q) at the x-band (x layer) and y-row
+                // (y layer) positions, in place; F21 goes to the extra box.
                 float* E = der;
-                const float* lm = sz + Cfg::BLAM * BOXS;
-                const float* i0 = sz + Cfg::BMU * BOXS;
-                const float* i1 = sz1 + Cfg::BMU * BOXS;
                 if (ok) {
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const unsigned char f = cross.f[k];
                         if (!(f & CP_EXISTS)) continue;
                         const int q = cross.q[k];
-                        float vqx = 0.f, vqy = 0.f, v12 = 0.f, e12 = 0.f, v13 = 0.f, v23 = 0.f;
-                        if (f & CP_IN) {
-                            const int qx1 = q + cross.dx[k], qy1 = q + cross.dy[k];
-                            const float a11 = sz[q], a22 = sz[BOXS + q], a33 = sz[2 * BOXS + q];
-                            const float r0 = i0[q];
-                            const float ltr = dt * lm[q] * (a11 + a22 + a33);
-                            const float mu2 = 2.0f * dt * mu_of(r0);
-                            const float b12 = dt * harm_inv(r0, i0[qx1], i0[qy1], i0[qy1 + cross.dx[k]]) * sz[5 * BOXS + q];
-                            v12 = e12 = b12;
-                            if (f & CP_XB) {
-                                vqx = ltr + mu2 * a11;
-                                v13 = dt * harm_inv(r0, i0[qx1], i1[q], i1[qx1]) * sz[4 * BOXS + q];
-                                if (cpm.sx[k] >= 0) {
-                                    const float* t = cxt + 4 * (q % BW);
-                                    vqx += t[0] * (dps[k][0] + ltr + mu2 * t[1] * a11);
-                                    e12 = b12 + t[2] * (dps[k][1] + t[3] * b12);
-                                    v13 += t[2] * (dps[k][2] + t[3] * v13);
-                                }
-                            }
-                            if (f & CP_YB) {
-                                vqy = ltr + mu2 * a22;
-                                v23 = dt * harm_inv(r0, i0[qy1], i1[q], i1[qy1]) * sz[3 * BOXS + q];
-                                if (cpm.sy[k] >= 0) {
-                                    const float* t = cyt + 4 * (q / BW);
-                                    vqy += t[0] * (dps[k][3] + ltr + mu2 * t[1] * a22);
-                                    v12 = b12 + t[2] * (dps[k][4] + t[3] * b12);
-                                    v23 += t[2] * (dps[k][5] + t[3] * v23);
-                                }
-                            }
+                        const float q11 = sz[q], q22 = sz[BOXS + q], q23 = sz[3 * BOXS + q];
+                        const float q13 = sz[4 * BOXS + q], q12 = sz[5 * BOXS + q];
+                        float f11 = q11, f21 = q12, f31 = q13, f22 = q22, f12 = q12, f32 = q23;
+                        if (cpm.sx[k] >= 0) {
+                            const float* t = cxt + 4 * (q % BW);
+                            f11 += t[0] * (dps[k][0] + t[1] * q11);
+                            f21 += t[2] * (dps[k][1] + t[3] * q12);
+                            f31 += t[2] * (dps[k][2] + t[3] * q13);
                         }
-                        szw[5 * BOXS + q] = v12;
-                        E[q] = e12;
+                        if (cpm.sy[k] >= 0) {
+                            const float* t = cyt + 4 * (q / BW);
+                            f22 += t[0] * (dps[k][3] + t[1] * q22);
+                            f12 += t[2] * (dps[k][4] + t[3] * q12);
+                            f32 += t[2] * (dps[k][5] + t[3] * q23);
+                        }
                         if (f & CP_XB) {
-                            szw[q] = vqx;
-                            szw[4 * BOXS + q] = v13;
+                            szw[q] = f11;
+                            E[q] = f21;
+                            szw[4 * BOXS + q] = f31;
                         }
                         if (f & CP_YB) {
-                            szw[BOXS + q] = vqy;
-                            szw[3 * BOXS + q] = v23;
+                            szw[BOXS + q] = f22;
+                            szw[5 * BOXS + q] = f12;
+                            szw[3 * BOXS + q] = f32;
                         }
                     }
                 }
                 __syncthreads();
-                XD0 = sz;             // Q_x
-                XD1 = E;              // S_yx
-                XD2 = sz + 4 * BOXS;  // S_zx
-                YD0 = sz + BOXS;      // Q_y
-                YD1 = sz + 5 * BOXS;  // S_xy
-                YD2 = sz + 3 * BOXS;  // S_zy
+                XD1 = E;
             }
             if (ok && own) {
                 const float g[3][3] = {{dpx(XD0, o) * h, dmy(YD1, o) * h, dq(q13) * h},   // u^x
                                        {dmx(XD1, o) * h, dpy(YD0, o) * h, dq(q23) * h},   // u^y
                                        {dmx(XD2, o) * h, dmy(YD2, o) * h, dq(q33) * h}};  // u^z
-                float rb[3] = {1.f, 1.f, 1.f}, ab[3];
-                if constexpr (Cfg::BALPHA >= 0) {
-                    const float* r0 = sz + Cfg::BRHO * BOXS;
-                    const float* a0 = sz + Cfg::BALPHA * BOXS;
-                    rb[0] = 0.5f * (r0[o] + r0[o + xc1]);
-                    rb[1] = 0.5f * (r0[o] + r0[o + yc1]);
-                    rb[2] = 0.5f * (r0[o] + sz1[Cfg::BRHO * BOXS + o]);
-                    ab[0] = 0.5f * (a0[o] + a0[o + xc1]);
-                    ab[1] = 0.5f * (a0[o] + a0[o + yc1]);
-                    ab[2] = 0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o]);
-                } else {
-                    ab[0] = 0.5f * (ca[0] + ca[1]);
-                    ab[1] = 0.5f * (ca[0] + ca[2]);
-                    ab[2] = 0.5f * (ca[0] + ca[3]);
-                    if constexpr (PML) {
-                        rb[0] = 0.5f * (cr[0] + cr[1]);
-                        rb[1] = 0.5f * (cr[0] + cr[2]);
-                        rb[2] = 0.5f * (cr[0] + cr[3]);
-                    }
-                }
+                const float* r0 = sz + Cfg::BRHO * BOXS;
+                const float* a0 = sz + Cfg::BALPHA * BOXS;
+                const float rb[3] = {0.5f * (r0[o] + r0[o + xc1]), 0.5f * (r0[o] + r0[o + yc1]),
+                                     0.5f * (r0[o] + sz1[Cfg::BRHO * BOXS + o])};
+                const float ab[3] = {0.5f * (a0[o] + a0[o + xc1]), 0.5f * (a0[o] + a0[o + yc1]),
+                                     0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o])};
                 PmlZ pz{};
                 if constexpr (PML) pml_z_init(pz, p, z);
                 const unsigned gi = (unsigned)z * nxy + gxy;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    float res;
-                    if constexpr (!ADJ) {
-                        float acc = g[i][0] + g[i][1] + g[i][2];
-                        if constexpr (PML) {
+                    float acc = g[i][0] + g[i][1] + g[i][2];
+                    if constexpr (PML) {
 #pragma unroll
-                            for (int j = 0; j < 3; ++j)
-                                if (in_axis(j, px, pz.lz)) {
-                                    const int hh = (i == j);
+                        for (int j = 0; j < 3; ++j)
+                            if (in_axis<PXY>(j, px, pz.lz)) {
+                                const int hh = (i == j);
+                                float* ph = &p.phi[i][j][own_slab(j, px, pz.lz, x, y, z, p)];
+                                if constexpr (!ADJ) {
                                     const float v = coef(j, hh, 1, px, pz) * cph[i][j] + coef(j, hh, 0, px, pz) * g[i][j];
-                                    p.phi[i][j][own_slab(j, px, pz.lz, x, y, z, p)] = v;
+                                    *ph = v;
                                     acc += coef(j, hh, 2, px, pz) * v;
+                                } else {
+                                    *ph = coef(j, hh, 1, px, pz) * (cph[i][j] + coef(j, hh, 2, px, pz) * cu[i]);
                                 }
-                        }
-                        res = (1.0f - dt * ab[i]) * cu[i] + __fdividef(dt, rb[i]) * acc;
-                    } else {
-                        if constexpr (PML) {
-                            const float w = __fdividef(dt, rb[i]) * cu[i];
-#pragma unroll
-                            for (int j = 0; j < 3; ++j)
-                                if (in_axis(j, px, pz.lz)) {
-                                    const int hh = (i == j);
-                                    p.phi[i][j][own_slab(j, px, pz.lz, x, y, z, p)] =
-                                        coef(j, hh, 1, px, pz) * (cph[i][j] + coef(j, hh, 2, px, pz) * w);
-                                }
-                        }
-                        res = (1.0f - dt * ab[i]) * cu[i] - (g[i][0] + g[i][1] + g[i][2]);
+                            }
                     }
+                    const float res = ADJ ? (1.0f - dt * ab[i]) * cu[i] - __fdividef(dt * dt, rb[i]) * acc
+                                          : (1.0f - dt * ab[i]) * cu[i] + __fdividef(dt, rb[i]) * acc;
                     p.u[i][gi] = res;
                 }
             }
@@ -697,10 +569,15 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
 // stress family
 // ===========================================================================
 // One (tile, z chunk) work item; false if a bounded wait timed out.
-template <bool ADJ, bool PML>
+//   forward: psi <- b psi + a e(u),  sigma <- sigma + dt C (e(u) + chi psi)
+//   adjoint: psi^ <- b (psi^ + chi Q)  (the deferred tail of the velocity-family
+//            half, own point, old Q), then Q <- Q - C e(E),
+//            E = w + a (phi~ + chi w) on the slabs
+template <bool ADJ, int PM>
 __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y, int zc0,
                                          int zc1, int* err, float* sm) {
-    using Cfg = StrCfg<ADJ, PML>;
+    using Cfg = StrCfg<ADJ, PM>;
+    constexpr bool PML = Cfg::PML, PXY = Cfg::PXY;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -714,7 +591,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     const int P = p.P;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
     PmlXY px{};
-    if constexpr (PML) pml_xy_init(px, p, x, y, own);
+    if constexpr (PXY) pml_xy_init(px, p, x, y, own);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
@@ -738,9 +615,9 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     const int oxy = o + xc1 + yc1;
     CrossPos cross{};
     CrossPml cpm{};
-    __shared__ float cxt[(ADJ && PML) ? 4 * BW : 1], cyt[(ADJ && PML) ? 4 * BH : 1];
-    if constexpr (ADJ) cross_init(cross, tid, x0, y0, p.nx, p.ny);
-    if constexpr (ADJ && PML) {
+    __shared__ float cxt[(ADJ && PXY) ? 4 * BW : 1], cyt[(ADJ && PXY) ? 4 * BH : 1];
+    if constexpr (ADJ && PXY) {
+        cross_init(cross, tid, x0, y0, p.nx, p.ny);
         __syncthreads();  // a persistent block may still read the tables of its previous item
         cross_pml_init(cpm, cxt, cyt, cross, tid, x0, y0, p);
         __syncthreads();
@@ -758,7 +635,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
             const int lz = slab_local(zn, p.nz, P);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (in_axis(j, px, lz)) {
+                if (in_axis<PXY>(j, px, lz)) {
                     const unsigned si = own_slab(j, px, lz, x, y, zn, p);
 #pragma unroll
                     for (int i = 0; i < 3; ++i) nps[i][j] = p.psi[i][j][si];
@@ -802,9 +679,9 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         const float chp[3] = {nhp[0], nhp[1], nhp[2]};
         prefetch(z + 1);
         prefetch_heads(pl + 1);
-        // C-PML adjoint: memory variables phi at the cross positions of plane z
+        // full C-PML adjoint: memory variables phi~ at the cross positions of plane z
         float dph[2][6];
-        if constexpr (ADJ && PML) {
+        if constexpr (ADJ && PXY) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
 #pragma unroll
@@ -828,148 +705,84 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
         const float* sp = ring.stage(pl);
         const float* spm = (pl - 1 >= pfirst) ? ring.stage(pl - 1) : nullptr;
-        // ---- queue heads: d_z u^x, d_z u^y are integer->half (plane pl);
-        //      d_z u^z is half->integer (plane pl-1)
+        // ---- queue heads: d_z of the x and y velocity-like fields is
+        //      integer->half (plane pl); d_z of the z one is half->integer (pl-1)
         if (ok) {
-            if constexpr (!ADJ) {
-                push(qx, sp[o]);
-                push(qy, sp[BOXS + o]);
-                push(qz, spm ? spm[2 * BOXS + o] : 0.f);
-            } else {
-                float hx = 0.f, hy = 0.f, hz = 0.f;
-                if (pl >= 0 && pl < p.nz) {
-                    const float* r = sp + 3 * BOXS;
-                    hx = __fdividef(2.0f * dt, r[o] + r[o + xc1]) * sp[o];
-                    hy = __fdividef(2.0f * dt, r[o] + r[o + yc1]) * sp[BOXS + o];
-                    if constexpr (PML) {
-                        if (own && slab_local(pl, p.nz, P) >= 0) {
-                            const float a = tabv(p, 2, 0, 0, pl), c = tabv(p, 2, 0, 2, pl);
-                            hx += a * (chp[0] + c * hx);
-                            hy += a * (chp[1] + c * hy);
-                        }
-                    }
+            float hx = sp[o], hy = sp[BOXS + o];
+            float hz = spm ? spm[2 * BOXS + o] : 0.f;
+            if constexpr (ADJ && PML) {
+                // z-layer terms of E13, E23 (integer lattice, plane pl) and E33
+                // (half lattice, plane pl-1)
+                if (own && pl >= 0 && pl < p.nz && slab_local(pl, p.nz, P) >= 0) {
+                    const float a = tabv(p, 2, 0, 0, pl), c = tabv(p, 2, 0, 2, pl);
+                    hx += a * (chp[0] + c * hx);
+                    hy += a * (chp[1] + c * hy);
                 }
                 const int zm = pl - 1;
-                if (spm && zm >= 0 && zm < p.nz) {
-                    const float* r = spm + 3 * BOXS;
-                    const float* r1 = (pl < p.nz) ? sp + 3 * BOXS : r;
-                    hz = __fdividef(2.0f * dt, r[o] + r1[o]) * spm[2 * BOXS + o];
-                    if constexpr (PML) {
-                        if (own && slab_local(zm, p.nz, P) >= 0) {
-                            const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
-                            hz += a * (chp[2] + c * hz);
-                        }
-                    }
+                if (own && spm && zm >= 0 && zm < p.nz && slab_local(zm, p.nz, P) >= 0) {
+                    const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
+                    hz += a * (chp[2] + c * hz);
                 }
-                push(qx, hx);
-                push(qy, hy);
-                push(qz, hz);
             }
+            push(qx, hx);
+            push(qy, hy);
+            push(qz, hz);
         }
 
         if (out) {
             float* szw = ring.stage(z);
             const float* sz = szw;
             const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
-            const float *XD0, *XD1, *XD2, *YD0, *YD1, *YD2;
-            if constexpr (!ADJ) {
-                XD0 = sz;             // u^x  (D-x for s11)
-                XD1 = sz + BOXS;      // u^y  (D+x for s12)
-                XD2 = sz + 2 * BOXS;  // u^z  (D+x for s13)
-                YD0 = sz + BOXS;      // u^y  (D-y for s22)
-                YD1 = sz;             // u^x  (D+y for s12)
-                YD2 = sz + 2 * BOXS;  // u^z  (D+y for s23)
-            } else if constexpr (!PML) {
-                // w = dt u / rho on the velocity nodes, in place over the
-                // cross-shaped region the differences read (x band and four y
-                // rows, as in the velocity family); zero outside the grid.  Off
-                // the layers R_ij = w_i for every difference direction j.
-                float* U0 = szw;
-                float* U1 = szw + BOXS;
-                float* U2 = szw + 2 * BOXS;
-                const float* r0 = sz + 3 * BOXS;
-                const float* r1 = sz1 + 3 * BOXS;
-                if (ok) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const unsigned char f = cross.f[k];
-                        if (!(f & CP_EXISTS)) continue;
-                        const int q = cross.q[k];
-                        float wx = 0.f, wy = 0.f, wz = 0.f;
-                        if (f & CP_IN) {
-                            const float rr = r0[q];
-                            wx = __fdividef(2.0f * dt, rr + r0[q + cross.dx[k]]) * U0[q];
-                            wy = __fdividef(2.0f * dt, rr + r0[q + cross.dy[k]]) * U1[q];
-                            wz = __fdividef(2.0f * dt, rr + r1[q]) * U2[q];
-                        }
-                        U0[q] = wx;
-                        U1[q] = wy;
-                        U2[q] = wz;
-                    }
-                }
-                __syncthreads();
-                XD0 = U0;
-                XD1 = U1;
-                XD2 = U2;
-                YD0 = U1;
-                YD1 = U0;
-                YD2 = U2;
-            } else {
-                // C-PML blocks: w as in the interior, plus the memory-variable
-                // terms of the x and y layers (adjoint of Gamma and E): the
-                // x-differenced fields R_xx, R_yx, R_zx stay in place, the
-                // y-differenced R_yy, R_xy, R_zy go to boxes E0, E1, E2.
-                float* U0 = szw;
-                float* U1 = szw + BOXS;
-                float* U2 = szw + 2 * BOXS;
+            // x-differenced fields and y-differenced ones
+            const float* XD0 = sz;             // u^x / E11  (D-x for s11)
+            const float* XD1 = sz + BOXS;      // u^y / E21  (D+x for s12)
+            const float* XD2 = sz + 2 * BOXS;  // u^z / E31  (D+x for s13)
+            const float* YD0 = sz + BOXS;      // u^y / E22  (D-y for s22)
+            const float* YD1 = sz;             // u^x / E12  (D+y for s12)
+            const float* YD2 = sz + 2 * BOXS;  // u^z / E32  (D+y for s23)
+            if constexpr (ADJ && PXY) {
+                // E = w + a (phi~ + chi w): the x-differenced fields in place at
+                // the x-band (x layer) positions, the y-differenced ones at the
+                // y-row (y layer) positions in the three extra boxes.
                 float* E0 = der;
                 float* E1 = der + BOXS;
                 float* E2 = der + 2 * BOXS;
-                const float* r0 = sz + 3 * BOXS;
-                const float* r1 = sz1 + 3 * BOXS;
                 if (ok) {
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const unsigned char f = cross.f[k];
                         if (!(f & CP_EXISTS)) continue;
                         const int q = cross.q[k];
-                        float wx = 0.f, wy = 0.f, wz = 0.f;
-                        if (f & CP_IN) {
-                            const float rr = r0[q];
-                            wx = __fdividef(2.0f * dt, rr + r0[q + cross.dx[k]]) * U0[q];
-                            wy = __fdividef(2.0f * dt, rr + r0[q + cross.dy[k]]) * U1[q];
-                            wz = __fdividef(2.0f * dt, rr + r1[q]) * U2[q];
-                        }
-                        float rxx = wx, ryx = wy, rzx = wz, ryy = wy, rxy = wx, rzy = wz;
+                        const float wx = sz[q], wy = sz[BOXS + q], wz = sz[2 * BOXS + q];
+                        float exx = wx, eyx = wy, ezx = wz, eyy = wy, exy = wx, ezy = wz;
                         if (cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
-                            rxx = wx + t[2] * (dph[k][0] + t[3] * wx);
-                            ryx = wy + t[0] * (dph[k][1] + t[1] * wy);
-                            rzx = wz + t[0] * (dph[k][2] + t[1] * wz);
+                            exx += t[2] * (dph[k][0] + t[3] * wx);
+                            eyx += t[0] * (dph[k][1] + t[1] * wy);
+                            ezx += t[0] * (dph[k][2] + t[1] * wz);
                         }
                         if (cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            ryy = wy + t[2] * (dph[k][3] + t[3] * wy);
-                            rxy = wx + t[0] * (dph[k][4] + t[1] * wx);
-                            rzy = wz + t[0] * (dph[k][5] + t[1] * wz);
+                            eyy += t[2] * (dph[k][3] + t[3] * wy);
+                            exy += t[0] * (dph[k][4] + t[1] * wx);
+                            ezy += t[0] * (dph[k][5] + t[1] * wz);
                         }
-                        U0[q] = rxx;
-                        U1[q] = ryx;
-                        U2[q] = rzx;
+                        if (f & CP_XB) {
+                            szw[q] = exx;
+                            szw[BOXS + q] = eyx;
+                            szw[2 * BOXS + q] = ezx;
+                        }
                         if (f & CP_YB) {
-                            E0[q] = ryy;
-                            E1[q] = rxy;
-                            E2[q] = rzy;
+                            E0[q] = eyy;
+                            E1[q] = exy;
+                            E2[q] = ezy;
                         }
                     }
                 }
                 __syncthreads();
-                XD0 = U0;  // R_xx
-                XD1 = U1;  // R_yx
-                XD2 = U2;  // R_zx
-                YD0 = E0;  // R_yy
-                YD1 = E1;  // R_xy
-                YD2 = E2;  // R_zy
+                YD0 = E0;
+                YD1 = E1;
+                YD2 = E2;
             }
             if (ok && own) {
                 // du[i][j] = d_j of the u^i-like field
@@ -979,21 +792,21 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 const unsigned gi = (unsigned)z * nxy + gxy;
                 PmlZ pz{};
                 if constexpr (PML) pml_z_init(pz, p, z);
+                const float* m0 = sz + Cfg::BMU * BOXS;
+                const float* m1 = sz1 + Cfg::BMU * BOXS;
+                const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(m0[o]);
+                const float m12 = harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
+                const float m13 = harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
+                const float m23 = harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);
                 float res[6];
                 if constexpr (!ADJ) {
-                    const float* m0 = sz + Cfg::BMU * BOXS;
-                    const float* m1 = sz1 + Cfg::BMU * BOXS;
-                    const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(m0[o]);
-                    const float m12 = harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
-                    const float m13 = harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
-                    const float m23 = harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);
                     // memory variables psi^{ij} (lattice: integer if i == j, else half)
                     float cp[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // chi * psi
                     float pd[3] = {0.f, 0.f, 0.f};                                         // psi^{kk}
                     if constexpr (PML) {
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
-                            if (in_axis(j, px, pz.lz)) {
+                            if (in_axis<PXY>(j, px, pz.lz)) {
                                 const unsigned si = own_slab(j, px, pz.lz, x, y, z, p);
 #pragma unroll
                                 for (int i = 0; i < 3; ++i) {
@@ -1016,34 +829,26 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                     res[5] = so[5] + dt * m12 * (du[0][1] + du[1][0] + cp[0][1] + cp[1][0]);
                 } else {
                     if constexpr (PML) {
-                        // psi <- B~ (psi + Delta^T sigma_old) at the own point
-                        const float* m0 = sz + Cfg::BMU * BOXS;
-                        const float* m1 = sz1 + Cfg::BMU * BOXS;
-                        const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(m0[o]);
-                        const float ltr = lam * (so[0] + so[1] + so[2]);
-                        const float msh[3] = {harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]),   // 23
-                                              harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]),   // 13
-                                              harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy])};  // 12
+                        // psi^ <- b (psi^ + chi Q_old) at the own point
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
-                            if (in_axis(j, px, pz.lz)) {
+                            if (in_axis<PXY>(j, px, pz.lz)) {
                                 const unsigned si = own_slab(j, px, pz.lz, x, y, z, p);
 #pragma unroll
                                 for (int i = 0; i < 3; ++i) {
                                     const int hh = (i != j);
-                                    const int v = voigt(i, j);
-                                    const float add = (i == j) ? dt * (ltr + mu2 * coef(j, 0, 2, px, pz) * so[j])
-                                                               : coef(j, 1, 2, px, pz) * dt * msh[v - 3] * so[v];
-                                    p.psi[i][j][si] = coef(j, hh, 1, px, pz) * (cps[i][j] + add);
+                                    p.psi[i][j][si] =
+                                        coef(j, hh, 1, px, pz) * (cps[i][j] + coef(j, hh, 2, px, pz) * so[voigt(i, j)]);
                                 }
                             }
                     }
-                    res[0] = so[0] - du[0][0];
-                    res[1] = so[1] - du[1][1];
-                    res[2] = so[2] - du[2][2];
-                    res[3] = so[3] - (du[1][2] + du[2][1]);
-                    res[4] = so[4] - (du[0][2] + du[2][0]);
-                    res[5] = so[5] - (du[0][1] + du[1][0]);
+                    const float lt = lam * (du[0][0] + du[1][1] + du[2][2]);
+                    res[0] = so[0] - (lt + mu2 * du[0][0]);
+                    res[1] = so[1] - (lt + mu2 * du[1][1]);
+                    res[2] = so[2] - (lt + mu2 * du[2][2]);
+                    res[3] = so[3] - m23 * (du[1][2] + du[2][1]);
+                    res[4] = so[4] - m13 * (du[0][2] + du[2][0]);
+                    res[5] = so[5] - m12 * (du[0][1] + du[1][0]);
                 }
 #pragma unroll
                 for (int v = 0; v < 6; ++v) p.s[v][gi] = res[v];
@@ -1066,34 +871,34 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 // ===========================================================================
 // kernels: one grid (single instance) and persistent (many instances)
 // ===========================================================================
-template <bool ADJ, bool PML>
+template <bool ADJ, int PM>
 __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
                                                   int* err) {
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1;
     locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
-    vel_body<ADJ, PML>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    vel_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
-template <bool ADJ, bool PML>
-__global__ void __launch_bounds__(NT, PML ? 3 : 1) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
+template <bool ADJ, int PM>
+__global__ void __launch_bounds__(NT, PM == PM_NONE ? 1 : (PM == PM_Z && !ADJ ? 4 : 3)) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
                                                   int* err) {
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1;
     locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
-    str_body<ADJ, PML>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    str_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
 // Persistent multi-instance half steps: a fixed grid walks the work items of
 // every unfinished instance of the table (block b takes items b, b + grid,
 // ...), forward and adjoint instances alike.  STR selects the stress family.
-template <bool STR, bool PML>
-__global__ void __launch_bounds__(NT) k_multi(const MultiTable* __restrict__ T, int* err) {
+template <bool STR, int PM>
+__global__ void __launch_bounds__(NT, PM == PM_Z ? 3 : 1) k_multi(const MultiTable* __restrict__ T, int* err) {
     extern __shared__ __align__(128) float sm[];
     __shared__ StepParams sp;
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int n = T->n_inst;
-    const int* pre = PML ? T->pre_outer : T->pre_inner;
+    const int* pre = PM == PM_FULL ? T->pre_outer : (PM == PM_Z ? T->pre_zslab : T->pre_inner);
     const int total = pre[n];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         int i = 0;
@@ -1101,7 +906,7 @@ __global__ void __launch_bounds__(NT) k_multi(const MultiTable* __restrict__ T, 
         const InstDev& I = T->inst[i];
         if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
         int tile_x, tile_y, zc0, zc1;
-        locate(PML ? I.outer : I.inner, item - pre[i], tile_x, tile_y, zc0, zc1);
+        locate(PM == PM_FULL ? I.outer : (PM == PM_Z ? I.zslab : I.inner), item - pre[i], tile_x, tile_y, zc0, zc1);
         // a work item must lie inside its instance's grid; otherwise record
         // the inconsistency and touch nothing
         if (tile_x < 0 || tile_x * TX >= I.p.nx || tile_y < 0 || tile_y * TY >= I.p.ny || zc0 < 0 || zc0 >= zc1 ||
@@ -1116,10 +921,10 @@ __global__ void __launch_bounds__(NT) k_multi(const MultiTable* __restrict__ T, 
             for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
         __syncthreads();
         bool ok;
-        if (STR) ok = I.adj ? str_body<true, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
-                            : str_body<false, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
-        else ok = I.adj ? vel_body<true, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
-                        : vel_body<false, PML>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+        if (STR) ok = I.adj ? str_body<true, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
+                            : str_body<false, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+        else ok = I.adj ? vel_body<true, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
+                        : vel_body<false, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
         if (!ok) return;
     }
 }
@@ -1165,59 +970,91 @@ int add_region(RegionList& rl, int tx0, int tx1, int ty0, int ty1, int za, int z
     return 1;
 }
 
-// interior region (no C-PML code) and up to six C-PML regions
-void make_regions(const StepParams& p, int per_sm_int, int sms, RegionList& inner, int& inner_blocks,
-                  RegionList& outer, int& outer_blocks) {
-    inner.n = outer.n = 0;
-    inner_blocks = outer_blocks = 0;
+// z chunk length for `tiles` tile columns of zlen planes run by `slots`
+// concurrently resident blocks: the chunk count that fills the last wave
+// best, discounted by the three extra planes every chunk loads.
+int chunk_planes(long tiles, int zlen, long slots) {
+    const int cmax = std::max(1, zlen / 16);
+    int best = 1;
+    double best_s = -1.0;
+    for (int c = 1; c <= cmax; ++c) {
+        const double w = (double)tiles * c / (double)std::max(1L, slots);
+        const double sc = w / std::ceil(w) / (1.0 + 3.0 * c / zlen);
+        if (sc > best_s + 1e-9) {
+            best_s = sc;
+            best = c;
+        }
+    }
+    return (zlen + best - 1) / best;
+}
+
+// Work regions of one half step: the interior tiles off the z slabs (no
+// layer code), the interior tiles on the z slabs (z-layer code) and the frame
+// of tiles around the interior ones (all planes; full C-PML code, up to four
+// rectangles).  With P = 0 every tile is interior and there are no slabs.
+void make_regions(const StepParams& p, long slots_inner, long slots_outer, RegionList& inner, int& inner_blocks,
+                  RegionList& zslab, int& zslab_blocks, RegionList& outer, int& outer_blocks) {
+    inner.n = zslab.n = outer.n = 0;
+    inner_blocks = zslab_blocks = outer_blocks = 0;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
     const int P = p.P;
-    const long want = 2L * sms * std::max(1, per_sm_int);  // about two waves
-    if (P == 0) {
-        const long tiles = (long)ntx * nty;
-        long chunks = std::max(1L, std::min((want + tiles - 1) / tiles, (long)std::max(1, p.nz / 16)));
-        add_region(inner, 0, ntx, 0, nty, 0, p.nz, (int)((p.nz + chunks - 1) / chunks), inner_blocks);
+    int txlo = 0, txhi = ntx - 1, tylo = 0, tyhi = nty - 1;
+    if (P > 0 && !interior_tiles(p, txlo, txhi, tylo, tyhi)) {
+        add_region(outer, 0, ntx, 0, nty, 0, p.nz, chunk_planes((long)ntx * nty, p.nz, slots_outer), outer_blocks);
         return;
     }
-    const int za = P, zb = p.nz - P - 1;  // planes off the z slabs
-    int txlo, txhi, tylo, tyhi;
-    const bool has = za < zb && interior_tiles(p, txlo, txhi, tylo, tyhi);
-    // z slabs: every tile, one chunk each
-    add_region(outer, 0, ntx, 0, nty, 0, std::min(P, p.nz), P, outer_blocks);
-    add_region(outer, 0, ntx, 0, nty, std::max(zb, P), p.nz, p.nz, outer_blocks);
-    const int zcf = 64;
-    if (!has) {
-        add_region(outer, 0, ntx, 0, nty, za, zb, zcf, outer_blocks);
-        return;
-    }
-    add_region(outer, 0, txlo, 0, nty, za, zb, zcf, outer_blocks);
-    add_region(outer, txhi + 1, ntx, 0, nty, za, zb, zcf, outer_blocks);
-    add_region(outer, txlo, txhi + 1, 0, tylo, za, zb, zcf, outer_blocks);
-    add_region(outer, txlo, txhi + 1, tyhi + 1, nty, za, zb, zcf, outer_blocks);
     const long tiles = (long)(txhi + 1 - txlo) * (tyhi + 1 - tylo);
-    long chunks = std::max(1L, std::min((want + tiles - 1) / tiles, (long)std::max(1, (zb - za) / 16)));
-    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, (int)((zb - za + chunks - 1) / chunks), inner_blocks);
+    const long frame = (long)ntx * nty - tiles;
+    if (frame > 0) {
+        const int zc = chunk_planes(frame, p.nz, slots_outer);
+        add_region(outer, 0, txlo, 0, nty, 0, p.nz, zc, outer_blocks);
+        add_region(outer, txhi + 1, ntx, 0, nty, 0, p.nz, zc, outer_blocks);
+        add_region(outer, txlo, txhi + 1, 0, tylo, 0, p.nz, zc, outer_blocks);
+        add_region(outer, txlo, txhi + 1, tyhi + 1, nty, 0, p.nz, zc, outer_blocks);
+    }
+    const int za = P > 0 ? std::min(P, p.nz) : 0;               // planes [za, zb) are off the z slabs
+    const int zb = P > 0 ? std::max(za, p.nz - P - 1) : p.nz;
+    add_region(zslab, txlo, txhi + 1, tylo, tyhi + 1, 0, za, za, zslab_blocks);
+    add_region(zslab, txlo, txhi + 1, tylo, tyhi + 1, zb, p.nz, p.nz - zb, zslab_blocks);
+    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, chunk_planes(tiles, zb - za, slots_inner),
+               inner_blocks);
 }
 
 struct LaunchPlan {
     int dev, nx, ny, nz, P, family;
-    RegionList inner, outer;
-    int inner_blocks, outer_blocks;
+    RegionList inner, zslab, outer;
+    int inner_blocks, zslab_blocks, outer_blocks;
 };
 
-}  // namespace
-
-template <bool ADJ, bool PML>
-static const void* vel_fn() {
-    return (const void*)k_vel_tiled<ADJ, PML>;
+// kernel and dynamic shared memory of a family (0 vel fwd, 1 vel adj, 2 str
+// fwd, 3 str adj) and C-PML mode
+template <int PM>
+const void* fam_fn(int f) {
+    return f == 0 ? (const void*)k_vel_tiled<false, PM> : f == 1 ? (const void*)k_vel_tiled<true, PM>
+         : f == 2 ? (const void*)k_str_tiled<false, PM> : (const void*)k_str_tiled<true, PM>;
 }
-template <bool ADJ, bool PML>
-static const void* str_fn() {
-    return (const void*)k_str_tiled<ADJ, PML>;
+template <int PM>
+size_t fam_smem(int f) {
+    return f == 0 ? VelCfg<false, PM>::SMEM : f == 1 ? VelCfg<true, PM>::SMEM
+         : f == 2 ? StrCfg<false, PM>::SMEM : StrCfg<true, PM>::SMEM;
+}
+const void* fam_fn(int f, int pm) {
+    return pm == PM_FULL ? fam_fn<PM_FULL>(f) : pm == PM_Z ? fam_fn<PM_Z>(f) : fam_fn<PM_NONE>(f);
+}
+size_t fam_smem(int f, int pm) {
+    return pm == PM_FULL ? fam_smem<PM_FULL>(f) : pm == PM_Z ? fam_smem<PM_Z>(f) : fam_smem<PM_NONE>(f);
 }
 
-// family: 0 vel fwd, 1 vel adj, 2 str fwd, 3 str adj
-static LaunchPlan plan_for(int family, const StepParams& p) {
+// resident blocks of a kernel on the whole device
+long device_slots(const void* fn, size_t smem, int dev) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int sms = 148, per_sm = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
+    return (long)sms * std::max(1, per_sm);
+}
+
+LaunchPlan plan_for(int family, const StepParams& p) {
     static LaunchPlan plans[32];
     static int nplans = 0;
     static std::mutex mu;
@@ -1229,19 +1066,9 @@ static LaunchPlan plan_for(int family, const StepParams& p) {
         if (L.dev == dev && L.family == family && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz && L.P == p.P)
             return L;
     }
-    const void* fi = family == 0 ? vel_fn<false, false>() : family == 1 ? vel_fn<true, false>()
-                   : family == 2 ? str_fn<false, false>() : str_fn<true, false>();
-    const void* fo = family == 0 ? vel_fn<false, true>() : family == 1 ? vel_fn<true, true>()
-                   : family == 2 ? str_fn<false, true>() : str_fn<true, true>();
-    const size_t si = family == 0 ? VelCfg<false, false>::SMEM : family == 1 ? VelCfg<true, false>::SMEM
-                    : family == 2 ? StrCfg<false, false>::SMEM : StrCfg<true, false>::SMEM;
-    const size_t so = family == 0 ? VelCfg<false, true>::SMEM : family == 1 ? VelCfg<true, true>::SMEM
-                    : family == 2 ? StrCfg<false, true>::SMEM : StrCfg<true, true>::SMEM;
-    cudaFuncSetAttribute(fi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)si);
-    cudaFuncSetAttribute(fo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)so);
-    int sms = 148, per_sm = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fi, NT, si);
+    const long si = device_slots(fam_fn(family, PM_NONE), fam_smem(family, PM_NONE), dev);
+    const long so = device_slots(fam_fn(family, PM_FULL), fam_smem(family, PM_FULL), dev);
+    device_slots(fam_fn(family, PM_Z), fam_smem(family, PM_Z), dev);  // sets its shared-memory limit
     LaunchPlan& L = plans[nplans % 32];
     L.dev = dev;
     L.family = family;
@@ -1249,95 +1076,123 @@ static LaunchPlan plan_for(int family, const StepParams& p) {
     L.ny = p.ny;
     L.nz = p.nz;
     L.P = p.P;
-    make_regions(p, per_sm, sms, L.inner, L.inner_blocks, L.outer, L.outer_blocks);
+    make_regions(p, si, so, L.inner, L.inner_blocks, L.zslab, L.zslab_blocks, L.outer, L.outer_blocks);
     nplans = std::min(nplans + 1, 32);
     return L;
 }
 
+}  // namespace
+
+// The frame launch goes to `aux` (when given) between a fork and a join
+// event, so that it overlaps the interior launch on `st`.
 template <bool ADJ>
-static void launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
+static void launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 1 : 0, p);
+    const dim3 blk(TX, TY, 1);
+    const bool split = ss.aux && (L.outer_blocks || L.zslab_blocks) && L.inner_blocks;
+    cudaStream_t so = ss.st;
+    if (split) {
+        cudaEventRecord(ss.fork, ss.st);
+        cudaStreamWaitEvent(ss.aux, ss.fork, 0);
+        so = ss.aux;
+    }
     if (L.outer_blocks)
-        k_vel_tiled<ADJ, true><<<L.outer_blocks, dim3(TX, TY, 1), VelCfg<ADJ, true>::SMEM, st>>>(p, tm, L.outer, err);
+        k_vel_tiled<ADJ, PM_FULL><<<L.outer_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.outer, err);
+    if (L.zslab_blocks)
+        k_vel_tiled<ADJ, PM_Z><<<L.zslab_blocks, blk, VelCfg<ADJ, PM_Z>::SMEM, so>>>(p, tm, L.zslab, err);
     if (L.inner_blocks)
-        k_vel_tiled<ADJ, false><<<L.inner_blocks, dim3(TX, TY, 1), VelCfg<ADJ, false>::SMEM, st>>>(p, tm, L.inner, err);
+        k_vel_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
+    if (split) {
+        cudaEventRecord(ss.join, ss.aux);
+        cudaStreamWaitEvent(ss.st, ss.join, 0);
+    }
 }
 
 template <bool ADJ>
-static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
+static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 3 : 2, p);
+    const dim3 blk(TX, TY, 1);
+    const bool split = ss.aux && (L.outer_blocks || L.zslab_blocks) && L.inner_blocks;
+    cudaStream_t so = ss.st;
+    if (split) {
+        cudaEventRecord(ss.fork, ss.st);
+        cudaStreamWaitEvent(ss.aux, ss.fork, 0);
+        so = ss.aux;
+    }
     if (L.outer_blocks)
-        k_str_tiled<ADJ, true><<<L.outer_blocks, dim3(TX, TY, 1), StrCfg<ADJ, true>::SMEM, st>>>(p, tm, L.outer, err);
+        k_str_tiled<ADJ, PM_FULL><<<L.outer_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.outer, err);
+    if (L.zslab_blocks)
+        k_str_tiled<ADJ, PM_Z><<<L.zslab_blocks, blk, StrCfg<ADJ, PM_Z>::SMEM, so>>>(p, tm, L.zslab, err);
     if (L.inner_blocks)
-        k_str_tiled<ADJ, false><<<L.inner_blocks, dim3(TX, TY, 1), StrCfg<ADJ, false>::SMEM, st>>>(p, tm, L.inner, err);
+        k_str_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
+    if (split) {
+        cudaEventRecord(ss.join, ss.aux);
+        cudaStreamWaitEvent(ss.st, ss.join, 0);
+    }
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
-template <bool STR, bool PML>
+template <bool STR, int PM>
 static size_t multi_smem() {
-    return STR ? std::max(StrCfg<false, PML>::SMEM, StrCfg<true, PML>::SMEM)
-               : std::max(VelCfg<false, PML>::SMEM, VelCfg<true, PML>::SMEM);
+    return STR ? std::max(StrCfg<false, PM>::SMEM, StrCfg<true, PM>::SMEM)
+               : std::max(VelCfg<false, PM>::SMEM, VelCfg<true, PM>::SMEM);
 }
 
-template <bool STR, bool PML>
+template <bool STR, int PM>
 static int multi_grid() {
     static int grid[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!grid[dev]) {
-        const void* fn = (const void*)k_multi<STR, PML>;
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)multi_smem<STR, PML>());
-        int sms = 148, per_sm = 1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, multi_smem<STR, PML>());
-        grid[dev] = sms * std::max(1, per_sm);
-    }
+    if (!grid[dev]) grid[dev] = (int)device_slots((const void*)k_multi<STR, PM>, multi_smem<STR, PM>(), dev);
     return grid[dev];
+}
+
+template <bool STR, int PM>
+static void launch_multi(const MultiTable* dT, int* err, cudaStream_t st) {
+    k_multi<STR, PM><<<multi_grid<STR, PM>(), dim3(TX, TY, 1), multi_smem<STR, PM>(), st>>>(dT, err);
 }
 
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, cudaStream_t st) {
     if (str) {
-        k_multi<true, true><<<multi_grid<true, true>(), dim3(TX, TY, 1), multi_smem<true, true>(), st>>>(dT, err);
-        k_multi<true, false><<<multi_grid<true, false>(), dim3(TX, TY, 1), multi_smem<true, false>(), st>>>(dT, err);
+        launch_multi<true, PM_FULL>(dT, err, st);
+        launch_multi<true, PM_Z>(dT, err, st);
+        launch_multi<true, PM_NONE>(dT, err, st);
     } else {
-        k_multi<false, true><<<multi_grid<false, true>(), dim3(TX, TY, 1), multi_smem<false, true>(), st>>>(dT, err);
-        k_multi<false, false><<<multi_grid<false, false>(), dim3(TX, TY, 1), multi_smem<false, false>(), st>>>(dT, err);
+        launch_multi<false, PM_FULL>(dT, err, st);
+        launch_multi<false, PM_Z>(dT, err, st);
+        launch_multi<false, PM_NONE>(dT, err, st);
     }
 }
 
 // Region plan of one instance for the persistent kernels: z chunks of about
 // `zc` planes so that work items of different instances are of similar size.
-void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
-                           int& nouter) {
-    const int sms = 148;
-    // a large "want" makes make_regions cap the interior chunking at zc
-    make_regions(p, 1, sms, inner, ninner, outer, nouter);
-    const int tiles_in = inner.n ? (inner.r[0].tx1 - inner.r[0].tx0) * (inner.r[0].ty1 - inner.r[0].ty0) : 0;
-    if (inner.n) {
-        Region& r = inner.r[0];
-        r.zc = std::max(1, std::min(zc, r.zb - r.za));
-        ninner = tiles_in * ((r.zb - r.za + r.zc - 1) / r.zc);
-    }
-    // outer frame regions (beyond the two z slabs) use the same chunk length
-    int blocks = 0;
-    for (int k = 0; k < outer.n; ++k) {
-        Region& r = outer.r[k];
-        if (k >= 2) r.zc = std::max(1, std::min(zc, r.zb - r.za));
-        r.bstart = blocks;
-        blocks += (r.tx1 - r.tx0) * (r.ty1 - r.ty0) * ((r.zb - r.za + r.zc - 1) / r.zc);
-    }
-    nouter = blocks;
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& zslab,
+                           int& nzslab, RegionList& outer, int& nouter) {
+    make_regions(p, 1, 1, inner, ninner, zslab, nzslab, outer, nouter);
+    auto rechunk = [zc](RegionList& rl) {
+        int blocks = 0;
+        for (int k = 0; k < rl.n; ++k) {
+            Region& r = rl.r[k];
+            r.zc = std::max(1, std::min(zc, r.zb - r.za));
+            r.bstart = blocks;
+            blocks += (r.tx1 - r.tx0) * (r.ty1 - r.ty0) * ((r.zb - r.za + r.zc - 1) / r.zc);
+        }
+        return blocks;
+    };
+    ninner = rechunk(inner);
+    nzslab = rechunk(zslab);
+    nouter = rechunk(outer);
 }
 
-void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
-    if (adj) launch_vel_impl<true>(p, tm, err, st);
-    else launch_vel_impl<false>(p, tm, err, st);
+void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
+    if (adj) launch_vel_impl<true>(p, tm, err, ss);
+    else launch_vel_impl<false>(p, tm, err, ss);
 }
 
-void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
-    if (adj) launch_str_impl<true>(p, tm, err, st);
-    else launch_str_impl<false>(p, tm, err, st);
+void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
+    if (adj) launch_str_impl<true>(p, tm, err, ss);
+    else launch_str_impl<false>(p, tm, err, ss);
 }
 
 // Tensor maps: one 3-D float32 map per array, box 40 x 13 x 1, zero fill.

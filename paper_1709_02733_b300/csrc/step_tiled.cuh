@@ -1,6 +1,7 @@
 // step_tiled.cuh -- host interface of the TMA-staged step kernels.
 #pragma once
 #include <cuda.h>
+#include <cuda_runtime.h>
 
 #include "pact_internal.cuh"
 
@@ -27,8 +28,9 @@ struct RegionList {
 struct alignas(128) InstDev {
     TmaSet tm;            // tensor maps of this instance's arrays
     StepParams p;
-    RegionList inner;     // work items without C-PML code
-    RegionList outer;     // work items with C-PML code
+    RegionList inner;     // work items of the interior tiles off the z slabs
+    RegionList zslab;     // work items of the interior tiles on the z slabs
+    RegionList outer;     // work items of the C-PML frame tiles
     RecTable rec;
     const float* src;     // adjoint: traces to inject
     float* dst;           // forward: traces to sample into
@@ -42,15 +44,24 @@ constexpr int kMaxInst = 64;
 struct MultiTable {
     int n_inst;
     int pre_inner[kMaxInst + 1];   // first work item of each instance
+    int pre_zslab[kMaxInst + 1];
     int pre_outer[kMaxInst + 1];
     InstDev inst[kMaxInst];
 };
 
 // 0 on success; arrays[i] is the device base address of array i (order above)
 int make_tma_set(TmaSet* out, float* const* arrays, int nx, int ny, int nz);
-void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st);
-void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st);
+// Streams of one half step: the interior launch goes to st; with aux set,
+// the C-PML frame launch goes to aux between the events fork (recorded on st)
+// and join (waited for by st), so that the two launches overlap.
+struct SplitStreams {
+    cudaStream_t st;
+    cudaStream_t aux;
+    cudaEvent_t fork, join;
+};
+void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
+void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
 // persistent multi-instance half step (str = stress family) over a device table
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, cudaStream_t st);
-void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
-                           int& nouter);
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& zslab,
+                           int& nzslab, RegionList& outer, int& nouter);
