@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="serve a seeded Poisson stream (continuous batching vs one at a time)")
-    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--ksteps", type=int, default=16)
     return ap.parse_args()
 
@@ -390,7 +390,7 @@ def run_ours(args):
 
 def run_serving(args):
     """Serving workload: Poisson arrivals at 40 req/s, cubic grids of side 96..320
-    (multiples of 32), dx 0.4 mm, 10-cell C-PML, 800..2500 steps, 64..512
+    (multiples of 8), dx 0.4 mm, 10-cell C-PML, 800..2500 steps, 64..512
     hemisphere receivers, forward/adjoint 50/50, 120 GB HBM budget, 32 slots.
     The same requests are served (a) with continuous batching through
     pact_advance and (b) one at a time with pact_forward / pact_adjoint."""
@@ -399,7 +399,7 @@ def run_serving(args):
     from paper_1709_02733_b300 import serving
     pbuild.build()
     torch.cuda.set_device(0)
-    kw = dict(rate=40.0, seed=5, n_range=(96, 320), n_step=32, steps_range=(800, 2500), L_range=(64, 512))
+    kw = dict(rate=40.0, seed=5, n_range=(96, 320), n_step=8, steps_range=(800, 2500), L_range=(64, 512))
     cache = serving.InputCache()
     cont = serving.run_continuous(serving.make_stream(args.requests, **kw), 120 * 10 ** 9, ksteps=args.ksteps,
                                   max_slots=32, cache=cache, realtime=True)
@@ -407,7 +407,7 @@ def run_serving(args):
     line = {"metric": "served p50/p99 latency beside throughput", "value": cont["p99_s"], "unit": "s (p99)",
             "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving stream: {args.requests} seeded Poisson requests at 40 req/s, "
-                                   "sides 96..320 step 32, 800..2500 steps, 64..512 receivers, fwd/adj 50/50, "
+                                   "sides 96..320 step 8, 800..2500 steps, 64..512 receivers, fwd/adj 50/50, "
                                    "120 GB budget, 32 slots", "ksteps": args.ksteps},
             "continuous": cont, "one_at_a_time": solo,
             "throughput_ratio": cont["updates_per_s"] / solo["updates_per_s"],

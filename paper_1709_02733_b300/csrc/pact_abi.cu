@@ -690,7 +690,7 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
         if (nsteps == 0) launch_readout(out, p, h->stream);
     }
-    plan_instance_regions(p, 32, h->sv_inner, h->sv_ninner, h->sv_zslab, h->sv_nzslab, h->sv_outer, h->sv_nouter);
+    plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_zslab, h->sv_nzslab, h->sv_outer, h->sv_nouter);
     h->sv_active = nsteps > 0;
     CK(h, cudaGetLastError());
     return PACT_OK;
@@ -704,29 +704,34 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
     if (!T) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
     int dev = -1, ni = 0;
     T->pre_inner[0] = T->pre_zslab[0] = T->pre_outer[0] = 0;
-    for (int k = 0; k < n; ++k) {
-        pact_handle h = hs[k];
-        if (!h) return fail(nullptr, PACT_EINVAL, "pact_advance: NULL handle");
-        if (!h->sv_active) continue;
-        if (dev < 0) dev = h->device;
-        if (h->device != dev) return fail(h, PACT_EINVAL, "pact_advance: handles on different devices");
-        InstDev& e = T->inst[ni];
-        e.tm = h->tm;
-        e.p = make_params(h);
-        e.inner = h->sv_inner;
-        e.zslab = h->sv_zslab;
-        e.outer = h->sv_outer;
-        e.rec = make_rec(h);
-        e.src = h->sv_adj ? h->sv_in : nullptr;
-        e.dst = h->sv_adj ? nullptr : h->sv_out;
-        e.adj = h->sv_adj;
-        e.m = h->sv_m;
-        e.nsteps = h->sv_nsteps;
-        e.L = h->L;
-        T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
-        T->pre_zslab[ni + 1] = T->pre_zslab[ni] + h->sv_nzslab;
-        T->pre_outer[ni + 1] = T->pre_outer[ni] + h->sv_nouter;
-        ++ni;
+    // forward instances first, then adjoint ones (each persistent kernel
+    // serves one direction)
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int k = 0; k < n; ++k) {
+            pact_handle h = hs[k];
+            if (!h) return fail(nullptr, PACT_EINVAL, "pact_advance: NULL handle");
+            if (!h->sv_active || h->sv_adj != pass) continue;
+            if (dev < 0) dev = h->device;
+            if (h->device != dev) return fail(h, PACT_EINVAL, "pact_advance: handles on different devices");
+            InstDev& e = T->inst[ni];
+            e.tm = h->tm;
+            e.p = make_params(h);
+            e.inner = h->sv_inner;
+            e.zslab = h->sv_zslab;
+            e.outer = h->sv_outer;
+            e.rec = make_rec(h);
+            e.src = h->sv_adj ? h->sv_in : nullptr;
+            e.dst = h->sv_adj ? nullptr : h->sv_out;
+            e.adj = h->sv_adj;
+            e.m = h->sv_m;
+            e.nsteps = h->sv_nsteps;
+            e.L = h->L;
+            T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
+            T->pre_zslab[ni + 1] = T->pre_zslab[ni] + h->sv_nzslab;
+            T->pre_outer[ni + 1] = T->pre_outer[ni] + h->sv_nouter;
+            ++ni;
+        }
+        if (pass == 0) T->n_fwd = ni;
     }
     T->n_inst = ni;
     if (ni == 0) return PACT_OK;

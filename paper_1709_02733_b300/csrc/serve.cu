@@ -63,7 +63,11 @@ struct Server {
     int* err = nullptr;
     unsigned int* host_err = nullptr;  // pinned copy of the status word
     cudaStream_t cap = nullptr;
-    std::map<int, cudaGraphExec_t> graphs;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int* next = nullptr;  // work-item counters of the graph's launches
+    };
+    std::map<int, Graph> graphs;
 };
 
 std::mutex g_serve_mu;
@@ -103,22 +107,27 @@ int serve_run(const MultiTable& T, int ksteps, cudaStream_t st, std::string& why
     }
     auto it = S.graphs.find(ksteps);
     if (it == S.graphs.end()) {
+        // one counter per persistent launch of the k steps, zeroed by the
+        // graph's first node on every replay
+        const size_t ncount = (size_t)ksteps * 2 * kMultiLaunches;
+        Server::Graph G;
+        SCK(cudaMalloc(&G.next, ncount * sizeof(int)));
         cudaGraph_t g = nullptr;
         SCK(cudaStreamBeginCapture(S.cap, cudaStreamCaptureModeRelaxed));
+        cudaMemsetAsync(G.next, 0, ncount * sizeof(int), S.cap);
         for (int k = 0; k < ksteps; ++k) {
-            launch_multi_step_half(false, S.dT, S.err, S.cap);
-            launch_multi_step_half(true, S.dT, S.err, S.cap);
+            launch_multi_step_half(false, S.dT, S.err, G.next + (2 * k) * kMultiLaunches, S.cap);
+            launch_multi_step_half(true, S.dT, S.err, G.next + (2 * k + 1) * kMultiLaunches, S.cap);
             k_multi_receivers<<<kMaxInst, 256, 0, S.cap>>>(S.dT);
         }
         SCK(cudaStreamEndCapture(S.cap, &g));
-        cudaGraphExec_t ex = nullptr;
-        SCK(cudaGraphInstantiate(&ex, g, 0));
+        SCK(cudaGraphInstantiate(&G.exec, g, 0));
         cudaGraphDestroy(g);
-        it = S.graphs.emplace(ksteps, ex).first;
+        it = S.graphs.emplace(ksteps, G).first;
     }
     const size_t bytes = offsetof(MultiTable, inst) + (size_t)T.n_inst * sizeof(InstDev);
     SCK(cudaMemcpyAsync(S.dT, &T, bytes, cudaMemcpyHostToDevice, st));
-    SCK(cudaGraphLaunch(it->second, st));
+    SCK(cudaGraphLaunch(it->second.exec, st));
     SCK(cudaMemcpyAsync(S.host_err, S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
 #undef SCK
     return PACT_OK;

@@ -56,6 +56,11 @@ constexpr int D = 4;            // stage ring depth (planes)
 //   PM_Z     z layer only (tiles whose halo stays off the x and y slabs, all planes)
 constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2;
 
+// Full C-PML adjoint blocks copy the memory variables at their threads' cross
+// positions (two positions, six values each) one plane ahead with cp.async
+// into two plane slots of shared memory: [slot][position][value][thread].
+constexpr int MVBUF = 2 * 2 * 6 * (TX * TY);
+
 template <bool ADJ, int PM> struct VelCfg {
     static constexpr bool PML = PM != PM_NONE, PXY = PM == PM_FULL;
     // stage boxes 0..5: sigma (forward) or Q (adjoint), Voigt order; 6 rho,
@@ -65,7 +70,8 @@ template <bool ADJ, int PM> struct VelCfg {
     static constexpr int NB = 8;
     static constexpr int BRHO = 6, BALPHA = 7;
     static constexpr int NDER = (ADJ && PXY) ? 1 : 0;
-    static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
+    static constexpr int MV = (ADJ && PXY) ? MVBUF : 0;  // floats of the memory-variable buffer
+    static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) { return b < 6 ? TM_S0 + b : (b == BRHO ? TM_RHO : TM_ALPHA); }
 };
 
@@ -77,8 +83,9 @@ template <bool ADJ, int PM> struct StrCfg {
     // the layers, in three extra boxes.
     static constexpr int NB = 5;
     static constexpr int NDER = (ADJ && PXY) ? 3 : 0;
+    static constexpr int MV = (ADJ && PXY) ? MVBUF : 0;  // floats of the memory-variable buffer
     static constexpr int BLAM = 3, BMU = 4;
-    static constexpr size_t SMEM = (size_t)(D * NB + NDER) * BOXS * sizeof(float) + D * sizeof(uint64_t);
+    static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : (b == 3 ? TM_LAM : TM_MU); }
 };
 
@@ -320,7 +327,8 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     const int pfirst = zc0 - 2, plast = zc1 + 1;
     const Ring ring{sm, Cfg::NB, pfirst};
     float* der = sm + (size_t)D * Cfg::NB * BOXS;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)(D * Cfg::NB + Cfg::NDER) * BOXS);
+    float* mvb = der + (size_t)Cfg::NDER * BOXS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(mvb + Cfg::MV);
     const int o = (ty + OY) * BW + tx + OX;
     const float dt = p.dt, h = p.inv_dx;
     const int P = p.P;
@@ -412,27 +420,31 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const float chp[3] = {nhp[0], nhp[1], nhp[2]};
         prefetch(z + 1);
         prefetch_heads(pl + 1);
-        // full C-PML adjoint: memory variables psi^ at the cross positions of plane z
-        float dps[2][6];
+        // full C-PML adjoint: copy psi^ at the cross positions of plane z + 1
+        // into its buffer slot; the slot of plane z (copied one visit ago) is
+        // complete after the wait
         if constexpr (ADJ && PXY) {
+            const int zn = z + 1;
+            if (zn >= zc0 && zn < zc1) {
+                float* dst = mvb + (size_t)(zn & 1) * 12 * NT + tid;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-#pragma unroll
-                for (int t = 0; t < 6; ++t) dps[k][t] = 0.f;
-                if (!out) continue;
-                if (cpm.sx[k] >= 0) {
-                    const unsigned si = (unsigned)z * p.ny * (2 * P + 1) + cpm.sx[k];
-                    dps[k][0] = p.psi[0][0][si];
-                    dps[k][1] = p.psi[1][0][si];
-                    dps[k][2] = p.psi[2][0][si];
-                }
-                if (cpm.sy[k] >= 0) {
-                    const unsigned si = (unsigned)z * (2 * P + 1) * p.nx + cpm.sy[k];
-                    dps[k][3] = p.psi[1][1][si];
-                    dps[k][4] = p.psi[0][1][si];
-                    dps[k][5] = p.psi[2][1][si];
+                for (int k = 0; k < 2; ++k) {
+                    if (cpm.sx[k] >= 0) {
+                        const unsigned si = (unsigned)zn * p.ny * (2 * P + 1) + cpm.sx[k];
+                        cp_async_4(dst + (k * 6 + 0) * NT, p.psi[0][0] + si);
+                        cp_async_4(dst + (k * 6 + 1) * NT, p.psi[1][0] + si);
+                        cp_async_4(dst + (k * 6 + 2) * NT, p.psi[2][0] + si);
+                    }
+                    if (cpm.sy[k] >= 0) {
+                        const unsigned si = (unsigned)zn * (2 * P + 1) * p.nx + cpm.sy[k];
+                        cp_async_4(dst + (k * 6 + 3) * NT, p.psi[1][1] + si);
+                        cp_async_4(dst + (k * 6 + 4) * NT, p.psi[0][1] + si);
+                        cp_async_4(dst + (k * 6 + 5) * NT, p.psi[2][1] + si);
+                    }
                 }
             }
+            cp_async_commit();
+            cp_async_wait<1>();
         }
         const int kk = pl - pfirst;
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
@@ -487,17 +499,18 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                         const float q11 = sz[q], q22 = sz[BOXS + q], q23 = sz[3 * BOXS + q];
                         const float q13 = sz[4 * BOXS + q], q12 = sz[5 * BOXS + q];
                         float f11 = q11, f21 = q12, f31 = q13, f22 = q22, f12 = q12, f32 = q23;
+                        const float* mv = mvb + (size_t)((z & 1) * 12 + k * 6) * NT + tid;
                         if (cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
-                            f11 += t[0] * (dps[k][0] + t[1] * q11);
-                            f21 += t[2] * (dps[k][1] + t[3] * q12);
-                            f31 += t[2] * (dps[k][2] + t[3] * q13);
+                            f11 += t[0] * (mv[0] + t[1] * q11);
+                            f21 += t[2] * (mv[NT] + t[3] * q12);
+                            f31 += t[2] * (mv[2 * NT] + t[3] * q13);
                         }
                         if (cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            f22 += t[0] * (dps[k][3] + t[1] * q22);
-                            f12 += t[2] * (dps[k][4] + t[3] * q12);
-                            f32 += t[2] * (dps[k][5] + t[3] * q23);
+                            f22 += t[0] * (mv[3 * NT] + t[1] * q22);
+                            f12 += t[2] * (mv[4 * NT] + t[3] * q12);
+                            f32 += t[2] * (mv[5 * NT] + t[3] * q23);
                         }
                         if (f & CP_XB) {
                             szw[q] = f11;
@@ -554,12 +567,14 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
             drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
+            if constexpr (ADJ && PXY) cp_async_wait<0>();
             return false;
         }
         if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
     }
     // every issued plane has been waited for: retire the barriers so that a
     // persistent block can initialise them again for its next work item
+    if constexpr (ADJ && PXY) cp_async_wait<0>();
     if (tid == 0)
         for (int s = 0; s < D; ++s) mbar_inval(&bar[s]);
     return true;
@@ -585,7 +600,8 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     const int pfirst = zc0 - 2, plast = zc1 + 1;
     const Ring ring{sm, Cfg::NB, pfirst};
     float* der = sm + (size_t)D * Cfg::NB * BOXS;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)(D * Cfg::NB + Cfg::NDER) * BOXS);
+    float* mvb = der + (size_t)Cfg::NDER * BOXS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(mvb + Cfg::MV);
     const int o = (ty + OY) * BW + tx + OX;
     const float dt = p.dt, h = p.inv_dx;
     const int P = p.P;
@@ -679,27 +695,31 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         const float chp[3] = {nhp[0], nhp[1], nhp[2]};
         prefetch(z + 1);
         prefetch_heads(pl + 1);
-        // full C-PML adjoint: memory variables phi~ at the cross positions of plane z
-        float dph[2][6];
+        // full C-PML adjoint: copy phi~ at the cross positions of plane z + 1
+        // into its buffer slot; the slot of plane z (copied one visit ago) is
+        // complete after the wait
         if constexpr (ADJ && PXY) {
+            const int zn = z + 1;
+            if (zn >= zc0 && zn < zc1) {
+                float* dst = mvb + (size_t)(zn & 1) * 12 * NT + tid;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-#pragma unroll
-                for (int t = 0; t < 6; ++t) dph[k][t] = 0.f;
-                if (!out) continue;
-                if (cpm.sx[k] >= 0) {
-                    const unsigned si = (unsigned)z * p.ny * (2 * P + 1) + cpm.sx[k];
-                    dph[k][0] = p.phi[0][0][si];
-                    dph[k][1] = p.phi[1][0][si];
-                    dph[k][2] = p.phi[2][0][si];
-                }
-                if (cpm.sy[k] >= 0) {
-                    const unsigned si = (unsigned)z * (2 * P + 1) * p.nx + cpm.sy[k];
-                    dph[k][3] = p.phi[1][1][si];
-                    dph[k][4] = p.phi[0][1][si];
-                    dph[k][5] = p.phi[2][1][si];
+                for (int k = 0; k < 2; ++k) {
+                    if (cpm.sx[k] >= 0) {
+                        const unsigned si = (unsigned)zn * p.ny * (2 * P + 1) + cpm.sx[k];
+                        cp_async_4(dst + (k * 6 + 0) * NT, p.phi[0][0] + si);
+                        cp_async_4(dst + (k * 6 + 1) * NT, p.phi[1][0] + si);
+                        cp_async_4(dst + (k * 6 + 2) * NT, p.phi[2][0] + si);
+                    }
+                    if (cpm.sy[k] >= 0) {
+                        const unsigned si = (unsigned)zn * (2 * P + 1) * p.nx + cpm.sy[k];
+                        cp_async_4(dst + (k * 6 + 3) * NT, p.phi[1][1] + si);
+                        cp_async_4(dst + (k * 6 + 4) * NT, p.phi[0][1] + si);
+                        cp_async_4(dst + (k * 6 + 5) * NT, p.phi[2][1] + si);
+                    }
                 }
             }
+            cp_async_commit();
+            cp_async_wait<1>();
         }
         const int kk = pl - pfirst;
         const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
@@ -755,17 +775,18 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                         const int q = cross.q[k];
                         const float wx = sz[q], wy = sz[BOXS + q], wz = sz[2 * BOXS + q];
                         float exx = wx, eyx = wy, ezx = wz, eyy = wy, exy = wx, ezy = wz;
+                        const float* mv = mvb + (size_t)((z & 1) * 12 + k * 6) * NT + tid;
                         if (cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
-                            exx += t[2] * (dph[k][0] + t[3] * wx);
-                            eyx += t[0] * (dph[k][1] + t[1] * wy);
-                            ezx += t[0] * (dph[k][2] + t[1] * wz);
+                            exx += t[2] * (mv[0] + t[3] * wx);
+                            eyx += t[0] * (mv[NT] + t[1] * wy);
+                            ezx += t[0] * (mv[2 * NT] + t[1] * wz);
                         }
                         if (cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            eyy += t[2] * (dph[k][3] + t[3] * wy);
-                            exy += t[0] * (dph[k][4] + t[1] * wx);
-                            ezy += t[0] * (dph[k][5] + t[1] * wz);
+                            eyy += t[2] * (mv[3 * NT] + t[3] * wy);
+                            exy += t[0] * (mv[4 * NT] + t[1] * wx);
+                            ezy += t[0] * (mv[5 * NT] + t[1] * wz);
                         }
                         if (f & CP_XB) {
                             szw[q] = exx;
@@ -857,12 +878,14 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
             drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
+            if constexpr (ADJ && PXY) cp_async_wait<0>();
             return false;
         }
         if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
     }
     // every issued plane has been waited for: retire the barriers so that a
     // persistent block can initialise them again for its next work item
+    if constexpr (ADJ && PXY) cp_async_wait<0>();
     if (tid == 0)
         for (int s = 0; s < D; ++s) mbar_inval(&bar[s]);
     return true;
@@ -871,9 +894,23 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 // ===========================================================================
 // kernels: one grid (single instance) and persistent (many instances)
 // ===========================================================================
+// Minimum resident blocks per SM of each instantiation (register budget)
+// (0: no minimum; the velocity family is limited by its shared memory)
+template <bool STR, bool ADJ, int PM>
+constexpr int min_blocks() {
+    return !STR ? 0 : (PM == PM_NONE ? 1 : (PM == PM_Z && !ADJ ? 4 : 3));
+}
+// the persistent kernels read their parameters from shared memory, which
+// costs registers: give their velocity-family C-PML bodies an explicit budget
+template <bool STR, bool ADJ, int PM>
+constexpr int multi_min_blocks() {
+    return !STR ? (PM == PM_FULL ? (ADJ ? 2 : 3) : min_blocks<STR, ADJ, PM>()) : (PM == PM_NONE ? 4 : 3);
+}
+
 template <bool ADJ, int PM>
-__global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
-                                                  int* err) {
+__global__ void __launch_bounds__(NT, (min_blocks<false, ADJ, PM>())) k_vel_tiled(StepParams p,
+                                                                                 const __grid_constant__ TmaSet tm,
+                                                                                 RegionList rl, int* err) {
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1;
     locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
@@ -881,50 +918,60 @@ __global__ void __launch_bounds__(NT) k_vel_tiled(StepParams p, const __grid_con
 }
 
 template <bool ADJ, int PM>
-__global__ void __launch_bounds__(NT, PM == PM_NONE ? 1 : (PM == PM_Z && !ADJ ? 4 : 3)) k_str_tiled(StepParams p, const __grid_constant__ TmaSet tm, RegionList rl,
-                                                  int* err) {
+__global__ void __launch_bounds__(NT, (min_blocks<true, ADJ, PM>())) k_str_tiled(StepParams p,
+                                                                                const __grid_constant__ TmaSet tm,
+                                                                                RegionList rl, int* err) {
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1;
     locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
     str_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
-// Persistent multi-instance half steps: a fixed grid walks the work items of
-// every unfinished instance of the table (block b takes items b, b + grid,
-// ...), forward and adjoint instances alike.  STR selects the stress family.
-template <bool STR, int PM>
-__global__ void __launch_bounds__(NT, PM == PM_Z ? 3 : 1) k_multi(const MultiTable* __restrict__ T, int* err) {
+// Persistent multi-instance half steps: a fixed grid works through the work
+// items of every unfinished instance of one direction in the table; each block
+// takes the next item from an atomic counter (zeroed before the launch), so
+// items of different cost (frame, z-slab and interior tiles of grids of any
+// size) balance across the blocks.  STR selects the stress family, ADJ the
+// direction: forward instances come first in the table, adjoint ones after
+// them, so each kernel carries one body and the register budget of its
+// single-grid twin.
+template <bool STR, bool ADJ, int PM>
+__global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_multi(const MultiTable* __restrict__ T,
+                                                                                 int* err, int* next) {
     extern __shared__ __align__(128) float sm[];
     __shared__ StepParams sp;
+    __shared__ int s_item;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const int n = T->n_inst;
+    const int i0 = ADJ ? T->n_fwd : 0, i1 = ADJ ? T->n_inst : T->n_fwd;
     const int* pre = PM == PM_FULL ? T->pre_outer : (PM == PM_Z ? T->pre_zslab : T->pre_inner);
-    const int total = pre[n];
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        int i = 0;
-        while (i + 1 < n && item >= pre[i + 1]) ++i;
+    const int first = pre[i0], total = pre[i1];
+    for (;;) {
+        __syncthreads();  // the previous item is finished with s_item and sp
+        if (tid == 0) s_item = first + atomicAdd(next, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) return;
+        int i = i0;
+        while (i + 1 < i1 && item >= pre[i + 1]) ++i;
         const InstDev& I = T->inst[i];
         if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
         int tile_x, tile_y, zc0, zc1;
         locate(PM == PM_FULL ? I.outer : (PM == PM_Z ? I.zslab : I.inner), item - pre[i], tile_x, tile_y, zc0, zc1);
-        // a work item must lie inside its instance's grid; otherwise record
-        // the inconsistency and touch nothing
+        // a work item must lie inside its instance's grid and the instance
+        // must be of this kernel's direction; otherwise record the
+        // inconsistency and touch nothing
         if (tile_x < 0 || tile_x * TX >= I.p.nx || tile_y < 0 || tile_y * TY >= I.p.ny || zc0 < 0 || zc0 >= zc1 ||
-            zc1 > I.p.nz) {
+            zc1 > I.p.nz || (I.adj != 0) != ADJ) {
             if (tid == 0) atomicExch(err, 2);
             continue;
         }
-        __syncthreads();
         for (int w = tid; w < (int)(sizeof(StepParams) / sizeof(int)); w += NT)
             reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&I.p)[w];
         if (tid == 0)
             for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
         __syncthreads();
-        bool ok;
-        if (STR) ok = I.adj ? str_body<true, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
-                            : str_body<false, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
-        else ok = I.adj ? vel_body<true, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
-                        : vel_body<false, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+        const bool ok = STR ? str_body<ADJ, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
+                            : vel_body<ADJ, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
         if (!ok) return;
     }
 }
@@ -1132,37 +1179,41 @@ static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, con
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
-template <bool STR, int PM>
+template <bool STR, bool ADJ, int PM>
 static size_t multi_smem() {
-    return STR ? std::max(StrCfg<false, PM>::SMEM, StrCfg<true, PM>::SMEM)
-               : std::max(VelCfg<false, PM>::SMEM, VelCfg<true, PM>::SMEM);
+    return STR ? StrCfg<ADJ, PM>::SMEM : VelCfg<ADJ, PM>::SMEM;
 }
 
-template <bool STR, int PM>
+template <bool STR, bool ADJ, int PM>
 static int multi_grid() {
     static int grid[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!grid[dev]) grid[dev] = (int)device_slots((const void*)k_multi<STR, PM>, multi_smem<STR, PM>(), dev);
+    if (!grid[dev])
+        grid[dev] = (int)device_slots((const void*)k_multi<STR, ADJ, PM>, multi_smem<STR, ADJ, PM>(), dev);
     return grid[dev];
 }
 
-template <bool STR, int PM>
-static void launch_multi(const MultiTable* dT, int* err, cudaStream_t st) {
-    k_multi<STR, PM><<<multi_grid<STR, PM>(), dim3(TX, TY, 1), multi_smem<STR, PM>(), st>>>(dT, err);
+template <bool STR, bool ADJ, int PM>
+static void launch_multi(const MultiTable* dT, int* err, int* next, cudaStream_t st) {
+    k_multi<STR, ADJ, PM>
+        <<<multi_grid<STR, ADJ, PM>(), dim3(TX, TY, 1), multi_smem<STR, ADJ, PM>(), st>>>(dT, err, next);
 }
 
-void launch_multi_step_half(bool str, const MultiTable* dT, int* err, cudaStream_t st) {
-    if (str) {
-        launch_multi<true, PM_FULL>(dT, err, st);
-        launch_multi<true, PM_Z>(dT, err, st);
-        launch_multi<true, PM_NONE>(dT, err, st);
-    } else {
-        launch_multi<false, PM_FULL>(dT, err, st);
-        launch_multi<false, PM_Z>(dT, err, st);
-        launch_multi<false, PM_NONE>(dT, err, st);
-    }
+template <bool STR>
+static void launch_multi_family(const MultiTable* dT, int* err, int* next, cudaStream_t st) {
+    launch_multi<STR, false, PM_FULL>(dT, err, next + 0, st);
+    launch_multi<STR, true, PM_FULL>(dT, err, next + 1, st);
+    launch_multi<STR, false, PM_Z>(dT, err, next + 2, st);
+    launch_multi<STR, true, PM_Z>(dT, err, next + 3, st);
+    launch_multi<STR, false, PM_NONE>(dT, err, next + 4, st);
+    launch_multi<STR, true, PM_NONE>(dT, err, next + 5, st);
+}
+
+void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st) {
+    if (str) launch_multi_family<true>(dT, err, next, st);
+    else launch_multi_family<false>(dT, err, next, st);
 }
 
 // Region plan of one instance for the persistent kernels: z chunks of about

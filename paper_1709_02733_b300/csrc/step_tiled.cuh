@@ -43,6 +43,7 @@ struct alignas(128) InstDev {
 constexpr int kMaxInst = 64;
 struct MultiTable {
     int n_inst;
+    int n_fwd;                     // instances [0, n_fwd) are forward, the rest adjoint
     int pre_inner[kMaxInst + 1];   // first work item of each instance
     int pre_zslab[kMaxInst + 1];
     int pre_outer[kMaxInst + 1];
@@ -61,7 +62,10 @@ struct SplitStreams {
 };
 void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
 void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
-// persistent multi-instance half step (str = stress family) over a device table
-void launch_multi_step_half(bool str, const MultiTable* dT, int* err, cudaStream_t st);
+// persistent multi-instance half step (str = stress family) over a device
+// table: six launches (two directions x three region kinds), launch k taking
+// its work items from the counter next[k], which must be zero beforehand
+constexpr int kMultiLaunches = 6;
+void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st);
 void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& zslab,
                            int& nzslab, RegionList& outer, int& nouter);

@@ -2,6 +2,10 @@
 
     python -m paper_1709_02733_b300.profiling launches <ncu.csv>
         per-kernel launches, device time and share (markdown table)
+    python -m paper_1709_02733_b300.profiling fullset <raw.csv>
+        key counters of a full-set capture (``ncu -i rep --page raw --csv``):
+        duration, DRAM bytes and throughput, occupancy, issue activity and the
+        top warp-stall reasons of every captured launch (markdown)
     python -m paper_1709_02733_b300.profiling traffic <ncu.csv> <out.json> [--scale F]
         DRAM bytes (read + write) per half step of each kernel role, as read by
         bench.py for the roofline "traffic" field; F scales a capture of a
@@ -86,9 +90,67 @@ def traffic(path, scale: float = 1.0) -> dict:
     return {role: {"dram_bytes_per_launch": b, "source_sha": sha, "scale": scale} for role, b in acc.items()}
 
 
+FULLSET_KEYS = [
+    ("gpu__time_duration.sum", "duration [us]", "us"),
+    ("dram__bytes_read.sum", "DRAM read [MB]", "MB"),
+    ("dram__bytes_write.sum", "DRAM write [MB]", "MB"),
+    ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "DRAM throughput [% of peak]", 1.0),
+    ("launch__registers_per_thread", "registers / thread", 1.0),
+    ("launch__occupancy_limit_registers", "blocks / SM (register limit)", 1.0),
+    ("launch__occupancy_limit_shared_mem", "blocks / SM (shared-memory limit)", 1.0),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active [% of peak]", 1.0),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active [% of peak]", 1.0),
+    ("smsp__inst_executed.sum", "warp instructions [M]", 1e-6),
+    ("lts__t_sector_hit_rate.pct", "L2 hit rate [%]", 1.0),
+    ("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active", "tensor pipe active [%]", 1.0),
+]
+
+
+def fullset_table(path) -> str:
+    """Markdown summary of a raw-page CSV export (one row per launch)."""
+    rows = [r for r in csv.reader(open(path)) if len(r) > 5]
+    hdr, units, data = rows[0], rows[1], rows[2:]
+    col = {h: i for i, h in enumerate(hdr)}
+    to_us = {"nsecond": 1e-3, "usecond": 1.0, "msecond": 1e3, "second": 1e6}
+    to_mb = {"byte": 1e-6, "Kbyte": 1e-3, "Mbyte": 1.0, "Gbyte": 1e3}
+
+    def num(r, k):
+        try:
+            return float(r[col[k]].replace(",", ""))
+        except (KeyError, ValueError):
+            return None
+
+    def factor(k, scale):
+        u = units[col[k]] if k in col else ""
+        if scale == "us":
+            return to_us.get(u, 1.0)
+        if scale == "MB":
+            return to_mb.get(u, 1.0)
+        return scale
+
+    names = [r[col["Kernel Name"]].split("(")[0].strip() for r in data]
+    out = ["| counter | " + " | ".join(f"`{n}`" for n in names) + " |", "|---|" + "---|" * len(names)]
+    for key, label, scale in FULLSET_KEYS:
+        vals = [num(r, key) for r in data]
+        if all(v is None for v in vals):
+            continue
+        f = factor(key, scale)
+        out.append(f"| {label} | " + " | ".join("" if v is None else f"{v * f:.4g}" for v in vals) + " |")
+    stall = [h for h in hdr if h.startswith("smsp__average_warps_issue_stalled_")
+             and h.endswith("_per_issue_active.ratio")]
+    for r, n in zip(data, names):
+        top = sorted(((num(r, h) or 0.0, h[len("smsp__average_warps_issue_stalled_"):-len("_per_issue_active.ratio")])
+                      for h in stall), reverse=True)[:5]
+        out.append("")
+        out.append(f"`{n}` top stall reasons (warps per issue): " + ", ".join(f"{k} {v:.2f}" for v, k in top))
+    return "\n".join(out)
+
+
 def main(argv):
     if len(argv) >= 2 and argv[0] == "launches":
         print(launch_table(argv[1]))
+    elif len(argv) >= 2 and argv[0] == "fullset":
+        print(fullset_table(argv[1]))
     elif len(argv) >= 3 and argv[0] == "traffic":
         scale = float(argv[argv.index("--scale") + 1]) if "--scale" in argv else 1.0
         with open(argv[2], "w") as f:
