@@ -898,13 +898,13 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 // (0: no minimum; the velocity family is limited by its shared memory)
 template <bool STR, bool ADJ, int PM>
 constexpr int min_blocks() {
-    return !STR ? 0 : (PM == PM_NONE ? 1 : (PM == PM_Z && !ADJ ? 4 : 3));
+    return !STR ? 0 : (PM == PM_NONE ? 1 : (PM == PM_Z ? (ADJ ? 3 : 4) : 2));
 }
 // the persistent kernels read their parameters from shared memory, which
 // costs registers: give their velocity-family C-PML bodies an explicit budget
 template <bool STR, bool ADJ, int PM>
 constexpr int multi_min_blocks() {
-    return !STR ? (PM == PM_FULL ? (ADJ ? 2 : 3) : min_blocks<STR, ADJ, PM>()) : (PM == PM_NONE ? 4 : 3);
+    return !STR ? (PM == PM_FULL ? (ADJ ? 2 : 3) : min_blocks<STR, ADJ, PM>()) : (PM == PM_NONE ? 4 : PM == PM_Z ? 3 : 2);
 }
 
 template <bool ADJ, int PM>
