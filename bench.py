@@ -352,8 +352,8 @@ def run_ours(args):
                 "frac": achieved / pk["hbm_gbs"], "peak_source": which + " (hbm_gbs, STREAM-style copy)",
                 "traffic": traffic_for(dom), "algorithmic_bytes_per_launch": alg,
                 "avg_launch_ms": avg_s * 1e3, "bytes_per_update": alg / d.N}
-    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
-    gpu_launches = int(sum(v[0] for v in prof.values()))
+    kernels = {k: {"invocations": v[0], "ms": v[1]} for k, v in prof.items() if v[0] and k != "all"}
+    gpu_launches = int(prof["all"][0])  # kernel launches in the timed region (a step half is 3 kernels)
 
     # end to end through the host-pointer C-ABI calls (pinned host buffers)
     e2e = None

@@ -200,6 +200,7 @@ int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const flo
 #define PACT_K_SOURCE 6       /* source tau                                       */
 #define PACT_K_READOUT 7      /* read-out tau^T                                   */
 #define PACT_NKIND 8
+#define PACT_K_ALL 8          /* pact_profile_read only: every kernel launch     */
 
 /* Reset this handle's launch counters and, if enable != 0, start recording a
  * CUDA event after every kernel launch on the handle's stream (so a launch's
@@ -207,8 +208,11 @@ int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const flo
  * consecutive launches of one call).  Synchronises the stream. */
 int pact_profile(pact_handle h, int enable);
 
-/* Launches of one kernel role since pact_profile, and their summed device time
- * in milliseconds (0 if recording was off).  Synchronises the stream.
+/* Invocations of one kernel role since pact_profile (one step half of the
+ * role may launch up to three kernels: C-PML frame, z-slab planes, interior),
+ * and their summed device time in milliseconds (0 if recording was off).
+ * kind = PACT_K_ALL gives the number of kernel launches of all roles and the
+ * device time of all of them.  Synchronises the stream.
  * Errors: PACT_EINVAL (kind out of range or NULL output). */
 int pact_profile_read(pact_handle h, int kind, long long* launches, double* total_ms);
 

@@ -73,7 +73,8 @@ struct pact_grid {
     float* stage_b = nullptr;
     size_t stage_b_n = 0;
     // launch accounting and optional per-launch events (pact_profile)
-    long long launches[PACT_NKIND] = {};
+    long long launches[PACT_NKIND] = {};  // invocations of each role
+    long long kernels = 0;                 // kernel launches of all roles
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int> ev_kind;  // kind of the launch that ends at event i (-1: origin)
@@ -114,8 +115,11 @@ static int fail(pact_handle h, int code, const std::string& msg) {
 
 // Count a launch of `kind`; in profile mode record an event after it on the
 // stream, so that the launch's duration is the time since the previous event.
-static void mark(pact_handle h, int kind) {
-    if (kind >= 0) h->launches[kind]++;
+static void mark(pact_handle h, int kind, int nkernels = 1) {
+    if (kind >= 0) {
+        h->launches[kind]++;
+        h->kernels += nkernels;
+    }
     if (!h->prof) return;
     const size_t i = h->ev_kind.size();
     if (i >= h->ev_pool.size()) {
@@ -357,10 +361,8 @@ static void fwd_step(pact_handle h, const StepParams& p) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
     if (h->tiled) {
         const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join};
-        launch_vel_tiled(false, p, h->tm, err, ss);
-        mark(h, PACT_K_FWD_VELOCITY);
-        launch_str_tiled(false, p, h->tm, err, ss);
-        mark(h, PACT_K_FWD_STRESS);
+        mark(h, PACT_K_FWD_VELOCITY, launch_vel_tiled(false, p, h->tm, err, ss));
+        mark(h, PACT_K_FWD_STRESS, launch_str_tiled(false, p, h->tm, err, ss));
     } else {
         launch_fwd_velocity(p, h->stream);
         mark(h, PACT_K_FWD_VELOCITY);
@@ -373,10 +375,8 @@ static void adj_step(pact_handle h, const StepParams& p) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
     if (h->tiled) {
         const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join};
-        launch_vel_tiled(true, p, h->tm, err, ss);
-        mark(h, PACT_K_ADJ_A);
-        launch_str_tiled(true, p, h->tm, err, ss);
-        mark(h, PACT_K_ADJ_B);
+        mark(h, PACT_K_ADJ_A, launch_vel_tiled(true, p, h->tm, err, ss));
+        mark(h, PACT_K_ADJ_B, launch_str_tiled(true, p, h->tm, err, ss));
     } else {
         launch_adj_a(p, h->stream);
         mark(h, PACT_K_ADJ_A);
@@ -411,11 +411,11 @@ static int run_adjoint(pact_handle h, const float* traces, float* image, int nst
     const RecTable r = make_rec(h);
     mark(h, -1);
     launch_inject(p, r, traces + (size_t)nsteps * h->L, h->stream);
-    mark(h, PACT_K_INJECT);
+    mark(h, PACT_K_INJECT, r.ncorner > 0);
     for (int m = nsteps; m >= 1; --m) {
         adj_step(h, p);
         launch_inject(p, r, traces + (size_t)(m - 1) * h->L, h->stream);
-        mark(h, PACT_K_INJECT);
+        mark(h, PACT_K_INJECT, r.ncorner > 0);
     }
     launch_readout(image, p, h->stream);
     mark(h, PACT_K_READOUT);
@@ -646,6 +646,7 @@ int pact_profile(pact_handle h, int enable) {
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
     for (int k = 0; k < PACT_NKIND; ++k) h->launches[k] = 0;
+    h->kernels = 0;
     h->ev_kind.clear();
     h->prof = enable != 0;
     return PACT_OK;
@@ -653,13 +654,13 @@ int pact_profile(pact_handle h, int enable) {
 
 int pact_profile_read(pact_handle h, int kind, long long* launches, double* total_ms) {
     if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
-    if (kind < 0 || kind >= PACT_NKIND || !launches || !total_ms) return fail(h, PACT_EINVAL, "bad kind or NULL");
+    if (kind < 0 || kind > PACT_K_ALL || !launches || !total_ms) return fail(h, PACT_EINVAL, "bad kind or NULL");
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
-    *launches = h->launches[kind];
+    *launches = kind == PACT_K_ALL ? h->kernels : h->launches[kind];
     double ms = 0.0;
     for (size_t i = 1; i < h->ev_kind.size(); ++i) {
-        if (h->ev_kind[i] != kind) continue;
+        if (kind == PACT_K_ALL ? h->ev_kind[i] < 0 : h->ev_kind[i] != kind) continue;
         float t = 0.0f;
         CK(h, cudaEventElapsedTime(&t, h->ev_pool[i - 1], h->ev_pool[i]));
         ms += t;

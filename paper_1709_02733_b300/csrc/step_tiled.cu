@@ -1133,7 +1133,7 @@ LaunchPlan plan_for(int family, const StepParams& p) {
 // The frame launch goes to `aux` (when given) between a fork and a join
 // event, so that it overlaps the interior launch on `st`.
 template <bool ADJ>
-static void launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
+static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 1 : 0, p);
     const dim3 blk(TX, TY, 1);
     const bool split = ss.aux && (L.outer_blocks || L.zslab_blocks) && L.inner_blocks;
@@ -1153,10 +1153,11 @@ static void launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, con
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
     }
+    return (L.outer_blocks > 0) + (L.zslab_blocks > 0) + (L.inner_blocks > 0);
 }
 
 template <bool ADJ>
-static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
+static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 3 : 2, p);
     const dim3 blk(TX, TY, 1);
     const bool split = ss.aux && (L.outer_blocks || L.zslab_blocks) && L.inner_blocks;
@@ -1176,6 +1177,7 @@ static void launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, con
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
     }
+    return (L.outer_blocks > 0) + (L.zslab_blocks > 0) + (L.inner_blocks > 0);
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
@@ -1236,14 +1238,12 @@ void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& 
     nouter = rechunk(outer);
 }
 
-void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
-    if (adj) launch_vel_impl<true>(p, tm, err, ss);
-    else launch_vel_impl<false>(p, tm, err, ss);
+int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
+    return adj ? launch_vel_impl<true>(p, tm, err, ss) : launch_vel_impl<false>(p, tm, err, ss);
 }
 
-void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
-    if (adj) launch_str_impl<true>(p, tm, err, ss);
-    else launch_str_impl<false>(p, tm, err, ss);
+int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
+    return adj ? launch_str_impl<true>(p, tm, err, ss) : launch_str_impl<false>(p, tm, err, ss);
 }
 
 // Tensor maps: one 3-D float32 map per array, box 40 x 13 x 1, zero fill.

@@ -60,8 +60,9 @@ struct SplitStreams {
     cudaStream_t aux;
     cudaEvent_t fork, join;
 };
-void launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
-void launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
+// both return the number of kernels launched
+int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
+int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
 // persistent multi-instance half step (str = stress family) over a device
 // table: six launches (two directions x three region kinds), launch k taking
 // its work items from the counter next[k], which must be zero beforehand

@@ -262,9 +262,10 @@ class Grid:
     profile = pact_profile
 
     def pact_profile_read(self):
-        """{kind: (launches, device_ms)} since the last pact_profile call."""
+        """{kind: (invocations, device_ms)} since the last pact_profile call,
+        plus "all": (kernel launches of every role, device_ms)."""
         out = {}
-        for k, name in enumerate(KINDS):
+        for k, name in enumerate(KINDS + ["all"]):
             n, ms = ctypes.c_longlong(0), ctypes.c_double(0.0)
             _check(self.lib.pact_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)), self._h)
             out[name] = (int(n.value), float(ms.value))
