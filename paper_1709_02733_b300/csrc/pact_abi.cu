@@ -89,8 +89,8 @@ struct pact_grid {
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
     const float* sv_in = nullptr;
     float* sv_out = nullptr;
-    RegionList sv_inner{}, sv_zslab{}, sv_outer{};
-    int sv_ninner = 0, sv_nzslab = 0, sv_nouter = 0;
+    RegionList sv_inner{}, sv_outer{};
+    int sv_ninner = 0, sv_nouter = 0;
     std::string err;
 };
 
@@ -691,7 +691,7 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
         if (nsteps == 0) launch_readout(out, p, h->stream);
     }
-    plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_zslab, h->sv_nzslab, h->sv_outer, h->sv_nouter);
+    plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_outer, h->sv_nouter);
     h->sv_active = nsteps > 0;
     CK(h, cudaGetLastError());
     return PACT_OK;
@@ -704,7 +704,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
     if (!T) T = new (std::nothrow) MultiTable();
     if (!T) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
     int dev = -1, ni = 0;
-    T->pre_inner[0] = T->pre_zslab[0] = T->pre_outer[0] = 0;
+    T->pre_inner[0] = T->pre_outer[0] = 0;
     // forward instances first, then adjoint ones (each persistent kernel
     // serves one direction)
     for (int pass = 0; pass < 2; ++pass) {
@@ -718,7 +718,6 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             e.tm = h->tm;
             e.p = make_params(h);
             e.inner = h->sv_inner;
-            e.zslab = h->sv_zslab;
             e.outer = h->sv_outer;
             e.rec = make_rec(h);
             e.src = h->sv_adj ? h->sv_in : nullptr;
@@ -728,7 +727,6 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             e.nsteps = h->sv_nsteps;
             e.L = h->L;
             T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
-            T->pre_zslab[ni + 1] = T->pre_zslab[ni] + h->sv_nzslab;
             T->pre_outer[ni + 1] = T->pre_outer[ni] + h->sv_nouter;
             ++ni;
         }

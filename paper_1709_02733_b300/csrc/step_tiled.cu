@@ -50,10 +50,12 @@ constexpr int BOXS = 544;       // box stride in floats (2176 B, 128-B aligned)
 constexpr int OX = 4, OY = 2;   // own point offset inside the box
 constexpr int D = 4;            // stage ring depth (planes)
 
-// C-PML code compiled into a kernel instantiation:
+// C-PML code of a work-item body:
 //   PM_NONE  no layer (tiles and planes whose reach stays off every slab, or P = 0)
 //   PM_FULL  x, y and z layers (tiles whose halo touches an x or y slab)
-//   PM_Z     z layer only (tiles whose halo stays off the x and y slabs, all planes)
+//   PM_Z     z layer only (the other tiles, planes on the z slabs)
+// Two kernels per family and direction: the frame kernel (PM_FULL) and the
+// interior kernel (PM_NONE), whose blocks run the PM_NONE or the PM_Z body.
 constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2;
 
 // Full C-PML adjoint blocks copy the memory variables at their threads' cross
@@ -89,7 +91,8 @@ template <bool ADJ, int PM> struct StrCfg {
     __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : (b == 3 ? TM_LAM : TM_MU); }
 };
 
-__device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1) {
+__device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1,
+                                       int& kind) {
     int r = 0;
     while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
     const Region& R = rl.r[r];
@@ -100,6 +103,7 @@ __device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x,
     tile_y = R.ty0 + t / ntx;
     zc0 = R.za + ch * R.zc;
     zc1 = min(zc0 + R.zc, R.zb);
+    kind = R.kind;
 }
 
 // differences on a box (own index o) and on a register queue
@@ -898,13 +902,31 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 // (0: no minimum; the velocity family is limited by its shared memory)
 template <bool STR, bool ADJ, int PM>
 constexpr int min_blocks() {
-    return !STR ? 0 : (PM == PM_NONE ? 1 : (PM == PM_Z ? (ADJ ? 3 : 4) : 2));
+    return !STR ? 0 : (PM == PM_FULL ? 2 : 4);
 }
 // the persistent kernels read their parameters from shared memory, which
 // costs registers: give their velocity-family C-PML bodies an explicit budget
 template <bool STR, bool ADJ, int PM>
 constexpr int multi_min_blocks() {
-    return !STR ? (PM == PM_FULL ? (ADJ ? 2 : 3) : min_blocks<STR, ADJ, PM>()) : (PM == PM_NONE ? 4 : PM == PM_Z ? 3 : 2);
+    return !STR ? (PM == PM_FULL ? (ADJ ? 2 : 3) : 0) : (PM == PM_FULL ? 2 : (ADJ ? 4 : 3));
+}
+
+// One work item of a launch: the frame launch (PM_FULL) runs the full C-PML
+// body; the interior launch (PM_NONE) runs, per block, the body its region
+// asks for (z-slab regions: z-layer code only).
+template <bool ADJ, int PM>
+__device__ __forceinline__ bool vel_item(const StepParams& p, const CUtensorMap* maps, int kind, int tile_x,
+                                         int tile_y, int zc0, int zc1, int* err, float* sm) {
+    if constexpr (PM == PM_FULL) return vel_body<ADJ, PM_FULL>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    else if (kind == PM_Z) return vel_body<ADJ, PM_Z>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    else return vel_body<ADJ, PM_NONE>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+}
+template <bool ADJ, int PM>
+__device__ __forceinline__ bool str_item(const StepParams& p, const CUtensorMap* maps, int kind, int tile_x,
+                                         int tile_y, int zc0, int zc1, int* err, float* sm) {
+    if constexpr (PM == PM_FULL) return str_body<ADJ, PM_FULL>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    else if (kind == PM_Z) return str_body<ADJ, PM_Z>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    else return str_body<ADJ, PM_NONE>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
 template <bool ADJ, int PM>
@@ -912,9 +934,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<false, ADJ, PM>())) k_vel_tile
                                                                                  const __grid_constant__ TmaSet tm,
                                                                                  RegionList rl, int* err) {
     extern __shared__ __align__(128) float sm[];
-    int tile_x, tile_y, zc0, zc1;
-    locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
-    vel_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    int tile_x, tile_y, zc0, zc1, kind;
+    locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
+    vel_item<ADJ, PM>(p, tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
 template <bool ADJ, int PM>
@@ -922,9 +944,9 @@ __global__ void __launch_bounds__(NT, (min_blocks<true, ADJ, PM>())) k_str_tiled
                                                                                 const __grid_constant__ TmaSet tm,
                                                                                 RegionList rl, int* err) {
     extern __shared__ __align__(128) float sm[];
-    int tile_x, tile_y, zc0, zc1;
-    locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1);
-    str_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    int tile_x, tile_y, zc0, zc1, kind;
+    locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
+    str_item<ADJ, PM>(p, tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
 // Persistent multi-instance half steps: a fixed grid works through the work
@@ -943,7 +965,7 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
     __shared__ int s_item;
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = ADJ ? T->n_fwd : 0, i1 = ADJ ? T->n_inst : T->n_fwd;
-    const int* pre = PM == PM_FULL ? T->pre_outer : (PM == PM_Z ? T->pre_zslab : T->pre_inner);
+    const int* pre = PM == PM_FULL ? T->pre_outer : T->pre_inner;
     const int first = pre[i0], total = pre[i1];
     for (;;) {
         __syncthreads();  // the previous item is finished with s_item and sp
@@ -955,8 +977,8 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
         while (i + 1 < i1 && item >= pre[i + 1]) ++i;
         const InstDev& I = T->inst[i];
         if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
-        int tile_x, tile_y, zc0, zc1;
-        locate(PM == PM_FULL ? I.outer : (PM == PM_Z ? I.zslab : I.inner), item - pre[i], tile_x, tile_y, zc0, zc1);
+        int tile_x, tile_y, zc0, zc1, kind;
+        locate(PM == PM_FULL ? I.outer : I.inner, item - pre[i], tile_x, tile_y, zc0, zc1, kind);
         // a work item must lie inside its instance's grid and the instance
         // must be of this kernel's direction; otherwise record the
         // inconsistency and touch nothing
@@ -970,8 +992,8 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
         if (tid == 0)
             for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
         __syncthreads();
-        const bool ok = STR ? str_body<ADJ, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm)
-                            : vel_body<ADJ, PM>(sp, I.tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+        const bool ok = STR ? str_item<ADJ, PM>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)
+                            : vel_item<ADJ, PM>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
         if (!ok) return;
     }
 }
@@ -1007,11 +1029,11 @@ bool interior_tiles(const StepParams& p, int& txlo, int& txhi, int& tylo, int& t
     return txlo <= txhi && tylo <= tyhi;
 }
 
-int add_region(RegionList& rl, int tx0, int tx1, int ty0, int ty1, int za, int zb, int zc, int& blocks) {
+int add_region(RegionList& rl, int tx0, int tx1, int ty0, int ty1, int za, int zb, int zc, int kind, int& blocks) {
     if (tx0 >= tx1 || ty0 >= ty1 || za >= zb) return 0;
     zc = std::max(1, std::min(zc, zb - za));
     Region& r = rl.r[rl.n++];
-    r = {tx0, tx1, ty0, ty1, za, zb, zc, blocks};
+    r = {tx0, tx1, ty0, ty1, za, zb, zc, blocks, kind};
     const int chunks = (zb - za + zc - 1) / zc;
     blocks += (tx1 - tx0) * (ty1 - ty0) * chunks;
     return 1;
@@ -1035,42 +1057,45 @@ int chunk_planes(long tiles, int zlen, long slots) {
     return (zlen + best - 1) / best;
 }
 
-// Work regions of one half step: the interior tiles off the z slabs (no
-// layer code), the interior tiles on the z slabs (z-layer code) and the frame
-// of tiles around the interior ones (all planes; full C-PML code, up to four
-// rectangles).  With P = 0 every tile is interior and there are no slabs.
+// Work regions of one half step.  Interior launch: the interior tiles off
+// the z slabs (no layer code; long chunks, first) and on the z slabs (z-layer
+// code; one chunk per slab, last, so that they fill the launch's tail).
+// Frame launch: the tiles around the interior ones, all planes, full C-PML
+// code, up to four rectangles.  With P = 0 every tile is interior and there
+// are no slabs.
 void make_regions(const StepParams& p, long slots_inner, long slots_outer, RegionList& inner, int& inner_blocks,
-                  RegionList& zslab, int& zslab_blocks, RegionList& outer, int& outer_blocks) {
-    inner.n = zslab.n = outer.n = 0;
-    inner_blocks = zslab_blocks = outer_blocks = 0;
+                  RegionList& outer, int& outer_blocks) {
+    inner.n = outer.n = 0;
+    inner_blocks = outer_blocks = 0;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
     const int P = p.P;
     int txlo = 0, txhi = ntx - 1, tylo = 0, tyhi = nty - 1;
     if (P > 0 && !interior_tiles(p, txlo, txhi, tylo, tyhi)) {
-        add_region(outer, 0, ntx, 0, nty, 0, p.nz, chunk_planes((long)ntx * nty, p.nz, slots_outer), outer_blocks);
+        add_region(outer, 0, ntx, 0, nty, 0, p.nz, chunk_planes((long)ntx * nty, p.nz, slots_outer), PM_FULL,
+                   outer_blocks);
         return;
     }
     const long tiles = (long)(txhi + 1 - txlo) * (tyhi + 1 - tylo);
     const long frame = (long)ntx * nty - tiles;
     if (frame > 0) {
         const int zc = chunk_planes(frame, p.nz, slots_outer);
-        add_region(outer, 0, txlo, 0, nty, 0, p.nz, zc, outer_blocks);
-        add_region(outer, txhi + 1, ntx, 0, nty, 0, p.nz, zc, outer_blocks);
-        add_region(outer, txlo, txhi + 1, 0, tylo, 0, p.nz, zc, outer_blocks);
-        add_region(outer, txlo, txhi + 1, tyhi + 1, nty, 0, p.nz, zc, outer_blocks);
+        add_region(outer, 0, txlo, 0, nty, 0, p.nz, zc, PM_FULL, outer_blocks);
+        add_region(outer, txhi + 1, ntx, 0, nty, 0, p.nz, zc, PM_FULL, outer_blocks);
+        add_region(outer, txlo, txhi + 1, 0, tylo, 0, p.nz, zc, PM_FULL, outer_blocks);
+        add_region(outer, txlo, txhi + 1, tyhi + 1, nty, 0, p.nz, zc, PM_FULL, outer_blocks);
     }
-    const int za = P > 0 ? std::min(P, p.nz) : 0;               // planes [za, zb) are off the z slabs
+    const int za = P > 0 ? std::min(P, p.nz) : 0;  // planes [za, zb) are off the z slabs
     const int zb = P > 0 ? std::max(za, p.nz - P - 1) : p.nz;
-    add_region(zslab, txlo, txhi + 1, tylo, tyhi + 1, 0, za, za, zslab_blocks);
-    add_region(zslab, txlo, txhi + 1, tylo, tyhi + 1, zb, p.nz, p.nz - zb, zslab_blocks);
-    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, chunk_planes(tiles, zb - za, slots_inner),
+    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, chunk_planes(tiles, zb - za, slots_inner), PM_NONE,
                inner_blocks);
+    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, 0, za, za, PM_Z, inner_blocks);
+    add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, zb, p.nz, p.nz - zb, PM_Z, inner_blocks);
 }
 
 struct LaunchPlan {
     int dev, nx, ny, nz, P, family;
-    RegionList inner, zslab, outer;
-    int inner_blocks, zslab_blocks, outer_blocks;
+    RegionList inner, outer;
+    int inner_blocks, outer_blocks;
 };
 
 // kernel and dynamic shared memory of a family (0 vel fwd, 1 vel adj, 2 str
@@ -1086,10 +1111,10 @@ size_t fam_smem(int f) {
          : f == 2 ? StrCfg<false, PM>::SMEM : StrCfg<true, PM>::SMEM;
 }
 const void* fam_fn(int f, int pm) {
-    return pm == PM_FULL ? fam_fn<PM_FULL>(f) : pm == PM_Z ? fam_fn<PM_Z>(f) : fam_fn<PM_NONE>(f);
+    return pm == PM_FULL ? fam_fn<PM_FULL>(f) : fam_fn<PM_NONE>(f);
 }
 size_t fam_smem(int f, int pm) {
-    return pm == PM_FULL ? fam_smem<PM_FULL>(f) : pm == PM_Z ? fam_smem<PM_Z>(f) : fam_smem<PM_NONE>(f);
+    return pm == PM_FULL ? fam_smem<PM_FULL>(f) : fam_smem<PM_NONE>(f);
 }
 
 // resident blocks of a kernel on the whole device
@@ -1115,7 +1140,6 @@ LaunchPlan plan_for(int family, const StepParams& p) {
     }
     const long si = device_slots(fam_fn(family, PM_NONE), fam_smem(family, PM_NONE), dev);
     const long so = device_slots(fam_fn(family, PM_FULL), fam_smem(family, PM_FULL), dev);
-    device_slots(fam_fn(family, PM_Z), fam_smem(family, PM_Z), dev);  // sets its shared-memory limit
     LaunchPlan& L = plans[nplans % 32];
     L.dev = dev;
     L.family = family;
@@ -1123,7 +1147,7 @@ LaunchPlan plan_for(int family, const StepParams& p) {
     L.ny = p.ny;
     L.nz = p.nz;
     L.P = p.P;
-    make_regions(p, si, so, L.inner, L.inner_blocks, L.zslab, L.zslab_blocks, L.outer, L.outer_blocks);
+    make_regions(p, si, so, L.inner, L.inner_blocks, L.outer, L.outer_blocks);
     nplans = std::min(nplans + 1, 32);
     return L;
 }
@@ -1136,7 +1160,7 @@ template <bool ADJ>
 static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 1 : 0, p);
     const dim3 blk(TX, TY, 1);
-    const bool split = ss.aux && (L.outer_blocks || L.zslab_blocks) && L.inner_blocks;
+    const bool split = ss.aux && L.outer_blocks && L.inner_blocks;
     cudaStream_t so = ss.st;
     if (split) {
         cudaEventRecord(ss.fork, ss.st);
@@ -1145,22 +1169,20 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
     }
     if (L.outer_blocks)
         k_vel_tiled<ADJ, PM_FULL><<<L.outer_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.outer, err);
-    if (L.zslab_blocks)
-        k_vel_tiled<ADJ, PM_Z><<<L.zslab_blocks, blk, VelCfg<ADJ, PM_Z>::SMEM, so>>>(p, tm, L.zslab, err);
     if (L.inner_blocks)
         k_vel_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
     }
-    return (L.outer_blocks > 0) + (L.zslab_blocks > 0) + (L.inner_blocks > 0);
+    return (L.outer_blocks > 0) + (L.inner_blocks > 0);
 }
 
 template <bool ADJ>
 static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 3 : 2, p);
     const dim3 blk(TX, TY, 1);
-    const bool split = ss.aux && (L.outer_blocks || L.zslab_blocks) && L.inner_blocks;
+    const bool split = ss.aux && L.outer_blocks && L.inner_blocks;
     cudaStream_t so = ss.st;
     if (split) {
         cudaEventRecord(ss.fork, ss.st);
@@ -1169,15 +1191,13 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
     }
     if (L.outer_blocks)
         k_str_tiled<ADJ, PM_FULL><<<L.outer_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.outer, err);
-    if (L.zslab_blocks)
-        k_str_tiled<ADJ, PM_Z><<<L.zslab_blocks, blk, StrCfg<ADJ, PM_Z>::SMEM, so>>>(p, tm, L.zslab, err);
     if (L.inner_blocks)
         k_str_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
     }
-    return (L.outer_blocks > 0) + (L.zslab_blocks > 0) + (L.inner_blocks > 0);
+    return (L.outer_blocks > 0) + (L.inner_blocks > 0);
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
@@ -1207,10 +1227,8 @@ template <bool STR>
 static void launch_multi_family(const MultiTable* dT, int* err, int* next, cudaStream_t st) {
     launch_multi<STR, false, PM_FULL>(dT, err, next + 0, st);
     launch_multi<STR, true, PM_FULL>(dT, err, next + 1, st);
-    launch_multi<STR, false, PM_Z>(dT, err, next + 2, st);
-    launch_multi<STR, true, PM_Z>(dT, err, next + 3, st);
-    launch_multi<STR, false, PM_NONE>(dT, err, next + 4, st);
-    launch_multi<STR, true, PM_NONE>(dT, err, next + 5, st);
+    launch_multi<STR, false, PM_NONE>(dT, err, next + 2, st);
+    launch_multi<STR, true, PM_NONE>(dT, err, next + 3, st);
 }
 
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st) {
@@ -1220,9 +1238,9 @@ void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next,
 
 // Region plan of one instance for the persistent kernels: z chunks of about
 // `zc` planes so that work items of different instances are of similar size.
-void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& zslab,
-                           int& nzslab, RegionList& outer, int& nouter) {
-    make_regions(p, 1, 1, inner, ninner, zslab, nzslab, outer, nouter);
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
+                           int& nouter) {
+    make_regions(p, 1, 1, inner, ninner, outer, nouter);
     auto rechunk = [zc](RegionList& rl) {
         int blocks = 0;
         for (int k = 0; k < rl.n; ++k) {
@@ -1234,7 +1252,6 @@ void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& 
         return blocks;
     };
     ninner = rechunk(inner);
-    nzslab = rechunk(zslab);
     nouter = rechunk(outer);
 }
 

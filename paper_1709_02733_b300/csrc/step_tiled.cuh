@@ -13,9 +13,10 @@ struct TmaSet {
 };
 
 // A rectangular block of work: tiles [tx0,tx1) x [ty0,ty1), planes [za,zb)
-// in chunks of zc planes; bstart = first block (work item) of the region.
+// in chunks of zc planes; bstart = first block (work item) of the region;
+// kind = the C-PML code its blocks run (0 none, 1 full, 2 z layer only).
 struct Region {
-    int tx0, tx1, ty0, ty1, za, zb, zc, bstart;
+    int tx0, tx1, ty0, ty1, za, zb, zc, bstart, kind;
 };
 constexpr int kMaxRegions = 7;
 struct RegionList {
@@ -28,8 +29,7 @@ struct RegionList {
 struct alignas(128) InstDev {
     TmaSet tm;            // tensor maps of this instance's arrays
     StepParams p;
-    RegionList inner;     // work items of the interior tiles off the z slabs
-    RegionList zslab;     // work items of the interior tiles on the z slabs
+    RegionList inner;     // work items of the interior tiles (off and on the z slabs)
     RegionList outer;     // work items of the C-PML frame tiles
     RecTable rec;
     const float* src;     // adjoint: traces to inject
@@ -45,7 +45,6 @@ struct MultiTable {
     int n_inst;
     int n_fwd;                     // instances [0, n_fwd) are forward, the rest adjoint
     int pre_inner[kMaxInst + 1];   // first work item of each instance
-    int pre_zslab[kMaxInst + 1];
     int pre_outer[kMaxInst + 1];
     InstDev inst[kMaxInst];
 };
@@ -54,7 +53,7 @@ struct MultiTable {
 int make_tma_set(TmaSet* out, float* const* arrays, int nx, int ny, int nz);
 // Streams of one half step: the interior launch goes to st; with aux set,
 // the C-PML frame launch goes to aux between the events fork (recorded on st)
-// and join (waited for by st), so that the two launches overlap.
+// and join (waited for by st), so that the two launches may overlap.
 struct SplitStreams {
     cudaStream_t st;
     cudaStream_t aux;
@@ -64,9 +63,9 @@ struct SplitStreams {
 int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
 int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
 // persistent multi-instance half step (str = stress family) over a device
-// table: six launches (two directions x three region kinds), launch k taking
+// table: four launches (two directions x frame / interior), launch k taking
 // its work items from the counter next[k], which must be zero beforehand
-constexpr int kMultiLaunches = 6;
+constexpr int kMultiLaunches = 4;
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st);
-void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& zslab,
-                           int& nzslab, RegionList& outer, int& nouter);
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
+                           int& nouter);
