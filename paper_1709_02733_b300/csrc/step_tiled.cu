@@ -52,44 +52,67 @@ constexpr int D = 4;            // stage ring depth (planes)
 
 // C-PML code of a work-item body:
 //   PM_NONE  no layer (tiles and planes whose reach stays off every slab, or P = 0)
-//   PM_FULL  x, y and z layers (tiles whose halo touches an x or y slab)
+//   PM_FULL  x, y and z layers (corner tiles: halo on an x and a y slab)
+//   PM_X     x and z layers (tiles whose halo touches an x slab only)
+//   PM_Y     y and z layers (tiles whose halo touches a y slab only)
 //   PM_Z     z layer only (the other tiles, planes on the z slabs)
-// Two kernels per family and direction: the frame kernel (PM_FULL) and the
-// interior kernel (PM_NONE), whose blocks run the PM_NONE or the PM_Z body.
-constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2;
+// The frame tiles run in three launches (PM_X, PM_Y, PM_FULL); the interior
+// launch (PM_NONE) runs, per block, the PM_NONE or the PM_Z body.
+constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2, PM_X = 3, PM_Y = 4;
+constexpr bool has_x(int pm) { return pm == PM_FULL || pm == PM_X; }
+constexpr bool has_y(int pm) { return pm == PM_FULL || pm == PM_Y; }
 
-// Full C-PML adjoint blocks copy the memory variables at their threads' cross
-// positions (two positions, six values each) one plane ahead with cp.async
-// into two plane slots of shared memory: [slot][position][value][thread].
-constexpr int MVBUF = 2 * 2 * 6 * (TX * TY);
+// Frame adjoint blocks copy the memory variables at their threads' cross
+// positions (two positions, three values per layer axis) one plane ahead with
+// cp.async into two plane slots of shared memory: [slot][position][value][thread].
+constexpr int mv_values(int pm) { return (has_x(pm) ? 3 : 0) + (has_y(pm) ? 3 : 0); }
+constexpr int mv_floats(int pm) { return 2 * 2 * mv_values(pm) * (TX * TY); }
 
 template <bool ADJ, int PM> struct VelCfg {
-    static constexpr bool PML = PM != PM_NONE, PXY = PM == PM_FULL;
+    static constexpr bool PML = PM != PM_NONE, LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
     // stage boxes 0..5: sigma (forward) or Q (adjoint), Voigt order; 6 rho,
-    // 7 alpha.  Full C-PML adjoint blocks form the layer-augmented fields F in
+    // 7 alpha.  Frame adjoint blocks form the layer-augmented fields F in
     // place and keep the x-differenced F^21, which differs from the
     // y-differenced F^12 inside the layers, in one extra box.
     static constexpr int NB = 8;
     static constexpr int BRHO = 6, BALPHA = 7;
     static constexpr int NDER = (ADJ && PXY) ? 1 : 0;
-    static constexpr int MV = (ADJ && PXY) ? MVBUF : 0;  // floats of the memory-variable buffer
+    static constexpr int MV = ADJ ? mv_floats(PM) : 0;  // floats of the memory-variable buffer
     static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) { return b < 6 ? TM_S0 + b : (b == BRHO ? TM_RHO : TM_ALPHA); }
 };
 
 template <bool ADJ, int PM> struct StrCfg {
-    static constexpr bool PML = PM != PM_NONE, PXY = PM == PM_FULL;
+    static constexpr bool PML = PM != PM_NONE, LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
     // stage boxes 0..2: u (forward) or w (adjoint); 3 lambda, 4 1/mu.  Full
     // C-PML adjoint blocks form the layer-augmented fields E in place (the
     // x-differenced ones) and keep the y-differenced ones, which differ inside
     // the layers, in three extra boxes.
     static constexpr int NB = 5;
     static constexpr int NDER = (ADJ && PXY) ? 3 : 0;
-    static constexpr int MV = (ADJ && PXY) ? MVBUF : 0;  // floats of the memory-variable buffer
+    static constexpr int MV = ADJ ? mv_floats(PM) : 0;  // floats of the memory-variable buffer
     static constexpr int BLAM = 3, BMU = 4;
     static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : (b == 3 ? TM_LAM : TM_MU); }
 };
+
+// the edge kernel runs PM_X and PM_Y bodies with one shared-memory layout;
+// the interior kernel runs PM_NONE and PM_Z bodies
+static_assert(VelCfg<true, PM_X>::SMEM == VelCfg<true, PM_Y>::SMEM && StrCfg<true, PM_X>::SMEM == StrCfg<true, PM_Y>::SMEM &&
+                  VelCfg<false, PM_X>::SMEM == VelCfg<false, PM_Y>::SMEM &&
+                  StrCfg<false, PM_X>::SMEM == StrCfg<false, PM_Y>::SMEM,
+              "edge bodies share one layout");
+static_assert(VelCfg<true, PM_NONE>::SMEM == VelCfg<true, PM_Z>::SMEM &&
+                  StrCfg<true, PM_NONE>::SMEM == StrCfg<true, PM_Z>::SMEM &&
+                  VelCfg<false, PM_NONE>::SMEM == VelCfg<false, PM_Z>::SMEM &&
+                  StrCfg<false, PM_NONE>::SMEM == StrCfg<false, PM_Z>::SMEM,
+              "interior bodies share one layout");
+// the persistent frame kernels run every frame body with the corner layout
+static_assert(VelCfg<true, PM_FULL>::SMEM >= VelCfg<true, PM_X>::SMEM &&
+                  StrCfg<true, PM_FULL>::SMEM >= StrCfg<true, PM_X>::SMEM &&
+                  VelCfg<false, PM_FULL>::SMEM >= VelCfg<false, PM_X>::SMEM &&
+                  StrCfg<false, PM_FULL>::SMEM >= StrCfg<false, PM_X>::SMEM,
+              "corner layout covers the edge bodies");
 
 __device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1,
                                        int& kind) {
@@ -193,6 +216,7 @@ struct CrossPml {
     int sx[2], sy[2];
 };
 
+template <bool LX, bool LY>
 __device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy, const CrossPos& cp, int tid,
                                                int x0, int y0, const StepParams& p) {
     const int W = 2 * p.P + 1;
@@ -215,8 +239,8 @@ __device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy
         const int bx = cp.q[k] % BW, by = cp.q[k] / BW;
         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
         const int lx = slab_local(gx, p.nx, p.P), ly = slab_local(gy, p.ny, p.P);
-        if ((f & CP_XB) && lx >= 0) c.sx[k] = gy * W + lx;
-        if ((f & CP_YB) && ly >= 0) c.sy[k] = ly * p.nx + gx;
+        if (LX && (f & CP_XB) && lx >= 0) c.sx[k] = gy * W + lx;
+        if (LY && (f & CP_YB) && ly >= 0) c.sy[k] = ly * p.nx + gx;
     }
 }
 
@@ -265,15 +289,16 @@ struct PmlXY {
     float c[2][2][3];    // [axis x, y][lattice integer, half][a, b, chi]
 };
 
+template <bool LX, bool LY>
 __device__ __forceinline__ void pml_xy_init(PmlXY& q, const StepParams& p, int x, int y, bool own) {
-    q.lx = own ? slab_local(x, p.nx, p.P) : -1;
-    q.ly = own ? slab_local(y, p.ny, p.P) : -1;
+    q.lx = (LX && own) ? slab_local(x, p.nx, p.P) : -1;
+    q.ly = (LY && own) ? slab_local(y, p.ny, p.P) : -1;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
         for (int w = 0; w < 3; ++w) {
-            q.c[0][hh][w] = q.lx >= 0 ? tabv(p, 0, hh, w, x) : 0.f;
-            q.c[1][hh][w] = q.ly >= 0 ? tabv(p, 1, hh, w, y) : 0.f;
+            q.c[0][hh][w] = (LX && q.lx >= 0) ? tabv(p, 0, hh, w, x) : 0.f;
+            q.c[1][hh][w] = (LY && q.ly >= 0) ? tabv(p, 1, hh, w, y) : 0.f;
         }
 }
 
@@ -300,11 +325,11 @@ __device__ __forceinline__ unsigned own_slab(int axis, const PmlXY& q, int lz, i
     return ((unsigned)lz * p.ny + y) * p.nx + x;
 }
 
-// own point on the layer of axis j?  Without x / y layer code (PXY false)
-// only the z layer exists, which the compiler sees for an unrolled j.
-template <bool PXY>
+// own point on the layer of axis j?  Layers without code in the body (LX or
+// LY false) are absent, which the compiler sees for an unrolled j.
+template <bool LX, bool LY>
 __device__ __forceinline__ bool in_axis(int j, const PmlXY& q, int lz) {
-    return j == 2 ? lz >= 0 : (PXY && (j == 0 ? q.lx >= 0 : q.ly >= 0));
+    return j == 2 ? lz >= 0 : (j == 0 ? (LX && q.lx >= 0) : (LY && q.ly >= 0));
 }
 
 __device__ __forceinline__ float coef(int j, int hh, int w, const PmlXY& q, const PmlZ& qz) {
@@ -323,7 +348,8 @@ template <bool ADJ, int PM>
 __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y, int zc0,
                                          int zc1, int* err, float* sm) {
     using Cfg = VelCfg<ADJ, PM>;
-    constexpr bool PML = Cfg::PML, PXY = Cfg::PXY;
+    constexpr bool PML = Cfg::PML, LX = Cfg::LX, LY = Cfg::LY, PXY = Cfg::PXY;
+    constexpr int NV = mv_values(PM), YV = LX ? 3 : 0;  // buffered values per position; first y value
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -338,7 +364,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     const int P = p.P;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
     PmlXY px{};
-    if constexpr (PXY) pml_xy_init(px, p, x, y, own);
+    if constexpr (PXY) pml_xy_init<LX, LY>(px, p, x, y, own);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
@@ -365,7 +391,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     if constexpr (ADJ && PXY) {
         cross_init(cross, tid, x0, y0, p.nx, p.ny);
         __syncthreads();  // a persistent block may still read the tables of its previous item
-        cross_pml_init(cpm, cxt, cyt, cross, tid, x0, y0, p);
+        cross_pml_init<LX, LY>(cpm, cxt, cyt, cross, tid, x0, y0, p);
         __syncthreads();
     }
 
@@ -382,7 +408,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
             const int lz = slab_local(zn, p.nz, P);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (in_axis<PXY>(j, px, lz)) {
+                if (in_axis<LX, LY>(j, px, lz)) {
                     const unsigned si = own_slab(j, px, lz, x, y, zn, p);
 #pragma unroll
                     for (int i = 0; i < 3; ++i) nph[i][j] = p.phi[i][j][si];
@@ -430,20 +456,20 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         if constexpr (ADJ && PXY) {
             const int zn = z + 1;
             if (zn >= zc0 && zn < zc1) {
-                float* dst = mvb + (size_t)(zn & 1) * 12 * NT + tid;
+                float* dst = mvb + (size_t)(zn & 1) * 2 * NV * NT + tid;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    if (cpm.sx[k] >= 0) {
+                    if (LX && cpm.sx[k] >= 0) {
                         const unsigned si = (unsigned)zn * p.ny * (2 * P + 1) + cpm.sx[k];
-                        cp_async_4(dst + (k * 6 + 0) * NT, p.psi[0][0] + si);
-                        cp_async_4(dst + (k * 6 + 1) * NT, p.psi[1][0] + si);
-                        cp_async_4(dst + (k * 6 + 2) * NT, p.psi[2][0] + si);
+                        cp_async_4(dst + (k * NV + 0) * NT, p.psi[0][0] + si);
+                        cp_async_4(dst + (k * NV + 1) * NT, p.psi[1][0] + si);
+                        cp_async_4(dst + (k * NV + 2) * NT, p.psi[2][0] + si);
                     }
-                    if (cpm.sy[k] >= 0) {
+                    if (LY && cpm.sy[k] >= 0) {
                         const unsigned si = (unsigned)zn * (2 * P + 1) * p.nx + cpm.sy[k];
-                        cp_async_4(dst + (k * 6 + 3) * NT, p.psi[1][1] + si);
-                        cp_async_4(dst + (k * 6 + 4) * NT, p.psi[0][1] + si);
-                        cp_async_4(dst + (k * 6 + 5) * NT, p.psi[2][1] + si);
+                        cp_async_4(dst + (k * NV + YV + 0) * NT, p.psi[1][1] + si);
+                        cp_async_4(dst + (k * NV + YV + 1) * NT, p.psi[0][1] + si);
+                        cp_async_4(dst + (k * NV + YV + 2) * NT, p.psi[2][1] + si);
                     }
                 }
             }
@@ -503,18 +529,18 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                         const float q11 = sz[q], q22 = sz[BOXS + q], q23 = sz[3 * BOXS + q];
                         const float q13 = sz[4 * BOXS + q], q12 = sz[5 * BOXS + q];
                         float f11 = q11, f21 = q12, f31 = q13, f22 = q22, f12 = q12, f32 = q23;
-                        const float* mv = mvb + (size_t)((z & 1) * 12 + k * 6) * NT + tid;
-                        if (cpm.sx[k] >= 0) {
+                        const float* mv = mvb + (size_t)(((z & 1) * 2 + k) * NV) * NT + tid;
+                        if (LX && cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
                             f11 += t[0] * (mv[0] + t[1] * q11);
                             f21 += t[2] * (mv[NT] + t[3] * q12);
                             f31 += t[2] * (mv[2 * NT] + t[3] * q13);
                         }
-                        if (cpm.sy[k] >= 0) {
+                        if (LY && cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            f22 += t[0] * (mv[3 * NT] + t[1] * q22);
-                            f12 += t[2] * (mv[4 * NT] + t[3] * q12);
-                            f32 += t[2] * (mv[5 * NT] + t[3] * q23);
+                            f22 += t[0] * (mv[YV * NT] + t[1] * q22);
+                            f12 += t[2] * (mv[(YV + 1) * NT] + t[3] * q12);
+                            f32 += t[2] * (mv[(YV + 2) * NT] + t[3] * q23);
                         }
                         if (f & CP_XB) {
                             szw[q] = f11;
@@ -536,9 +562,9 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                                        {dmx(XD1, o) * h, dpy(YD0, o) * h, dq(q23) * h},   // u^y
                                        {dmx(XD2, o) * h, dmy(YD2, o) * h, dq(q33) * h}};  // u^z
                 const float* r0 = sz + Cfg::BRHO * BOXS;
-                const float* a0 = sz + Cfg::BALPHA * BOXS;
                 const float rb[3] = {0.5f * (r0[o] + r0[o + xc1]), 0.5f * (r0[o] + r0[o + yc1]),
                                      0.5f * (r0[o] + sz1[Cfg::BRHO * BOXS + o])};
+                const float* a0 = sz + Cfg::BALPHA * BOXS;
                 const float ab[3] = {0.5f * (a0[o] + a0[o + xc1]), 0.5f * (a0[o] + a0[o + yc1]),
                                      0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o])};
                 PmlZ pz{};
@@ -550,7 +576,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                     if constexpr (PML) {
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
-                            if (in_axis<PXY>(j, px, pz.lz)) {
+                            if (in_axis<LX, LY>(j, px, pz.lz)) {
                                 const int hh = (i == j);
                                 float* ph = &p.phi[i][j][own_slab(j, px, pz.lz, x, y, z, p)];
                                 if constexpr (!ADJ) {
@@ -596,7 +622,8 @@ template <bool ADJ, int PM>
 __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y, int zc0,
                                          int zc1, int* err, float* sm) {
     using Cfg = StrCfg<ADJ, PM>;
-    constexpr bool PML = Cfg::PML, PXY = Cfg::PXY;
+    constexpr bool PML = Cfg::PML, LX = Cfg::LX, LY = Cfg::LY, PXY = Cfg::PXY;
+    constexpr int NV = mv_values(PM), YV = LX ? 3 : 0;  // buffered values per position; first y value
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
@@ -611,7 +638,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     const int P = p.P;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
     PmlXY px{};
-    if constexpr (PXY) pml_xy_init(px, p, x, y, own);
+    if constexpr (PXY) pml_xy_init<LX, LY>(px, p, x, y, own);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
@@ -639,7 +666,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     if constexpr (ADJ && PXY) {
         cross_init(cross, tid, x0, y0, p.nx, p.ny);
         __syncthreads();  // a persistent block may still read the tables of its previous item
-        cross_pml_init(cpm, cxt, cyt, cross, tid, x0, y0, p);
+        cross_pml_init<LX, LY>(cpm, cxt, cyt, cross, tid, x0, y0, p);
         __syncthreads();
     }
 
@@ -655,7 +682,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
             const int lz = slab_local(zn, p.nz, P);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (in_axis<PXY>(j, px, lz)) {
+                if (in_axis<LX, LY>(j, px, lz)) {
                     const unsigned si = own_slab(j, px, lz, x, y, zn, p);
 #pragma unroll
                     for (int i = 0; i < 3; ++i) nps[i][j] = p.psi[i][j][si];
@@ -705,20 +732,20 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         if constexpr (ADJ && PXY) {
             const int zn = z + 1;
             if (zn >= zc0 && zn < zc1) {
-                float* dst = mvb + (size_t)(zn & 1) * 12 * NT + tid;
+                float* dst = mvb + (size_t)(zn & 1) * 2 * NV * NT + tid;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    if (cpm.sx[k] >= 0) {
+                    if (LX && cpm.sx[k] >= 0) {
                         const unsigned si = (unsigned)zn * p.ny * (2 * P + 1) + cpm.sx[k];
-                        cp_async_4(dst + (k * 6 + 0) * NT, p.phi[0][0] + si);
-                        cp_async_4(dst + (k * 6 + 1) * NT, p.phi[1][0] + si);
-                        cp_async_4(dst + (k * 6 + 2) * NT, p.phi[2][0] + si);
+                        cp_async_4(dst + (k * NV + 0) * NT, p.phi[0][0] + si);
+                        cp_async_4(dst + (k * NV + 1) * NT, p.phi[1][0] + si);
+                        cp_async_4(dst + (k * NV + 2) * NT, p.phi[2][0] + si);
                     }
-                    if (cpm.sy[k] >= 0) {
+                    if (LY && cpm.sy[k] >= 0) {
                         const unsigned si = (unsigned)zn * (2 * P + 1) * p.nx + cpm.sy[k];
-                        cp_async_4(dst + (k * 6 + 3) * NT, p.phi[1][1] + si);
-                        cp_async_4(dst + (k * 6 + 4) * NT, p.phi[0][1] + si);
-                        cp_async_4(dst + (k * 6 + 5) * NT, p.phi[2][1] + si);
+                        cp_async_4(dst + (k * NV + YV + 0) * NT, p.phi[1][1] + si);
+                        cp_async_4(dst + (k * NV + YV + 1) * NT, p.phi[0][1] + si);
+                        cp_async_4(dst + (k * NV + YV + 2) * NT, p.phi[2][1] + si);
                     }
                 }
             }
@@ -779,18 +806,18 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                         const int q = cross.q[k];
                         const float wx = sz[q], wy = sz[BOXS + q], wz = sz[2 * BOXS + q];
                         float exx = wx, eyx = wy, ezx = wz, eyy = wy, exy = wx, ezy = wz;
-                        const float* mv = mvb + (size_t)((z & 1) * 12 + k * 6) * NT + tid;
-                        if (cpm.sx[k] >= 0) {
+                        const float* mv = mvb + (size_t)(((z & 1) * 2 + k) * NV) * NT + tid;
+                        if (LX && cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
                             exx += t[2] * (mv[0] + t[3] * wx);
                             eyx += t[0] * (mv[NT] + t[1] * wy);
                             ezx += t[0] * (mv[2 * NT] + t[1] * wz);
                         }
-                        if (cpm.sy[k] >= 0) {
+                        if (LY && cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            eyy += t[2] * (mv[3 * NT] + t[3] * wy);
-                            exy += t[0] * (mv[4 * NT] + t[1] * wx);
-                            ezy += t[0] * (mv[5 * NT] + t[1] * wz);
+                            eyy += t[2] * (mv[YV * NT] + t[3] * wy);
+                            exy += t[0] * (mv[(YV + 1) * NT] + t[1] * wx);
+                            ezy += t[0] * (mv[(YV + 2) * NT] + t[1] * wz);
                         }
                         if (f & CP_XB) {
                             szw[q] = exx;
@@ -831,7 +858,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                     if constexpr (PML) {
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
-                            if (in_axis<PXY>(j, px, pz.lz)) {
+                            if (in_axis<LX, LY>(j, px, pz.lz)) {
                                 const unsigned si = own_slab(j, px, pz.lz, x, y, z, p);
 #pragma unroll
                                 for (int i = 0; i < 3; ++i) {
@@ -857,7 +884,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                         // psi^ <- b (psi^ + chi Q_old) at the own point
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
-                            if (in_axis<PXY>(j, px, pz.lz)) {
+                            if (in_axis<LX, LY>(j, px, pz.lz)) {
                                 const unsigned si = own_slab(j, px, pz.lz, x, y, z, p);
 #pragma unroll
                                 for (int i = 0; i < 3; ++i) {
@@ -902,31 +929,52 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 // (0: no minimum; the velocity family is limited by its shared memory)
 template <bool STR, bool ADJ, int PM>
 constexpr int min_blocks() {
-    return !STR ? 0 : (PM == PM_FULL ? 2 : 4);
+    return !STR ? 0 : (PM == PM_NONE ? 4 : (PM == PM_FULL ? 2 : 3));
 }
 // the persistent kernels read their parameters from shared memory, which
 // costs registers: give their velocity-family C-PML bodies an explicit budget
 template <bool STR, bool ADJ, int PM>
 constexpr int multi_min_blocks() {
-    return !STR ? (PM == PM_FULL ? (ADJ ? 2 : 3) : 0) : (PM == PM_FULL ? 2 : (ADJ ? 4 : 3));
+    return !STR ? (PM == PM_NONE ? 0 : (ADJ ? 2 : 3)) : (PM == PM_NONE ? (ADJ ? 4 : 3) : 2);
 }
 
-// One work item of a launch: the frame launch (PM_FULL) runs the full C-PML
-// body; the interior launch (PM_NONE) runs, per block, the body its region
-// asks for (z-slab regions: z-layer code only).
-template <bool ADJ, int PM>
+// One work item; a block runs the body of its region's kind.  Single-grid
+// launches: the interior kernel (PM_NONE) runs PM_NONE or PM_Z bodies, the
+// edge kernel (PM_X) PM_X or PM_Y bodies, the corner kernel (PM_FULL) PM_FULL
+// bodies; the persistent frame kernels (DISPATCH) run any frame body.
+template <bool ADJ, int PM, bool DISPATCH>
 __device__ __forceinline__ bool vel_item(const StepParams& p, const CUtensorMap* maps, int kind, int tile_x,
                                          int tile_y, int zc0, int zc1, int* err, float* sm) {
-    if constexpr (PM == PM_FULL) return vel_body<ADJ, PM_FULL>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
-    else if (kind == PM_Z) return vel_body<ADJ, PM_Z>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
-    else return vel_body<ADJ, PM_NONE>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    if constexpr (PM == PM_NONE) {
+        if (kind == PM_Z) return vel_body<ADJ, PM_Z>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        return vel_body<ADJ, PM_NONE>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    } else if constexpr (DISPATCH) {
+        if (kind == PM_X) return vel_body<ADJ, PM_X>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        if (kind == PM_Y) return vel_body<ADJ, PM_Y>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        return vel_body<ADJ, PM_FULL>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    } else if constexpr (PM == PM_X) {
+        if (kind == PM_Y) return vel_body<ADJ, PM_Y>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        return vel_body<ADJ, PM_X>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    } else {
+        return vel_body<ADJ, PM>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    }
 }
-template <bool ADJ, int PM>
+template <bool ADJ, int PM, bool DISPATCH>
 __device__ __forceinline__ bool str_item(const StepParams& p, const CUtensorMap* maps, int kind, int tile_x,
                                          int tile_y, int zc0, int zc1, int* err, float* sm) {
-    if constexpr (PM == PM_FULL) return str_body<ADJ, PM_FULL>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
-    else if (kind == PM_Z) return str_body<ADJ, PM_Z>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
-    else return str_body<ADJ, PM_NONE>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    if constexpr (PM == PM_NONE) {
+        if (kind == PM_Z) return str_body<ADJ, PM_Z>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        return str_body<ADJ, PM_NONE>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    } else if constexpr (DISPATCH) {
+        if (kind == PM_X) return str_body<ADJ, PM_X>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        if (kind == PM_Y) return str_body<ADJ, PM_Y>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        return str_body<ADJ, PM_FULL>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    } else if constexpr (PM == PM_X) {
+        if (kind == PM_Y) return str_body<ADJ, PM_Y>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+        return str_body<ADJ, PM_X>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    } else {
+        return str_body<ADJ, PM>(p, maps, tile_x, tile_y, zc0, zc1, err, sm);
+    }
 }
 
 template <bool ADJ, int PM>
@@ -936,7 +984,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<false, ADJ, PM>())) k_vel_tile
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    vel_item<ADJ, PM>(p, tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
+    vel_item<ADJ, PM, false>(p, tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
 template <bool ADJ, int PM>
@@ -946,7 +994,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<true, ADJ, PM>())) k_str_tiled
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    str_item<ADJ, PM>(p, tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
+    str_item<ADJ, PM, false>(p, tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
 // Persistent multi-instance half steps: a fixed grid works through the work
@@ -992,8 +1040,8 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
         if (tid == 0)
             for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
         __syncthreads();
-        const bool ok = STR ? str_item<ADJ, PM>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)
-                            : vel_item<ADJ, PM>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
+        const bool ok = STR ? str_item<ADJ, PM, true>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)
+                            : vel_item<ADJ, PM, true>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
         if (!ok) return;
     }
 }
@@ -1060,29 +1108,38 @@ int chunk_planes(long tiles, int zlen, long slots) {
 // Work regions of one half step.  Interior launch: the interior tiles off
 // the z slabs (no layer code; long chunks, first) and on the z slabs (z-layer
 // code; one chunk per slab, last, so that they fill the launch's tail).
-// Frame launch: the tiles around the interior ones, all planes, full C-PML
-// code, up to four rectangles.  With P = 0 every tile is interior and there
+// Frame: the tiles around the interior ones, all planes, in up to eight
+// rectangles: the edges (x layer only, y layer only; one launch) and the
+// corners (both layers; a second launch), each chunked for its own launch.  With P = 0 every tile is interior and there
 // are no slabs.
-void make_regions(const StepParams& p, long slots_inner, long slots_outer, RegionList& inner, int& inner_blocks,
-                  RegionList& outer, int& outer_blocks) {
+void make_regions(const StepParams& p, long slots_inner, long slots_edge, long slots_corner, RegionList& inner,
+                  int& inner_blocks, RegionList& outer, int& outer_blocks) {
     inner.n = outer.n = 0;
     inner_blocks = outer_blocks = 0;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
     const int P = p.P;
     int txlo = 0, txhi = ntx - 1, tylo = 0, tyhi = nty - 1;
     if (P > 0 && !interior_tiles(p, txlo, txhi, tylo, tyhi)) {
-        add_region(outer, 0, ntx, 0, nty, 0, p.nz, chunk_planes((long)ntx * nty, p.nz, slots_outer), PM_FULL,
+        add_region(outer, 0, ntx, 0, nty, 0, p.nz, chunk_planes((long)ntx * nty, p.nz, slots_corner), PM_FULL,
                    outer_blocks);
         return;
     }
     const long tiles = (long)(txhi + 1 - txlo) * (tyhi + 1 - tylo);
     const long frame = (long)ntx * nty - tiles;
     if (frame > 0) {
-        const int zc = chunk_planes(frame, p.nz, slots_outer);
-        add_region(outer, 0, txlo, 0, nty, 0, p.nz, zc, PM_FULL, outer_blocks);
-        add_region(outer, txhi + 1, ntx, 0, nty, 0, p.nz, zc, PM_FULL, outer_blocks);
-        add_region(outer, txlo, txhi + 1, 0, tylo, 0, p.nz, zc, PM_FULL, outer_blocks);
-        add_region(outer, txlo, txhi + 1, tyhi + 1, nty, 0, p.nz, zc, PM_FULL, outer_blocks);
+        // x-frame columns beside the interior rows (x layer), y-frame rows
+        // beside the interior columns (y layer), and the four corners
+        const long corners = (long)(ntx - (txhi + 1 - txlo)) * (nty - (tyhi + 1 - tylo));
+        const int ze = chunk_planes(frame - corners, p.nz, slots_edge);
+        const int zk = chunk_planes(corners, p.nz, slots_corner);
+        add_region(outer, 0, txlo, tylo, tyhi + 1, 0, p.nz, ze, PM_X, outer_blocks);
+        add_region(outer, txhi + 1, ntx, tylo, tyhi + 1, 0, p.nz, ze, PM_X, outer_blocks);
+        add_region(outer, txlo, txhi + 1, 0, tylo, 0, p.nz, ze, PM_Y, outer_blocks);
+        add_region(outer, txlo, txhi + 1, tyhi + 1, nty, 0, p.nz, ze, PM_Y, outer_blocks);
+        add_region(outer, 0, txlo, 0, tylo, 0, p.nz, zk, PM_FULL, outer_blocks);
+        add_region(outer, txhi + 1, ntx, 0, tylo, 0, p.nz, zk, PM_FULL, outer_blocks);
+        add_region(outer, 0, txlo, tyhi + 1, nty, 0, p.nz, zk, PM_FULL, outer_blocks);
+        add_region(outer, txhi + 1, ntx, tyhi + 1, nty, 0, p.nz, zk, PM_FULL, outer_blocks);
     }
     const int za = P > 0 ? std::min(P, p.nz) : 0;  // planes [za, zb) are off the z slabs
     const int zb = P > 0 ? std::max(za, p.nz - P - 1) : p.nz;
@@ -1094,9 +1151,23 @@ void make_regions(const StepParams& p, long slots_inner, long slots_outer, Regio
 
 struct LaunchPlan {
     int dev, nx, ny, nz, P, family;
-    RegionList inner, outer;
-    int inner_blocks, outer_blocks;
+    RegionList inner, edge, corner;  // interior, frame edges (PM_X, PM_Y), frame corners (PM_FULL)
+    int inner_blocks, edge_blocks, corner_blocks;
 };
+
+// the regions of the kinds in `kinds` (bit mask), renumbered from block 0
+int select_kinds(const RegionList& all, unsigned kinds, RegionList& out) {
+    out.n = 0;
+    int blocks = 0;
+    for (int k = 0; k < all.n; ++k) {
+        if (!((kinds >> all.r[k].kind) & 1u)) continue;
+        Region r = all.r[k];
+        r.bstart = blocks;
+        blocks += (r.tx1 - r.tx0) * (r.ty1 - r.ty0) * ((r.zb - r.za + r.zc - 1) / r.zc);
+        out.r[out.n++] = r;
+    }
+    return blocks;
+}
 
 // kernel and dynamic shared memory of a family (0 vel fwd, 1 vel adj, 2 str
 // fwd, 3 str adj) and C-PML mode
@@ -1110,11 +1181,12 @@ size_t fam_smem(int f) {
     return f == 0 ? VelCfg<false, PM>::SMEM : f == 1 ? VelCfg<true, PM>::SMEM
          : f == 2 ? StrCfg<false, PM>::SMEM : StrCfg<true, PM>::SMEM;
 }
+// pm: PM_NONE (interior kernel), PM_X (edge kernel) or PM_FULL (corner kernel)
 const void* fam_fn(int f, int pm) {
-    return pm == PM_FULL ? fam_fn<PM_FULL>(f) : fam_fn<PM_NONE>(f);
+    return pm == PM_FULL ? fam_fn<PM_FULL>(f) : pm == PM_X ? fam_fn<PM_X>(f) : fam_fn<PM_NONE>(f);
 }
 size_t fam_smem(int f, int pm) {
-    return pm == PM_FULL ? fam_smem<PM_FULL>(f) : fam_smem<PM_NONE>(f);
+    return pm == PM_FULL ? fam_smem<PM_FULL>(f) : pm == PM_X ? fam_smem<PM_X>(f) : fam_smem<PM_NONE>(f);
 }
 
 // resident blocks of a kernel on the whole device
@@ -1139,7 +1211,8 @@ LaunchPlan plan_for(int family, const StepParams& p) {
             return L;
     }
     const long si = device_slots(fam_fn(family, PM_NONE), fam_smem(family, PM_NONE), dev);
-    const long so = device_slots(fam_fn(family, PM_FULL), fam_smem(family, PM_FULL), dev);
+    const long sc = device_slots(fam_fn(family, PM_FULL), fam_smem(family, PM_FULL), dev);
+    const long se = device_slots(fam_fn(family, PM_X), fam_smem(family, PM_X), dev);
     LaunchPlan& L = plans[nplans % 32];
     L.dev = dev;
     L.family = family;
@@ -1147,7 +1220,11 @@ LaunchPlan plan_for(int family, const StepParams& p) {
     L.ny = p.ny;
     L.nz = p.nz;
     L.P = p.P;
-    make_regions(p, si, so, L.inner, L.inner_blocks, L.outer, L.outer_blocks);
+    RegionList outer;
+    int outer_blocks = 0;
+    make_regions(p, si, se, sc, L.inner, L.inner_blocks, outer, outer_blocks);
+    L.edge_blocks = select_kinds(outer, (1u << PM_X) | (1u << PM_Y), L.edge);
+    L.corner_blocks = select_kinds(outer, 1u << PM_FULL, L.corner);
     nplans = std::min(nplans + 1, 32);
     return L;
 }
@@ -1160,44 +1237,50 @@ template <bool ADJ>
 static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 1 : 0, p);
     const dim3 blk(TX, TY, 1);
-    const bool split = ss.aux && L.outer_blocks && L.inner_blocks;
+    const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
+    const bool split = ss.aux && nframe && L.inner_blocks;
     cudaStream_t so = ss.st;
     if (split) {
         cudaEventRecord(ss.fork, ss.st);
         cudaStreamWaitEvent(ss.aux, ss.fork, 0);
         so = ss.aux;
     }
-    if (L.outer_blocks)
-        k_vel_tiled<ADJ, PM_FULL><<<L.outer_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.outer, err);
+    if (L.corner_blocks)
+        k_vel_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.corner, err);
+    if (L.edge_blocks)
+        k_vel_tiled<ADJ, PM_X><<<L.edge_blocks, blk, VelCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
     if (L.inner_blocks)
         k_vel_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
     }
-    return (L.outer_blocks > 0) + (L.inner_blocks > 0);
+    return nframe + (L.inner_blocks > 0);
 }
 
 template <bool ADJ>
 static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
     const LaunchPlan L = plan_for(ADJ ? 3 : 2, p);
     const dim3 blk(TX, TY, 1);
-    const bool split = ss.aux && L.outer_blocks && L.inner_blocks;
+    const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
+    const bool split = ss.aux && nframe && L.inner_blocks;
     cudaStream_t so = ss.st;
     if (split) {
         cudaEventRecord(ss.fork, ss.st);
         cudaStreamWaitEvent(ss.aux, ss.fork, 0);
         so = ss.aux;
     }
-    if (L.outer_blocks)
-        k_str_tiled<ADJ, PM_FULL><<<L.outer_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.outer, err);
+    if (L.corner_blocks)
+        k_str_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.corner, err);
+    if (L.edge_blocks)
+        k_str_tiled<ADJ, PM_X><<<L.edge_blocks, blk, StrCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
     if (L.inner_blocks)
         k_str_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
     }
-    return (L.outer_blocks > 0) + (L.inner_blocks > 0);
+    return nframe + (L.inner_blocks > 0);
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
@@ -1240,7 +1323,7 @@ void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next,
 // `zc` planes so that work items of different instances are of similar size.
 void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
                            int& nouter) {
-    make_regions(p, 1, 1, inner, ninner, outer, nouter);
+    make_regions(p, 1, 1, 1, inner, ninner, outer, nouter);
     auto rechunk = [zc](RegionList& rl) {
         int blocks = 0;
         for (int k = 0; k < rl.n; ++k) {

@@ -18,7 +18,7 @@ struct TmaSet {
 struct Region {
     int tx0, tx1, ty0, ty1, za, zb, zc, bstart, kind;
 };
-constexpr int kMaxRegions = 7;
+constexpr int kMaxRegions = 8;
 struct RegionList {
     int n;
     Region r[kMaxRegions];

@@ -139,14 +139,65 @@ class InputCache:
         return synth.band_limited_traces(r.nsteps, r.L, r.seed, dt)
 
 
+def handle_bytes(n: int, L: int, cache: InputCache) -> int:
+    """Device bytes of a solver handle for an n^3 grid (pact_query_bytes)."""
+    from .pact import pact_query_bytes
+    return pact_query_bytes(cache.workload(n)[0], L, -1)
+
+
+def io_bytes(r: Request) -> int:
+    """Device bytes of a request's input and output buffers."""
+    return (r.n ** 3 + (r.nsteps + 1) * r.L) * 4
+
+
 def request_bytes(r: Request, cache: InputCache) -> int:
     """Device bytes a request holds while admitted: the handle (pact_query_bytes)
     plus its medium copy, input and output buffers."""
-    from .pact import pact_query_bytes
-    d = cache.workload(r.n)[0]
-    N = r.n ** 3
-    io = (N + (r.nsteps + 1) * r.L) * 4
-    return pact_query_bytes(d, r.L, -1) + 4 * N * 4 + io
+    return handle_bytes(r.n, r.L, cache) + 4 * r.n ** 3 * 4 + io_bytes(r)
+
+
+class GridPool:
+    """Idle solver handles by grid side, their medium already set.  A retired
+    solve's handle serves the next request of the same size, so the serving
+    loop neither allocates nor frees device memory while solves are in flight
+    (a free synchronises the device).  Idle handles stay counted against the
+    budget; the largest ones are closed when a new size needs room."""
+
+    def __init__(self, cache: InputCache, stream):
+        self.cache, self.stream = cache, stream
+        self.idle: Dict[int, list] = {}
+
+    def take(self, n: int):
+        lst = self.idle.get(n)
+        return lst.pop() if lst else None
+
+    def put(self, n: int, g) -> None:
+        self.idle.setdefault(n, []).append(g)
+
+    def make(self, n: int):
+        """A new handle for side n with its medium set (on the pool's stream)."""
+        import torch
+        from .pact import Grid
+        d, dmed, _ = self.cache.device_workload(n)
+        with torch.cuda.stream(self.stream):
+            g = Grid(d, stream=self.stream)
+            g.set_medium(*dmed)
+        return g
+
+    def evict(self):
+        """Close one idle handle of the largest side; returns that side or None."""
+        sides = [n for n, lst in self.idle.items() if lst]
+        if not sides:
+            return None
+        n = max(sides)
+        self.idle[n].pop().close()
+        return n
+
+    def close(self) -> None:
+        for lst in self.idle.values():
+            for g in lst:
+                g.close()
+        self.idle.clear()
 
 
 # ---------------------------------------------------------------------------
@@ -159,35 +210,34 @@ class _Active:
         self.req, self.grid, self.bufs, self.nbytes, self.ev = req, grid, bufs, nbytes, None
 
 
-def _prepare(r: Request, cache: InputCache, stream):
-    """Handle + input/output buffers of one request, set up on `stream`
-    (pact_set_medium synchronises only that stream)."""
+def _buffers(r: Request, cache: InputCache, stream):
+    """Receivers and the input / output buffers of one request, on `stream`."""
     import torch
-    from .pact import Grid
-    d, dmed, p0 = cache.device_workload(r.n)
+    d, _, p0 = cache.device_workload(r.n)
     rec = cache.receivers(r.n, r.L)
     with torch.cuda.stream(stream):
-        g = Grid(d, stream=stream)
-        g.set_medium(*dmed)
         if r.adjoint:
             inp = torch.from_numpy(cache.traces(r, d.dt)).to("cuda", non_blocking=False)
             out = torch.empty(d.shape, device="cuda")
         else:
             inp = p0
             out = torch.empty((r.nsteps + 1, r.L), device="cuda")
-    return g, rec, inp, out
+    return rec, inp, out
 
 
 def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16, max_slots: int = 32,
                    cache: Optional[InputCache] = None, realtime: bool = True) -> Dict:
     """Serve the stream with continuous batching; returns statistics.
 
-    Loop: move arrived requests to the queue; admit FIFO under the budget
-    (each admission is prepared on a side stream that the serving stream then
-    waits for); replay one k-step multi-instance graph over all admitted
-    solves; retire solves whose last step has executed.  At most two graph
-    replays are in flight, so admissions and completions are seen within one
-    chunk.  realtime=False skips idle waits (arrivals are then virtual)."""
+    Loop: move arrived requests to the queue; admit FIFO while the budget and
+    the slots allow (a handle is reused from the pool when one of the same
+    size is idle, otherwise made, closing idle handles of other sizes if the
+    budget needs room; its buffers are set up on a side stream that the
+    serving stream then waits for); replay one k-step multi-instance graph over
+    all admitted solves; retire solves whose last step has executed (their
+    handles return to the pool).  At most two graph replays are in flight, so
+    admissions and completions are seen within one chunk.  realtime=False
+    skips idle waits (arrivals are then virtual)."""
     import collections
 
     import torch
@@ -195,13 +245,14 @@ def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16,
     cache = cache or InputCache()
     stream = torch.cuda.current_stream()
     side = torch.cuda.Stream()
+    pool = GridPool(cache, side)
     adm = Admission(budget_bytes, min(max_slots, MAX_SLOTS))
     pending = sorted(requests, key=lambda r: r.arrival)
     queue: List[Request] = []
     active: List[_Active] = []
     finished: List[Request] = []
-    sizes = {r.rid: request_bytes(r, cache) for r in requests}
-    for n in sorted({r.n for r in requests}):
+    hb = {n: handle_bytes(n, 512, cache) + 4 * n ** 3 * 4 for n in {r.n for r in requests}}
+    for n in sorted(hb):
         cache.device_workload(n)
     torch.cuda.synchronize()
     clock = {"t0": time.perf_counter()}
@@ -212,12 +263,34 @@ def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16,
             clock["t0"] -= pending[0].arrival - now()  # idle: jump to the next arrival
         while pending and pending[0].arrival <= now():
             queue.append(pending.pop(0))
-        admitted = adm.admit(queue, lambda q: sizes[q.rid])
-        for r in admitted:
+        admitted = False
+        while queue and adm.slots < adm.max_slots:
+            r = queue[0]
+            g = pool.take(r.n)
+            if g is None:
+                need = hb[r.n] + io_bytes(r)
+                while not adm.fits(need):
+                    n_ev = pool.evict()
+                    if n_ev is None:
+                        break
+                    adm.used -= hb[n_ev]
+                if not adm.fits(need):
+                    break  # FIFO: the head waits for memory
+                adm.take(need)
+                g = pool.make(r.n)
+            else:
+                if adm.used + io_bytes(r) > adm.budget:
+                    pool.put(r.n, g)
+                    break
+                adm.used += io_bytes(r)  # the handle's bytes are already counted
+                adm.slots += 1
+            queue.pop(0)
             r.admitted = now()
-            g, rec, inp, out = _prepare(r, cache, side)
-            g.begin(r.adjoint, inp, rec, r.nsteps, out)
-            active.append(_Active(r, g, (inp, out), sizes[r.rid]))
+            rec, inp, out = _buffers(r, cache, side)
+            with torch.cuda.stream(side):
+                g.begin(r.adjoint, inp, rec, r.nsteps, out)
+            active.append(_Active(r, g, (inp, out), io_bytes(r)))
+            admitted = True
         if admitted:
             stream.wait_stream(side)
         if not active:
@@ -238,21 +311,27 @@ def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16,
             if a.ev is not None and a.ev.query():
                 a.req.done = now()
                 a.req.result = a.bufs[1]
-                adm.release(a.nbytes)
-                a.grid.close()
+                adm.used -= a.nbytes  # the handle stays counted while idle in the pool
+                adm.slots -= 1
+                side.wait_event(a.ev)  # the handle's next solve starts after this one
+                pool.put(a.req.n, a.grid)
                 finished.append(a.req)
             else:
                 still.append(a)
         active = still
     torch.cuda.synchronize()
-    return summarize(finished, now())
+    stats = summarize(finished, now())
+    pool.close()
+    return stats
 
 
 def run_one_at_a_time(requests: List[Request], cache: Optional[InputCache] = None, realtime: bool = True) -> Dict:
-    """Baseline: each request alone on the GPU, in arrival order."""
+    """Baseline: each request alone on the GPU, in arrival order (handles
+    reused from a pool of the same kind as the server's)."""
     import torch
     cache = cache or InputCache()
     stream = torch.cuda.current_stream()
+    pool = GridPool(cache, stream)
     for n in sorted({r.n for r in requests}):
         cache.device_workload(n)
     torch.cuda.synchronize()
@@ -266,7 +345,8 @@ def run_one_at_a_time(requests: List[Request], cache: Optional[InputCache] = Non
             else:
                 clock["t0"] -= r.arrival - now()
         r.admitted = now()
-        g, rec, inp, out = _prepare(r, cache, stream)
+        g = pool.take(r.n) or pool.make(r.n)
+        rec, inp, out = _buffers(r, cache, stream)
         if r.adjoint:
             g.adjoint(inp, rec, out=out)
         else:
@@ -274,9 +354,11 @@ def run_one_at_a_time(requests: List[Request], cache: Optional[InputCache] = Non
         torch.cuda.synchronize()
         r.done = now()
         r.result = out
-        g.close()
+        pool.put(r.n, g)
         done.append(r)
-    return summarize(done, now())
+    stats = summarize(done, now())
+    pool.close()
+    return stats
 
 
 def summarize(done: List[Request], wall: float) -> Dict:

@@ -240,6 +240,27 @@ def test_tiled_random_medium(shape, npml, nsteps):
     assert rel_l2(img, o.adjoint(y, rec)) <= TOL
 
 
+# Grids with every region kind of the TMA-staged kernels: interior tiles off
+# and on the z slabs, x-layer and y-layer edge tiles and corner tiles (the
+# interior needs nx >= 72 and ny >= 24 at a 4-cell layer); ragged tiles too.
+@pytest.mark.parametrize("shape,npml,nsteps", [((40, 44, 104), 4, 40), ((52, 37, 100), 5, 45)])
+def test_tiled_all_region_kinds(shape, npml, nsteps, monkeypatch):
+    d, med, p0, rec = _random_case(shape, npml, 500 + npml, L=13)
+    o = Oracle(d.as_dict(), *med)
+    g = make_grid(d, med)
+    tr = g.forward(cuda(p0), rec, nsteps).cpu().numpy()
+    assert rel_l2(tr, o.forward(p0, rec, nsteps)) <= TOL
+    y = np.random.default_rng(8).standard_normal(tr.shape).astype(np.float32)
+    img = g.adjoint(cuda(y), rec).cpu().numpy()
+    assert rel_l2(img, o.adjoint(y, rec)) <= TOL
+    # and the one-thread-per-point kernels agree to FP32 rounding
+    monkeypatch.setenv("PACT_KERNELS", "direct")
+    g_d = make_grid(d, med)
+    monkeypatch.delenv("PACT_KERNELS")
+    assert rel_l2(tr, g_d.forward(cuda(p0), rec, nsteps).cpu().numpy()) <= 1e-5
+    assert rel_l2(img, g_d.adjoint(cuda(y), rec).cpu().numpy()) <= 1e-5
+
+
 def test_tiled_matches_direct(monkeypatch):
     """Both kernel families compute the same operator (agreement to FP32 rounding)."""
     d, med, p0, rec = _random_case((30, 27, 44), 4, 400)

@@ -47,6 +47,11 @@ def test_mixed_solves_match_solo():
     cases.append(("adj", d, med, p0, rec, 38))
     wp = synth.plain_fluid_64(npml=3, nsteps=50)
     cases.append(("adj", wp.desc, wp.medium, wp.p0, wp.rec, 50))
+    # grids with interior, z-slab, edge and corner work items
+    d, med, p0, rec = _random((40, 44, 104), 4, 24, 19)
+    cases.append(("fwd", d, med, p0, rec, 41))
+    d, med, p0, rec = _random((52, 37, 100), 5, 25, 23)
+    cases.append(("adj", d, med, p0, rec, 47))
     grids, bufs, solo = [], [], []
     rng = np.random.default_rng(3)
     for kind, d, med, p0, rec, ns in cases:
