@@ -1141,8 +1141,11 @@ void make_regions(const StepParams& p, long slots_inner, long slots_edge, long s
         add_region(outer, 0, txlo, tyhi + 1, nty, 0, p.nz, zk, PM_FULL, outer_blocks);
         add_region(outer, txhi + 1, ntx, tyhi + 1, nty, 0, p.nz, zk, PM_FULL, outer_blocks);
     }
-    const int za = P > 0 ? std::min(P, p.nz) : 0;  // planes [za, zb) are off the z slabs
-    const int zb = P > 0 ? std::max(za, p.nz - P - 1) : p.nz;
+    // Output planes [za, zb) run without layer code: their z differences reach
+    // two planes up and down, and the adjoint differences fields that carry
+    // z-layer terms on the slab planes, so the reach must stay off the slabs.
+    const int za = P > 0 ? std::min(P + 2, p.nz) : 0;
+    const int zb = P > 0 ? std::max(za, p.nz - P - 3) : p.nz;
     add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, chunk_planes(tiles, zb - za, slots_inner), PM_NONE,
                inner_blocks);
     add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, 0, za, za, PM_Z, inner_blocks);
