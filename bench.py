@@ -131,11 +131,13 @@ def slab_points(d):
     return [d.nz * d.ny * W, d.nz * W * d.nx, W * d.ny * d.nx]
 
 
-def algorithmic_bytes(kind, d, L):
-    """Compulsory DRAM bytes of one launch: every array the kernel must read
-    once and write once (neighbour reads served from cache are not counted)."""
-    N = d.N
-    S = sum(slab_points(d))
+def algorithmic_bytes(kind, d, L, points=None, slab=None):
+    """Compulsory DRAM bytes of one launch set of a role: every array the
+    kernels must read once and write once at the points they update
+    (neighbour reads served from cache are not counted).  points / slab: grid
+    points and C-PML slab points the role updates (default: the whole grid)."""
+    N = d.N if points is None else points
+    S = sum(slab_points(d)) if slab is None else slab
     f = 4
     if kind == "fwd_velocity":   # read 6 sigma, 3 u, rho, alpha; write 3 u; phi^{ij} r+w on slabs
         return f * (11 * N + 3 * N) + 2 * f * 3 * S
@@ -145,6 +147,8 @@ def algorithmic_bytes(kind, d, L):
         return f * (11 * N + 3 * N) + f * 3 * S + 2 * f * 3 * S
     if kind == "adj_b":          # read 3 w, 6 Q, lambda, mu; write 6 Q; phi~ read, psi^ r+w on slabs
         return f * (11 * N + 6 * N) + f * 3 * S + 2 * f * 3 * S
+    if kind in ("fwd_fused", "adj_fused"):  # read 9 fields, rho, alpha, lambda, 1/mu; write 9 fields
+        return f * (9 + 4 + 9) * N
     if kind == "sample":
         return f * (3 * 8 * L + L) + 8 * 8 * L
     if kind == "inject":         # 3 normal Q r+w and lambda, mu at the 8 corners of each receiver
@@ -341,17 +345,25 @@ def run_ours(args):
     value = updates / (ms * 1e-3)
 
     # roofline of the dominant kernel (measured live over the timed region)
-    steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b"]
+    steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "fwd_fused", "adj_fused"]
+    pts = {k: g.role_points(k) for k in steps_kinds}
     dom = max(steps_kinds, key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
     avg_s = dom_ms * 1e-3 / max(n_launch, 1)
-    alg = algorithmic_bytes(dom, d, L)
+    alg = algorithmic_bytes(dom, d, L, *pts[dom])
     pk, which = peaks()
     achieved = alg / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "peak_source": which + " (hbm_gbs, STREAM-style copy)",
                 "traffic": traffic_for(dom), "algorithmic_bytes_per_launch": alg,
-                "avg_launch_ms": avg_s * 1e3, "bytes_per_update": alg / d.N}
+                "avg_launch_ms": avg_s * 1e3, "bytes_per_update": alg / max(1, pts[dom][0]),
+                "grid_points_per_launch": pts[dom][0]}
+    # the whole step: algorithmic bytes of every role over the step's device time
+    step_bytes = sum(algorithmic_bytes(k, d, L, *pts[k]) * prof[k][0] for k in steps_kinds if prof[k][0])
+    step_ms = sum(prof[k][1] for k in steps_kinds)
+    roofline["step"] = {"algorithmic_bytes_per_step_pair": step_bytes / K, "achieved": step_bytes / (step_ms * 1e-3) / 1e9,
+                        "frac": step_bytes / (step_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                        "bytes_per_update": step_bytes / (2.0 * d.N * K)}
     kernels = {k: {"invocations": v[0], "ms": v[1]} for k, v in prof.items() if v[0] and k != "all"}
     gpu_launches = int(prof["all"][0])  # kernel launches in the timed region (a step half is 3 kernels)
 

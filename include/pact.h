@@ -94,7 +94,13 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
  * memory variables phi, then stress and memory variables psi; Appendix A.3) and
  * sample.  p0: device, N floats.  traces: device, (nsteps+1)*L floats,
  * overwritten.  nsteps >= 0, L >= 1.  Errors: PACT_EINVAL, PACT_ESTATE (no
- * medium), PACT_ECUDA. */
+ * medium), PACT_ENOMEM, PACT_ECUDA.
+ * With PACT_FUSED=1 in the environment at pact_create_grid, on grids with
+ * nx % 4 == 0 whose interior holds a region off the C-PML slabs, the interior
+ * tiles run one single-pass (velocity + stress) kernel per step on two
+ * wavefield buffers; the first pact_forward / pact_adjoint on such a handle
+ * then allocates the second buffer (9N floats).  By default every tile runs
+ * the in-place velocity and stress kernels. */
 int pact_forward(pact_handle h, const float* p0, const float* rec_xyz, int L, int nsteps, float* traces);
 
 /* p_adj = H^T p_hat (Eq. (adjHPML)) by the backward recursion of Eq. (AdjupPML):
@@ -118,9 +124,11 @@ int pact_destroy(pact_handle h);
  * The pointer stays valid until the next failing call on the same handle. */
 const char* pact_last_error(pact_handle h);
 
-/* Device bytes a handle with this desc will allocate (fields, medium, C-PML
- * slabs and tables, receiver tables for L receivers).  Used for admission
- * against a memory budget.  Errors: PACT_EINVAL. */
+/* Device bytes a handle with this desc will allocate for serving (fields,
+ * medium, C-PML slabs and tables, receiver tables for L receivers; pact_begin
+ * runs in place on one wavefield buffer).  Used for admission against a
+ * memory budget.  pact_forward / pact_adjoint may add a second wavefield
+ * buffer of 9N floats (see pact_forward).  Errors: PACT_EINVAL. */
 int pact_query_bytes(const pact_grid_desc* desc, int L, int nsteps, size_t* bytes);
 
 /* Diagnostics: copy the current wavefield to HOST memory, 9*N floats in the
@@ -199,8 +207,10 @@ int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const flo
 #define PACT_K_INJECT 5       /* receiver injection Theta^T                       */
 #define PACT_K_SOURCE 6       /* source tau                                       */
 #define PACT_K_READOUT 7      /* read-out tau^T                                   */
-#define PACT_NKIND 8
-#define PACT_K_ALL 8          /* pact_profile_read only: every kernel launch     */
+#define PACT_K_FWD_FUSED 8    /* single-pass velocity + stress kernel, forward    */
+#define PACT_K_ADJ_FUSED 9    /* single-pass kernel of one adjoint step           */
+#define PACT_NKIND 10
+#define PACT_K_ALL 10         /* pact_profile_read only: every kernel launch     */
 
 /* Reset this handle's launch counters and, if enable != 0, start recording a
  * CUDA event after every kernel launch on the handle's stream (so a launch's
@@ -215,6 +225,13 @@ int pact_profile(pact_handle h, int enable);
  * device time of all of them.  Synchronises the stream.
  * Errors: PACT_EINVAL (kind out of range or NULL output). */
 int pact_profile_read(pact_handle h, int kind, long long* launches, double* total_ms);
+
+/* Grid points that one invocation of a step role (PACT_K_FWD_VELOCITY,
+ * PACT_K_FWD_STRESS, PACT_K_ADJ_A, PACT_K_ADJ_B, PACT_K_FWD_FUSED,
+ * PACT_K_ADJ_FUSED) updates on this handle's grid, and the C-PML slab points
+ * among them; 0 for a role that this grid does not run.  Used to turn a
+ * role's device time into algorithmic bytes per second.  Errors: PACT_EINVAL. */
+int pact_role_points(pact_handle h, int kind, long long* points, long long* slab_points);
 
 #ifdef __cplusplus
 }

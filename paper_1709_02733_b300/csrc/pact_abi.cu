@@ -81,6 +81,16 @@ struct pact_grid {
     // TMA-staged kernels (nx % 4 == 0) or the direct kernels
     bool tiled = false;
     TmaSet tm{};
+    // single-pass interior kernel on two wavefield buffers: fields and
+    // fields2 (allocated at the first solve); cur = the buffer holding the
+    // state.  tmp[c] / fmp[c]: maps of a step whose input is buffer c (the
+    // two-pass kernels read the stresses of buffer c and the velocities of
+    // buffer 1-c; the single-pass kernel the stresses of buffer c).
+    bool fused = false;
+    float* fields2 = nullptr;
+    int cur = 0;
+    TmaSet tmp[2]{};
+    FusedMaps fmp[2]{};
     // the C-PML frame launches overlap the interior launches on this stream
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -197,7 +207,11 @@ void pml_coef(int n, int P, double dx, double dt, double vmax, double R0, double
     chi = 1.0;
 }
 
-static StepParams make_params(pact_handle h) {
+static float* buffer(pact_handle h, int c) { return c == 0 ? h->fields : h->fields2; }
+
+// Parameters of a step reading wavefield buffer `in` and writing buffer
+// `out` (out < 0: in place, which the direct, serving and small kernels use).
+static StepParams make_params(pact_handle h, int in = 0, int out = -1) {
     StepParams p{};
     const pact_grid_desc& d = h->d;
     p.nx = d.nx;
@@ -206,12 +220,17 @@ static StepParams make_params(pact_handle h) {
     p.P = d.npml;
     p.dt = (float)d.dt;
     p.inv_dx = (float)(1.0 / d.dx);
-    for (int i = 0; i < 3; ++i) p.u[i] = h->fields + i * h->N;
-    for (int v = 0; v < 6; ++v) p.s[v] = h->fields + (3 + v) * h->N;
+    float* fi = buffer(h, in);
+    float* fo = out < 0 ? fi : buffer(h, out);
+    for (int i = 0; i < 3; ++i) p.u[i] = fi + i * h->N;
+    for (int v = 0; v < 6; ++v) p.s[v] = fi + (3 + v) * h->N;
+    for (int i = 0; i < 3; ++i) p.u_out[i] = fo + i * h->N;
+    for (int v = 0; v < 6; ++v) p.s_out[v] = fo + (3 + v) * h->N;
     p.rho = h->medium;
     p.lam = h->medium + h->N;
     p.mu = h->medium + 2 * h->N;
     p.alpha = h->medium + 3 * h->N;
+    p.rmu = h->medium + 4 * h->N;
     for (int a = 0; a < 3; ++a)
         for (int l = 0; l < 2; ++l)
             for (int w = 0; w < 3; ++w) p.tab[a][l][w] = h->tables + ((a * 2 + l) * 3 + w) * (size_t)h->nmax;
@@ -357,12 +376,22 @@ static int device_status(pact_handle h) {
     return PACT_OK;
 }
 
-static void fwd_step(pact_handle h, const StepParams& p) {
+// One step of H (fwd) or of H^T: the velocity-family and stress-family
+// launches, with the single-pass interior launch between them when the
+// handle runs on two buffers (the step then reads buffer c and writes 1-c).
+static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
+    const bool fz = h->fused;
+    const TmaSet& tm = fz ? h->tmp[c] : h->tm;
+    const SplitStreams ss{h->stream, fz ? nullptr : h->aux, h->ev_fork, h->ev_join};
+    mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, fz));
+    if (fz) mark(h, adj ? PACT_K_ADJ_FUSED : PACT_K_FWD_FUSED, launch_fused_step(adj, p, h->fmp[c], err, h->stream));
+    mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, tm, err, ss, fz));
+}
+
+static void fwd_step(pact_handle h, const StepParams& p, int c) {
     if (h->tiled) {
-        const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join};
-        mark(h, PACT_K_FWD_VELOCITY, launch_vel_tiled(false, p, h->tm, err, ss));
-        mark(h, PACT_K_FWD_STRESS, launch_str_tiled(false, p, h->tm, err, ss));
+        tiled_step(h, p, c, false);
     } else {
         launch_fwd_velocity(p, h->stream);
         mark(h, PACT_K_FWD_VELOCITY);
@@ -371,12 +400,9 @@ static void fwd_step(pact_handle h, const StepParams& p) {
     }
 }
 
-static void adj_step(pact_handle h, const StepParams& p) {
-    int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
+static void adj_step(pact_handle h, const StepParams& p, int c) {
     if (h->tiled) {
-        const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join};
-        mark(h, PACT_K_ADJ_A, launch_vel_tiled(true, p, h->tm, err, ss));
-        mark(h, PACT_K_ADJ_B, launch_str_tiled(true, p, h->tm, err, ss));
+        tiled_step(h, p, c, true);
     } else {
         launch_adj_a(p, h->stream);
         mark(h, PACT_K_ADJ_A);
@@ -385,40 +411,86 @@ static void adj_step(pact_handle h, const StepParams& p) {
     }
 }
 
+// The second wavefield buffer and the maps of both step parities, made at
+// the first solve of a handle that runs the single-pass kernel.
+static int ensure_pingpong(pact_handle h) {
+    if (!h->fused || h->fields2) return PACT_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMalloc(&h->fields2, 9 * h->N * sizeof(float)));
+    for (int c = 0; c < 2; ++c) {
+        float* fi = buffer(h, c);
+        float* fo = buffer(h, 1 - c);
+        float* arrays[TM_N];
+        for (int i = 0; i < 3; ++i) arrays[TM_U0 + i] = fo + i * h->N;
+        for (int v = 0; v < 6; ++v) arrays[TM_S0 + v] = fi + (3 + v) * h->N;
+        arrays[TM_RHO] = h->medium;
+        arrays[TM_LAM] = h->medium + h->N;
+        arrays[TM_MU] = h->medium + 4 * h->N;
+        arrays[TM_ALPHA] = h->medium + 3 * h->N;
+        float* farr[FM_N];
+        for (int v = 0; v < 6; ++v) farr[v] = fi + (3 + v) * h->N;
+        farr[6] = h->medium;
+        farr[7] = h->medium + 3 * h->N;
+        if (make_tma_set(&h->tmp[c], arrays, h->d.nx, h->d.ny, h->d.nz) != 0 ||
+            make_fused_maps(&h->fmp[c], farr, h->d.nx, h->d.ny, h->d.nz) != 0) {
+            cudaFree(h->fields2);
+            h->fields2 = nullptr;
+            return fail(h, PACT_ECUDA, "encoding the tensor maps of the second wavefield buffer failed");
+        }
+    }
+    return PACT_OK;
+}
+
 static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps) {
-    int rc = zero_state(h);
+    int rc = ensure_pingpong(h);
     if (rc) return rc;
-    const StepParams p = make_params(h);
+    h->cur = 0;
+    rc = zero_state(h);
+    if (rc) return rc;
     const RecTable r = make_rec(h);
+    StepParams p = make_params(h, 0);
     mark(h, -1);
     launch_source(p0, p, h->stream);
     mark(h, PACT_K_SOURCE);
     launch_sample(p, r, traces, h->stream);
     mark(h, PACT_K_SAMPLE);
+    int c = 0;
     for (int m = 1; m <= nsteps; ++m) {
-        fwd_step(h, p);
+        const int out = h->fused ? 1 - c : -1;
+        fwd_step(h, make_params(h, c, out), c);
+        if (out >= 0) c = out;
+        p = make_params(h, c);
         launch_sample(p, r, traces + (size_t)m * h->L, h->stream);
         mark(h, PACT_K_SAMPLE);
     }
+    h->cur = c;
     CK(h, cudaGetLastError());
     return PACT_OK;
 }
 
 static int run_adjoint(pact_handle h, const float* traces, float* image, int nsteps) {
-    int rc = zero_state(h);
+    int rc = ensure_pingpong(h);
     if (rc) return rc;
-    const StepParams p = make_params(h);
+    h->cur = 0;
+    rc = zero_state(h);
+    if (rc) return rc;
     const RecTable r = make_rec(h);
+    StepParams p = make_params(h, 0);
     mark(h, -1);
     launch_inject(p, r, traces + (size_t)nsteps * h->L, h->stream);
     mark(h, PACT_K_INJECT, r.ncorner > 0);
+    int c = 0;
     for (int m = nsteps; m >= 1; --m) {
-        adj_step(h, p);
+        const int out = h->fused ? 1 - c : -1;
+        adj_step(h, make_params(h, c, out), c);
+        if (out >= 0) c = out;
+        p = make_params(h, c);
         launch_inject(p, r, traces + (size_t)(m - 1) * h->L, h->stream);
         mark(h, PACT_K_INJECT, r.ncorner > 0);
     }
     launch_readout(image, p, h->stream);
     mark(h, PACT_K_READOUT);
+    h->cur = c;
     CK(h, cudaGetLastError());
     return PACT_OK;
 }
@@ -484,6 +556,28 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
         arrays[TM_MU] = h->medium + 4 * h->N;  // the TMA-staged kernels read 1/mu
         arrays[TM_ALPHA] = h->medium + 3 * h->N;
         h->tiled = make_tma_set(&h->tm, arrays, desc->nx, desc->ny, desc->nz) == 0;
+        // PACT_FUSED=1 runs the interior tiles on the single-pass kernel (two
+        // wavefield buffers); by default every tile runs the in-place
+        // two-pass kernels, which measured faster on B300
+        const char* fenv = getenv("PACT_FUSED");
+        if (h->tiled && fenv && std::strcmp(fenv, "1") == 0) {
+            StepParams q{};
+            q.nx = desc->nx;
+            q.ny = desc->ny;
+            q.nz = desc->nz;
+            q.P = desc->npml;
+            RegionList rl;
+            int blocks = 0;
+            h->fused = fused_plan(q, rl, blocks);
+            // every grid point must be updated by exactly one launch of each
+            // half: the regions are disjoint by construction, so their point
+            // counts must add up to N
+            if (h->fused) {
+                const long long nf = role_points(2, true, q);
+                h->fused = role_points(0, true, q) + nf == (long long)h->N &&
+                           role_points(1, true, q) + nf == (long long)h->N;
+            }
+        }
         // PACT_OVERLAP=0 runs the frame and interior launches one after the other
         const char* oenv = getenv("PACT_OVERLAP");
         if (h->tiled && !(oenv && std::strcmp(oenv, "0") == 0)) {
@@ -607,6 +701,7 @@ int pact_destroy(pact_handle h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->fields);
+    cudaFree(h->fields2);
     cudaFree(h->medium);
     cudaFree(h->tables);
     cudaFree(h->scratch_u32);
@@ -637,7 +732,8 @@ int pact_get_wavefield(pact_handle h, float* host_out) {
     if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
     if (!host_out) return fail(h, PACT_EINVAL, "host_out is NULL");
     CK(h, cudaSetDevice(h->device));
-    CK(h, cudaMemcpyAsync(host_out, h->fields, 9 * h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(host_out, buffer(h, h->cur), 9 * h->N * sizeof(float), cudaMemcpyDeviceToHost,
+                          h->stream));
     return device_status(h);
 }
 
@@ -669,12 +765,37 @@ int pact_profile_read(pact_handle h, int kind, long long* launches, double* tota
     return device_status(h);
 }
 
+int pact_role_points(pact_handle h, int kind, long long* points, long long* slab_points) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (!points || !slab_points) return fail(h, PACT_EINVAL, "NULL output");
+    const bool vel = kind == PACT_K_FWD_VELOCITY || kind == PACT_K_ADJ_A;
+    const bool str = kind == PACT_K_FWD_STRESS || kind == PACT_K_ADJ_B;
+    const bool fz = kind == PACT_K_FWD_FUSED || kind == PACT_K_ADJ_FUSED;
+    if (!vel && !str && !fz) return fail(h, PACT_EINVAL, "kind is not a step role");
+    CK(h, cudaSetDevice(h->device));
+    const StepParams p = make_params(h);
+    long long slabs = 0;
+    for (int a = 0; a < 3; ++a) slabs += (long long)h->slab_n[a];
+    if (fz) {
+        *points = h->fused ? role_points(2, true, p) : 0;
+        *slab_points = 0;  // the single-pass region lies off the slabs
+    } else if (h->tiled) {
+        *points = role_points(vel ? 0 : 1, h->fused, p);
+        *slab_points = slabs;
+    } else {
+        *points = (long long)h->N;
+        *slab_points = slabs;
+    }
+    return PACT_OK;
+}
+
 int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_xyz, int L, int nsteps, float* out) {
     int rc = precheck(h, in, out, nsteps);
     if (rc) return rc;
     if (!h->tiled) return fail(h, PACT_EINVAL, "serving uses the TMA-staged kernels: nx must be a multiple of 4");
     rc = set_receivers(h, rec_xyz, L);
     if (rc) return rc;
+    h->cur = 0;
     rc = zero_state(h);
     if (rc) return rc;
     const StepParams p = make_params(h);

@@ -26,12 +26,15 @@ struct StepParams {
     int nx, ny, nz;
     int P;                      // C-PML thickness (0: none)
     float dt, inv_dx;
-    float* u[3];                // velocity components
-    float* s[6];                // stress, Voigt order
+    float* u[3];                // velocity components (input of a step)
+    float* s[6];                // stress, Voigt order (input of a step)
+    float* u_out[3];            // where the TMA-staged kernels write the new values:
+    float* s_out[6];            // u / s themselves (in place) or the other buffer
     const float* rho;
     const float* lam;
     const float* mu;
     const float* alpha;
+    const float* rmu;           // 1/mu (+inf at fluid nodes)
     const float* tab[3][2][3];  // [axis][lattice][a, b, chi]
     float* phi[3][3];           // phi^{ij}: [i][j], slab of axis j
     float* psi[3][3];           // psi^{ij}: [i][j], slab of axis j

@@ -590,7 +590,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                     }
                     const float res = ADJ ? (1.0f - dt * ab[i]) * cu[i] - __fdividef(dt * dt, rb[i]) * acc
                                           : (1.0f - dt * ab[i]) * cu[i] + __fdividef(dt, rb[i]) * acc;
-                    p.u[i][gi] = res;
+                    p.u_out[i][gi] = res;
                 }
             }
         }
@@ -903,7 +903,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                     res[5] = so[5] - m12 * (du[0][1] + du[1][0]);
                 }
 #pragma unroll
-                for (int v = 0; v < 6; ++v) p.s[v][gi] = res[v];
+                for (int v = 0; v < 6; ++v) p.s_out[v][gi] = res[v];
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -1089,14 +1089,14 @@ int add_region(RegionList& rl, int tx0, int tx1, int ty0, int ty1, int za, int z
 
 // z chunk length for `tiles` tile columns of zlen planes run by `slots`
 // concurrently resident blocks: the chunk count that fills the last wave
-// best, discounted by the three extra planes every chunk loads.
-int chunk_planes(long tiles, int zlen, long slots) {
+// best, discounted by the `extra` planes every chunk loads beyond its own.
+int chunk_planes(long tiles, int zlen, long slots, double extra = 3.0) {
     const int cmax = std::max(1, zlen / 16);
     int best = 1;
     double best_s = -1.0;
     for (int c = 1; c <= cmax; ++c) {
         const double w = (double)tiles * c / (double)std::max(1L, slots);
-        const double sc = w / std::ceil(w) / (1.0 + 3.0 * c / zlen);
+        const double sc = w / std::ceil(w) / (1.0 + extra * c / zlen);
         if (sc > best_s + 1e-9) {
             best_s = sc;
             best = c;
@@ -1105,15 +1105,50 @@ int chunk_planes(long tiles, int zlen, long slots) {
     return (zlen + best - 1) / best;
 }
 
+// Tiles and planes of the single-pass kernel: the whole reach of a tile
+// (stress points x0-3 .. x0+TX+2, y0-3 .. y0+TY+2; velocity points within)
+// inside [P, n-P-2] on x and y (the grid itself without a layer), and output
+// planes [P+3, hi-2) whose reach (zs-3 .. zs+3) stays inside [P, hi] too.
+struct FusedBox {
+    int txlo, txhi, tylo, tyhi, za, zb;  // inclusive tile ranges, planes [za, zb)
+};
+bool fused_box(const StepParams& p, FusedBox& f) {
+    const int P = p.P;
+    const int hx = P > 0 ? p.nx - P - 2 : p.nx - 1, hy = P > 0 ? p.ny - P - 2 : p.ny - 1;
+    const int hz = P > 0 ? p.nz - P - 2 : p.nz - 1;
+    const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
+    f.txlo = ntx;
+    f.txhi = -1;
+    for (int t = 0; t < ntx; ++t)
+        if (t * TX - 3 >= P && t * TX + TX + 2 <= hx) {
+            f.txlo = std::min(f.txlo, t);
+            f.txhi = std::max(f.txhi, t);
+        }
+    f.tylo = nty;
+    f.tyhi = -1;
+    for (int t = 0; t < nty; ++t)
+        if (t * TY - 3 >= P && t * TY + TY + 2 <= hy) {
+            f.tylo = std::min(f.tylo, t);
+            f.tyhi = std::max(f.tyhi, t);
+        }
+    f.za = P + 3;
+    f.zb = hz - 2;
+    return f.txlo <= f.txhi && f.tylo <= f.tyhi && f.zb - f.za >= 8;
+}
+
 // Work regions of one half step.  Interior launch: the interior tiles off
 // the z slabs (no layer code; long chunks, first) and on the z slabs (z-layer
 // code; one chunk per slab, last, so that they fill the launch's tail).
 // Frame: the tiles around the interior ones, all planes, in up to eight
 // rectangles: the edges (x layer only, y layer only; one launch) and the
-// corners (both layers; a second launch), each chunked for its own launch.  With P = 0 every tile is interior and there
-// are no slabs.
+// corners (both layers; a second launch), each chunked for its own launch.
+// With P = 0 every tile is interior and there are no slabs.  With fb given,
+// the tiles and planes of the single-pass kernel are left out of the
+// interior launch, which then runs the rest of the interior tiles (z-layer
+// code): the fused tiles' planes below and above the fused planes and every
+// plane of the interior tiles beside the fused ones.
 void make_regions(const StepParams& p, long slots_inner, long slots_edge, long slots_corner, RegionList& inner,
-                  int& inner_blocks, RegionList& outer, int& outer_blocks) {
+                  int& inner_blocks, RegionList& outer, int& outer_blocks, const FusedBox* fb = nullptr) {
     inner.n = outer.n = 0;
     inner_blocks = outer_blocks = 0;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY;
@@ -1141,6 +1176,19 @@ void make_regions(const StepParams& p, long slots_inner, long slots_edge, long s
         add_region(outer, 0, txlo, tyhi + 1, nty, 0, p.nz, zk, PM_FULL, outer_blocks);
         add_region(outer, txhi + 1, ntx, tyhi + 1, nty, 0, p.nz, zk, PM_FULL, outer_blocks);
     }
+    if (fb) {
+        // the fused tiles lie inside the interior ones (their reach is wider)
+        const FusedBox& f = *fb;
+        const long ring = tiles - (long)(f.txhi + 1 - f.txlo) * (f.tyhi + 1 - f.tylo);
+        const int zr = chunk_planes(std::max(1L, ring), p.nz, slots_inner);
+        add_region(inner, f.txlo, f.txhi + 1, f.tylo, f.tyhi + 1, 0, f.za, f.za, PM_Z, inner_blocks);
+        add_region(inner, f.txlo, f.txhi + 1, f.tylo, f.tyhi + 1, f.zb, p.nz, p.nz - f.zb, PM_Z, inner_blocks);
+        add_region(inner, txlo, txhi + 1, tylo, f.tylo, 0, p.nz, zr, PM_Z, inner_blocks);
+        add_region(inner, txlo, txhi + 1, f.tyhi + 1, tyhi + 1, 0, p.nz, zr, PM_Z, inner_blocks);
+        add_region(inner, txlo, f.txlo, f.tylo, f.tyhi + 1, 0, p.nz, zr, PM_Z, inner_blocks);
+        add_region(inner, f.txhi + 1, txhi + 1, f.tylo, f.tyhi + 1, 0, p.nz, zr, PM_Z, inner_blocks);
+        return;
+    }
     // Output planes [za, zb) run without layer code: their z differences reach
     // two planes up and down, and the adjoint differences fields that carry
     // z-layer terms on the slab planes, so the reach must stay off the slabs.
@@ -1154,6 +1202,7 @@ void make_regions(const StepParams& p, long slots_inner, long slots_edge, long s
 
 struct LaunchPlan {
     int dev, nx, ny, nz, P, family;
+    bool fz;
     RegionList inner, edge, corner;  // interior, frame edges (PM_X, PM_Y), frame corners (PM_FULL)
     int inner_blocks, edge_blocks, corner_blocks;
 };
@@ -1201,7 +1250,7 @@ long device_slots(const void* fn, size_t smem, int dev) {
     return (long)sms * std::max(1, per_sm);
 }
 
-LaunchPlan plan_for(int family, const StepParams& p) {
+LaunchPlan plan_for(int family, const StepParams& p, bool fz) {
     static LaunchPlan plans[32];
     static int nplans = 0;
     static std::mutex mu;
@@ -1210,7 +1259,8 @@ LaunchPlan plan_for(int family, const StepParams& p) {
     std::lock_guard<std::mutex> lock(mu);
     for (int i = 0; i < nplans; ++i) {
         const LaunchPlan& L = plans[i];
-        if (L.dev == dev && L.family == family && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz && L.P == p.P)
+        if (L.dev == dev && L.family == family && L.fz == fz && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz &&
+            L.P == p.P)
             return L;
     }
     const long si = device_slots(fam_fn(family, PM_NONE), fam_smem(family, PM_NONE), dev);
@@ -1219,17 +1269,31 @@ LaunchPlan plan_for(int family, const StepParams& p) {
     LaunchPlan& L = plans[nplans % 32];
     L.dev = dev;
     L.family = family;
+    L.fz = fz;
     L.nx = p.nx;
     L.ny = p.ny;
     L.nz = p.nz;
     L.P = p.P;
     RegionList outer;
     int outer_blocks = 0;
-    make_regions(p, si, se, sc, L.inner, L.inner_blocks, outer, outer_blocks);
+    FusedBox fb;
+    const bool use_fb = fz && fused_box(p, fb);
+    make_regions(p, si, se, sc, L.inner, L.inner_blocks, outer, outer_blocks, use_fb ? &fb : nullptr);
     L.edge_blocks = select_kinds(outer, (1u << PM_X) | (1u << PM_Y), L.edge);
     L.corner_blocks = select_kinds(outer, 1u << PM_FULL, L.corner);
     nplans = std::min(nplans + 1, 32);
     return L;
+}
+
+long long region_points(const RegionList& rl, const StepParams& p) {
+    long long n = 0;
+    for (int k = 0; k < rl.n; ++k) {
+        const Region& r = rl.r[k];
+        const long long ex = std::min(r.tx1 * TX, p.nx) - r.tx0 * TX;
+        const long long ey = std::min(r.ty1 * TY, p.ny) - r.ty0 * TY;
+        n += ex * ey * (long long)(r.zb - r.za);
+    }
+    return n;
 }
 
 }  // namespace
@@ -1237,8 +1301,8 @@ LaunchPlan plan_for(int family, const StepParams& p) {
 // The frame launch goes to `aux` (when given) between a fork and a join
 // event, so that it overlaps the interior launch on `st`.
 template <bool ADJ>
-static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
-    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p);
+static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
+    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, fz);
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
     const bool split = ss.aux && nframe && L.inner_blocks;
@@ -1262,8 +1326,8 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
 }
 
 template <bool ADJ>
-static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
-    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p);
+static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
+    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, fz);
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
     const bool split = ss.aux && nframe && L.inner_blocks;
@@ -1341,12 +1405,78 @@ void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& 
     nouter = rechunk(outer);
 }
 
-int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
-    return adj ? launch_vel_impl<true>(p, tm, err, ss) : launch_vel_impl<false>(p, tm, err, ss);
+int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
+    return adj ? launch_vel_impl<true>(p, tm, err, ss, fz) : launch_vel_impl<false>(p, tm, err, ss, fz);
 }
 
-int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss) {
-    return adj ? launch_str_impl<true>(p, tm, err, ss) : launch_str_impl<false>(p, tm, err, ss);
+int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
+    return adj ? launch_str_impl<true>(p, tm, err, ss, fz) : launch_str_impl<false>(p, tm, err, ss, fz);
+}
+
+// The fused region: one rectangle of tiles over the fused planes, in z
+// chunks that fill the last wave of resident single-pass blocks best (every
+// chunk computes four velocity planes and loads seven stress planes beyond
+// its own).
+bool fused_plan(const StepParams& p, RegionList& rl, int& blocks) {
+    rl.n = 0;
+    blocks = 0;
+    FusedBox f;
+    if (!fused_box(p, f)) return false;
+    static long slots[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!slots[dev]) {
+        // device_slots also raises the dynamic shared-memory limit of the kernel
+        slots[dev] = device_slots(fused_fn(false), fused_smem(), dev);
+        device_slots(fused_fn(true), fused_smem(), dev);
+    }
+    const long tiles = (long)(f.txhi + 1 - f.txlo) * (f.tyhi + 1 - f.tylo);
+    add_region(rl, f.txlo, f.txhi + 1, f.tylo, f.tyhi + 1, f.za, f.zb, chunk_planes(tiles, f.zb - f.za, slots[dev], 6.0),
+               PM_NONE, blocks);
+    return blocks > 0;
+}
+
+int launch_fused_step(bool adj, const StepParams& p, const FusedMaps& fm, int* err, cudaStream_t st) {
+    struct Cached {
+        int dev, nx, ny, nz, P, blocks;
+        RegionList rl;
+    };
+    static Cached cache[16];
+    static int ncache = 0;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Cached c{};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        int i = 0;
+        for (; i < ncache; ++i)
+            if (cache[i].dev == dev && cache[i].nx == p.nx && cache[i].ny == p.ny && cache[i].nz == p.nz &&
+                cache[i].P == p.P)
+                break;
+        if (i == ncache) {
+            Cached& n = cache[ncache % 16];
+            n = {dev, p.nx, p.ny, p.nz, p.P, 0, {}};
+            fused_plan(p, n.rl, n.blocks);
+            i = ncache % 16;
+            ncache = std::min(ncache + 1, 16);
+        }
+        c = cache[i];
+    }
+    if (c.blocks <= 0) return 0;
+    launch_fused(adj, p, fm, c.rl, c.blocks, err, st);
+    return 1;
+}
+
+long long role_points(int family, bool fz, const StepParams& p) {
+    if (family == 2) {
+        RegionList rl;
+        int blocks = 0;
+        return fused_plan(p, rl, blocks) ? region_points(rl, p) : 0;
+    }
+    const LaunchPlan L = plan_for(family == 0 ? 0 : 2, p, fz);
+    return region_points(L.inner, p) + region_points(L.edge, p) + region_points(L.corner, p);
 }
 
 // Tensor maps: one 3-D float32 map per array, box 40 x 13 x 1, zero fill.

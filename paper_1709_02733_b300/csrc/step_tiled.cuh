@@ -59,9 +59,33 @@ struct SplitStreams {
     cudaStream_t aux;
     cudaEvent_t fork, join;
 };
-// both return the number of kernels launched
-int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
-int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss);
+// Both return the number of kernels launched.  With fz set the interior
+// tiles and planes that the single-pass kernel takes (fused_plan) are left
+// out: the step is then launch_vel_tiled, launch_fused_step, launch_str_tiled.
+int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
+                     bool fz = false);
+int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
+                     bool fz = false);
+
+// Single-pass (velocity + stress) kernel of the interior tiles (step_fused.cu).
+// Its tensor maps: the six stress-like fields of the input buffer (Voigt
+// order), rho, alpha; box 40 x 14.
+enum { FM_N = 8 };
+struct FusedMaps {
+    CUtensorMap m[FM_N];
+};
+int make_fused_maps(FusedMaps* out, float* const* arrays, int nx, int ny, int nz);
+size_t fused_smem();
+const void* fused_fn(bool adj);
+void launch_fused(bool adj, const StepParams& p, const FusedMaps& fm, const RegionList& rl, int blocks, int* err,
+                  cudaStream_t st);
+// the fused region of a grid (false if the grid has none)
+bool fused_plan(const StepParams& p, RegionList& rl, int& blocks);
+// returns 1 if the fused kernel was launched (0: the grid has no fused region)
+int launch_fused_step(bool adj, const StepParams& p, const FusedMaps& fm, int* err, cudaStream_t st);
+// grid points one launch set of a role updates: family 0 velocity, 1 stress,
+// 2 fused; fz as above
+long long role_points(int family, bool fz, const StepParams& p);
 // persistent multi-instance half step (str = stress family) over a device
 // table: four launches (two directions x frame / interior), launch k taking
 // its work items from the counter next[k], which must be zero beforehand

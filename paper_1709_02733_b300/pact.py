@@ -27,10 +27,12 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 # every symbol include/pact.h declares
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
-           "pact_profile", "pact_profile_read", "pact_forward_noalloc", "pact_begin", "pact_advance", "pact_poll"]
+           "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
+           "pact_advance", "pact_poll"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
-KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout"]
+KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
+         "adj_fused"]
 
 
 class PactError(RuntimeError):
@@ -82,6 +84,7 @@ def load(path: str = SO_PATH):
     lib.pact_forward_noalloc.argtypes = [D, fp, fp, fp, fp, fp, fp, i, i, fp, vp]
     lib.pact_profile.argtypes = [vp, i]
     lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+    lib.pact_role_points.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTS:
         if name != "pact_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -272,3 +275,11 @@ class Grid:
         return out
 
     profile_read = pact_profile_read
+
+    def pact_role_points(self, kind: str):
+        """(grid points, C-PML slab points) one invocation of a step role updates."""
+        n, ns = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        _check(self.lib.pact_role_points(self._h, KINDS.index(kind), ctypes.byref(n), ctypes.byref(ns)), self._h)
+        return int(n.value), int(ns.value)
+
+    role_points = pact_role_points

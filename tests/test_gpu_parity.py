@@ -226,7 +226,7 @@ def test_full_size_512_sampled():
 # TMA-staged kernels (used when nx % 4 == 0): ragged tiles on every axis
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("shape,npml,nsteps", [((23, 19, 36), 3, 40), ((40, 44, 68), 5, 60), ((17, 33, 64), 0, 30),
-                                               ((70, 12, 8), 2, 25)])
+                                               ((70, 12, 8), 2, 25), ((30, 34, 132), 0, 30)])
 def test_tiled_random_medium(shape, npml, nsteps):
     d, med, p0, rec = _random_case(shape, npml, 300 + npml)
     assert d.nx % 4 == 0
@@ -277,3 +277,74 @@ def test_tiled_matches_direct(monkeypatch):
     ia = g_t.adjoint(y, rec).cpu().numpy()
     ib = g_d.adjoint(y, rec).cpu().numpy()
     assert rel_l2(ia, ib) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Single-pass interior kernel (PACT_FUSED=1: two wavefield buffers) against the
+# in-place two-pass kernels: fused regions with and without a layer, of one tile and of
+# several, beside ragged edge tiles.  Every grid point must be written by
+# exactly one launch per half step; a point left out would keep the value of
+# two steps before and show up here.  The two paths differ only by FP32
+# rounding (contraction order).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,npml,nsteps", [((40, 44, 104), 4, 41), ((33, 30, 72), 3, 30), ((48, 50, 132), 0, 35),
+                                               ((60, 61, 100), 6, 52)])
+def test_fused_matches_two_pass(shape, npml, nsteps, monkeypatch):
+    d, med, p0, rec = _random_case(shape, npml, 700 + npml, L=11)
+    g_2 = make_grid(d, med)
+    monkeypatch.setenv("PACT_FUSED", "1")
+    g_f = make_grid(d, med)
+    monkeypatch.delenv("PACT_FUSED")
+    nf = g_f.role_points("fwd_fused")[0]
+    assert nf > 0 and g_2.role_points("fwd_fused")[0] == 0
+    assert g_f.role_points("fwd_velocity")[0] + nf == d.N == g_f.role_points("fwd_stress")[0] + nf
+    a = g_f.forward(cuda(p0), rec, nsteps).cpu().numpy()
+    b = g_2.forward(cuda(p0), rec, nsteps).cpu().numpy()
+    assert rel_l2(a, b) <= 1e-6
+    assert rel_l2(g_f.get_wavefield(), g_2.get_wavefield()) <= 1e-6
+    y = cuda(np.random.default_rng(9).standard_normal(a.shape))
+    ia = g_f.adjoint(y, rec).cpu().numpy()
+    ib = g_2.adjoint(y, rec).cpu().numpy()
+    assert rel_l2(ia, ib) <= 1e-6
+    assert rel_l2(g_f.get_wavefield(), g_2.get_wavefield()) <= 1e-6
+
+
+def test_fused_odd_and_even_step_counts(monkeypatch):
+    """The state ends in either buffer: forward/adjoint results and the
+    wavefield read-back are right after an odd and an even number of steps,
+    and a solve after another one starts from zero."""
+    d, med, p0, rec = _random_case((36, 30, 72), 3, 801, L=7)
+    o = Oracle(d.as_dict(), *med)
+    monkeypatch.setenv("PACT_FUSED", "1")
+    g = make_grid(d, med)
+    monkeypatch.delenv("PACT_FUSED")
+    assert g.role_points("adj_fused")[0] > 0
+    for nsteps in (13, 14):
+        tr = g.forward(cuda(p0), rec, nsteps).cpu().numpy()
+        assert rel_l2(tr, o.forward(p0, rec, nsteps)) <= TOL
+        st = o.run_state(p0, nsteps)
+        v = Oracle.views(st)
+        ref = np.concatenate([v["u"], v["sigma"]])
+        assert rel_l2(g.get_wavefield(), ref) <= TOL
+        y = np.random.default_rng(nsteps).standard_normal(tr.shape).astype(np.float32)
+        img = g.adjoint(cuda(y), rec).cpu().numpy()
+        assert rel_l2(img, o.adjoint(y, rec)) <= TOL
+
+
+def test_fused_inner_product_and_oracle(monkeypatch):
+    """The single-pass path: FP32 inner-product test on a skull-like grid with
+    a fused region, and oracle parity on a random medium."""
+    monkeypatch.setenv("PACT_FUSED", "1")
+    w = synth.skull(96, 0.4e-3, 10, 300, 128, seed=3)
+    g = make_grid(w.desc, w.medium)
+    assert g.role_points("fwd_fused")[0] > 0
+    assert _dot_test(g, w.p0, w.rec, w.nsteps) <= DOT_TOL
+    d, med, p0, rec = _random_case((40, 44, 104), 4, 904, L=13)
+    g = make_grid(d, med)
+    monkeypatch.delenv("PACT_FUSED")
+    assert g.role_points("adj_fused")[0] > 0
+    o = Oracle(d.as_dict(), *med)
+    tr = g.forward(cuda(p0), rec, 37).cpu().numpy()
+    assert rel_l2(tr, o.forward(p0, rec, 37)) <= TOL
+    y = np.random.default_rng(10).standard_normal(tr.shape).astype(np.float32)
+    assert rel_l2(g.adjoint(cuda(y), rec).cpu().numpy(), o.adjoint(y, rec)) <= TOL
