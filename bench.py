@@ -276,6 +276,29 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# replicas on several GPUs (weak scaling, no collective on the data path)
+# --------------------------------------------------------------------------
+def max_over_ranks_of(x, world, device="cpu"):
+    """The slowest rank's value of x (one scalar all-reduce; x itself with
+    one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(updates_per_rank, ms_local, world, device="cpu"):
+    """(job ms, whole-job updates/s): every rank runs its own replica of the
+    workload, the job takes as long as the slowest rank, and the value counts
+    the updates of all ranks."""
+    ms = max_over_ranks_of(ms_local, world, device)
+    return ms, updates_per_rank * world / (ms * 1e-3)
+
+
+# --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
 def run_ours(args):
@@ -302,11 +325,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, device="cuda")
 
     w = make_workload(args.workload)
     d = w.desc
@@ -338,11 +357,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms, value = replica_rate(2.0 * d.N * K, e0.elapsed_time(e1), world, device="cuda")
     prof = g.profile_read()
     g.profile(False)
     updates = 2.0 * d.N * K * world
-    value = updates / (ms * 1e-3)
 
     # roofline of the dominant kernel (measured live over the timed region)
     steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "fwd_fused", "adj_fused"]
