@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", choices=["skull-512", "skull-256", "skull-192"], default="skull-512")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mu0", action="store_true",
+                    help="acoustic ablation H_{mu=0}: shear modulus set to 0 (lambda + 2 mu kept)")
     ap.add_argument("--serving", action="store_true",
                     help="serve a seeded Poisson stream (continuous batching vs one at a time)")
     ap.add_argument("--requests", type=int, default=200)
@@ -149,6 +151,10 @@ def algorithmic_bytes(kind, d, L, points=None, slab=None):
         return f * (11 * N + 6 * N) + f * 3 * S + 2 * f * 3 * S
     if kind in ("fwd_fused", "adj_fused"):  # read 9 fields, rho, alpha, lambda, 1/mu; write 9 fields
         return f * (9 + 4 + 9) * N
+    if kind in ("fwd_ac_vel", "adj_ac_a"):  # acoustic: read s, u x3, rho, alpha; write u x3
+        return f * 9 * N
+    if kind in ("fwd_ac_str", "adj_ac_b"):  # acoustic: read u x3, s, lambda; write s x3 (the normal stresses)
+        return f * 8 * N
     if kind == "sample":
         return f * (3 * 8 * L + L) + 8 * 8 * L
     if kind == "inject":         # 3 normal Q r+w and lambda, mu at the 8 corners of each receiver
@@ -328,6 +334,9 @@ def run_ours(args):
         return max_over_ranks_of(x, world, device="cuda")
 
     w = make_workload(args.workload)
+    if args.mu0:
+        w.lam = (w.lam + 2.0 * w.mu).astype(np.float32)
+        w.mu = np.zeros_like(w.mu)
     d = w.desc
     K, W = args.steps, args.warmup
     L = w.rec.shape[0]
@@ -363,7 +372,8 @@ def run_ours(args):
     updates = 2.0 * d.N * K * world
 
     # roofline of the dominant kernel (measured live over the timed region)
-    steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "fwd_fused", "adj_fused"]
+    steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "fwd_fused", "adj_fused", "fwd_ac_vel",
+                   "fwd_ac_str", "adj_ac_a", "adj_ac_b"]
     pts = {k: g.role_points(k) for k in steps_kinds}
     dom = max(steps_kinds, key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
@@ -409,7 +419,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (seeded skull-like medium, vessel tubes, Fibonacci receivers)",
-                "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}"),
+                "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}",
+                               **({"medium": "mu = 0 (acoustic ablation, lambda + 2 mu kept)"} if args.mu0 else {})),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "kernels": kernels, "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -88,6 +88,12 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
  * PACT_ECUDA. */
 int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const float* mu,
                     const float* alpha);
+/* (With mu = 0 at every node -- the acoustic operator pair H_{mu=0},
+ * H^T_{mu=0} of the paper's ablation, Sec. 7 -- the three normal stresses stay
+ * equal and the shear stresses zero; on TMA-staged grids the interior tiles
+ * then run acoustic kernels that carry one stress field, and the C-PML frame
+ * the elastic ones.  The results are those of the elastic operator with
+ * mu = 0.  PACT_ACOUSTIC=0 in the environment keeps the elastic kernels.) */
 
 /* p_hat = H p0 (Eq. (H); with the C-PML Eq. (HPML)): load sigma^ii = -p0/3,
  * sample p_hat_0, then nsteps times apply one leapfrog step (velocity and
@@ -209,8 +215,12 @@ int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const flo
 #define PACT_K_READOUT 7      /* read-out tau^T                                   */
 #define PACT_K_FWD_FUSED 8    /* single-pass velocity + stress kernel, forward    */
 #define PACT_K_ADJ_FUSED 9    /* single-pass kernel of one adjoint step           */
-#define PACT_NKIND 10
-#define PACT_K_ALL 10         /* pact_profile_read only: every kernel launch     */
+#define PACT_K_FWD_AC_VEL 10  /* acoustic interior velocity kernel (mu = 0)       */
+#define PACT_K_FWD_AC_STR 11  /* acoustic interior stress kernel (mu = 0)         */
+#define PACT_K_ADJ_AC_A 12    /* acoustic interior kernel, adjoint half A         */
+#define PACT_K_ADJ_AC_B 13    /* acoustic interior kernel, adjoint half B         */
+#define PACT_NKIND 14
+#define PACT_K_ALL 14         /* pact_profile_read only: every kernel launch     */
 
 /* Reset this handle's launch counters and, if enable != 0, start recording a
  * CUDA event after every kernel launch on the handle's stream (so a launch's
@@ -228,7 +238,8 @@ int pact_profile_read(pact_handle h, int kind, long long* launches, double* tota
 
 /* Grid points that one invocation of a step role (PACT_K_FWD_VELOCITY,
  * PACT_K_FWD_STRESS, PACT_K_ADJ_A, PACT_K_ADJ_B, PACT_K_FWD_FUSED,
- * PACT_K_ADJ_FUSED) updates on this handle's grid, and the C-PML slab points
+ * PACT_K_ADJ_FUSED, PACT_K_FWD_AC_VEL, PACT_K_FWD_AC_STR, PACT_K_ADJ_AC_A,
+ * PACT_K_ADJ_AC_B) updates on this handle's grid, and the C-PML slab points
  * among them; 0 for a role that this grid does not run.  Used to turn a
  * role's device time into algorithmic bytes per second.  Errors: PACT_EINVAL. */
 int pact_role_points(pact_handle h, int kind, long long* points, long long* slab_points);

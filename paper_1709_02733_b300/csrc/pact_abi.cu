@@ -53,7 +53,7 @@ struct pact_grid {
     int nmax = 0;
     float* slabs[3] = {nullptr, nullptr, nullptr};  // 6 x slab size per axis
     size_t slab_n[3] = {0, 0, 0};
-    unsigned int* scratch_u32 = nullptr;            // medium-check reduction
+    unsigned int* scratch_u32 = nullptr;            // [0..2] medium check, [3] error word, [4] any mu > 0
     bool medium_set = false;
     double cmax = 0.0;
     // receivers
@@ -87,6 +87,8 @@ struct pact_grid {
     // two-pass kernels read the stresses of buffer c and the velocities of
     // buffer 1-c; the single-pass kernel the stresses of buffer c).
     bool fused = false;
+    // mu = 0 at every node: the interior runs the acoustic kernels
+    bool acoustic = false;
     float* fields2 = nullptr;
     int cur = 0;
     TmaSet tmp[2]{};
@@ -379,14 +381,23 @@ static int device_status(pact_handle h) {
 // One step of H (fwd) or of H^T: the velocity-family and stress-family
 // launches, with the single-pass interior launch between them when the
 // handle runs on two buffers (the step then reads buffer c and writes 1-c).
+static int step_mode(pact_handle h) {
+    return h->fused ? STEP_FUSED : (h->acoustic ? STEP_ACOUSTIC : STEP_TWO_PASS);
+}
+
 static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
     const bool fz = h->fused;
+    const int mode = step_mode(h);
     const TmaSet& tm = fz ? h->tmp[c] : h->tm;
     const SplitStreams ss{h->stream, fz ? nullptr : h->aux, h->ev_fork, h->ev_join};
-    mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, fz));
+    mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, mode));
+    if (h->acoustic)
+        mark(h, adj ? PACT_K_ADJ_AC_A : PACT_K_FWD_AC_VEL, launch_acoustic_step(false, adj, p, tm, err, h->stream));
     if (fz) mark(h, adj ? PACT_K_ADJ_FUSED : PACT_K_FWD_FUSED, launch_fused_step(adj, p, h->fmp[c], err, h->stream));
-    mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, tm, err, ss, fz));
+    mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, tm, err, ss, mode));
+    if (h->acoustic)
+        mark(h, adj ? PACT_K_ADJ_AC_B : PACT_K_FWD_AC_STR, launch_acoustic_step(true, adj, p, tm, err, h->stream));
 }
 
 static void fwd_step(pact_handle h, const StepParams& p, int c) {
@@ -532,7 +543,7 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
     cudaError_t e = cudaMalloc(&h->fields, 9 * h->N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->medium, 5 * h->N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->tables, 18 * (size_t)h->nmax * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->scratch_u32, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->scratch_u32, 8 * sizeof(unsigned int));
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         h->slab_n[a] = slab_points(*desc, a);
         if (h->slab_n[a]) e = cudaMalloc(&h->slabs[a], 6 * h->slab_n[a] * sizeof(float));
@@ -541,7 +552,7 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
         h->err = std::string("allocation: ") + cudaGetErrorString(e);
         return bail(e == cudaErrorMemoryAllocation ? PACT_ENOMEM : PACT_ECUDA);
     }
-    if (cudaMemset(h->scratch_u32, 0, 4 * sizeof(unsigned int)) != cudaSuccess) {
+    if (cudaMemset(h->scratch_u32, 0, 8 * sizeof(unsigned int)) != cudaSuccess) {
         h->err = "cudaMemset of the status words failed";
         return bail(PACT_ECUDA);
     }
@@ -573,9 +584,9 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
             // half: the regions are disjoint by construction, so their point
             // counts must add up to N
             if (h->fused) {
-                const long long nf = role_points(2, true, q);
-                h->fused = role_points(0, true, q) + nf == (long long)h->N &&
-                           role_points(1, true, q) + nf == (long long)h->N;
+                const long long nf = role_points(2, STEP_FUSED, q);
+                h->fused = role_points(0, STEP_FUSED, q) + nf == (long long)h->N &&
+                           role_points(1, STEP_FUSED, q) + nf == (long long)h->N;
             }
         }
         // PACT_OVERLAP=0 runs the frame and interior launches one after the other
@@ -603,11 +614,12 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     CK(h, cudaMemcpyAsync(h->medium + N, lambda, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemcpyAsync(h->medium + 2 * N, mu, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemcpyAsync(h->medium + 3 * N, alpha, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    CK(h, cudaMemsetAsync(h->scratch_u32, 0, 4 * sizeof(unsigned int), s));
+    CK(h, cudaMemsetAsync(h->scratch_u32, 0, 8 * sizeof(unsigned int), s));
     launch_medium_check(h->medium, h->medium + N, h->medium + 2 * N, h->medium + 3 * N, N, h->scratch_u32, s);
+    launch_any_shear(h->medium + 2 * N, N, h->scratch_u32 + 4, s);
     launch_inv_mu(h->medium + 2 * N, h->medium + 4 * N, N, s);
     CK(h, cudaGetLastError());
-    unsigned int red[4];
+    unsigned int red[8];
     CK(h, cudaMemcpyAsync(red, h->scratch_u32, sizeof red, cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
     h->medium_set = false;
@@ -648,6 +660,11 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
             }
     CK(h, cudaMemcpyAsync(h->tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(h, cudaStreamSynchronize(s));
+    // mu = 0 everywhere (the acoustic operator pair of the paper's ablation):
+    // the interior runs the acoustic kernels unless PACT_ACOUSTIC=0
+    const char* aenv = getenv("PACT_ACOUSTIC");
+    h->acoustic = h->tiled && !h->fused && red[4] == 0 && !(aenv && std::strcmp(aenv, "0") == 0) &&
+                  role_points(3, STEP_ACOUSTIC, make_params(h)) > 0;  // needs a layer (see plan_for)
     h->medium_set = true;
     return PACT_OK;
 }
@@ -771,16 +788,20 @@ int pact_role_points(pact_handle h, int kind, long long* points, long long* slab
     const bool vel = kind == PACT_K_FWD_VELOCITY || kind == PACT_K_ADJ_A;
     const bool str = kind == PACT_K_FWD_STRESS || kind == PACT_K_ADJ_B;
     const bool fz = kind == PACT_K_FWD_FUSED || kind == PACT_K_ADJ_FUSED;
-    if (!vel && !str && !fz) return fail(h, PACT_EINVAL, "kind is not a step role");
+    const bool ac = kind == PACT_K_FWD_AC_VEL || kind == PACT_K_FWD_AC_STR || kind == PACT_K_ADJ_AC_A ||
+                    kind == PACT_K_ADJ_AC_B;
+    if (!vel && !str && !fz && !ac) return fail(h, PACT_EINVAL, "kind is not a step role");
     CK(h, cudaSetDevice(h->device));
     const StepParams p = make_params(h);
     long long slabs = 0;
     for (int a = 0; a < 3; ++a) slabs += (long long)h->slab_n[a];
-    if (fz) {
-        *points = h->fused ? role_points(2, true, p) : 0;
-        *slab_points = 0;  // the single-pass region lies off the slabs
+    if (fz || ac) {
+        // the single-pass and acoustic regions lie off the slabs
+        *points = fz ? (h->fused ? role_points(2, STEP_FUSED, p) : 0)
+                     : (h->acoustic ? role_points(3, STEP_ACOUSTIC, p) : 0);
+        *slab_points = 0;
     } else if (h->tiled) {
-        *points = role_points(vel ? 0 : 1, h->fused, p);
+        *points = role_points(vel ? 0 : 1, step_mode(h), p);
         *slab_points = slabs;
     } else {
         *points = (long long)h->N;

@@ -1201,10 +1201,11 @@ void make_regions(const StepParams& p, long slots_inner, long slots_edge, long s
 }
 
 struct LaunchPlan {
-    int dev, nx, ny, nz, P, family;
-    bool fz;
+    int dev, nx, ny, nz, P, family, mode;
     RegionList inner, edge, corner;  // interior, frame edges (PM_X, PM_Y), frame corners (PM_FULL)
     int inner_blocks, edge_blocks, corner_blocks;
+    RegionList ac;                   // STEP_ACOUSTIC: the no-layer interior region (acoustic kernels)
+    int ac_blocks;
 };
 
 // the regions of the kinds in `kinds` (bit mask), renumbered from block 0
@@ -1250,7 +1251,7 @@ long device_slots(const void* fn, size_t smem, int dev) {
     return (long)sms * std::max(1, per_sm);
 }
 
-LaunchPlan plan_for(int family, const StepParams& p, bool fz) {
+LaunchPlan plan_for(int family, const StepParams& p, int mode) {
     static LaunchPlan plans[32];
     static int nplans = 0;
     static std::mutex mu;
@@ -1259,7 +1260,7 @@ LaunchPlan plan_for(int family, const StepParams& p, bool fz) {
     std::lock_guard<std::mutex> lock(mu);
     for (int i = 0; i < nplans; ++i) {
         const LaunchPlan& L = plans[i];
-        if (L.dev == dev && L.family == family && L.fz == fz && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz &&
+        if (L.dev == dev && L.family == family && L.mode == mode && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz &&
             L.P == p.P)
             return L;
     }
@@ -1269,7 +1270,7 @@ LaunchPlan plan_for(int family, const StepParams& p, bool fz) {
     LaunchPlan& L = plans[nplans % 32];
     L.dev = dev;
     L.family = family;
-    L.fz = fz;
+    L.mode = mode;
     L.nx = p.nx;
     L.ny = p.ny;
     L.nz = p.nz;
@@ -1277,10 +1278,33 @@ LaunchPlan plan_for(int family, const StepParams& p, bool fz) {
     RegionList outer;
     int outer_blocks = 0;
     FusedBox fb;
-    const bool use_fb = fz && fused_box(p, fb);
+    const bool use_fb = mode == STEP_FUSED && fused_box(p, fb);
     make_regions(p, si, se, sc, L.inner, L.inner_blocks, outer, outer_blocks, use_fb ? &fb : nullptr);
     L.edge_blocks = select_kinds(outer, (1u << PM_X) | (1u << PM_Y), L.edge);
     L.corner_blocks = select_kinds(outer, 1u << PM_FULL, L.corner);
+    L.ac.n = 0;
+    L.ac_blocks = 0;
+    if (mode == STEP_ACOUSTIC && p.P > 0) {
+        // the no-layer region goes to the acoustic kernels, chunked for their
+        // occupancy; the z-slab planes stay with the elastic interior kernel.
+        // With a layer that region lies strictly inside the grid (its tiles
+        // are whole and their reach, +1 neighbours included, is off the
+        // slabs), which the acoustic kernels assume: they have no own-point
+        // or edge-clamping checks.  Without a layer every tile is interior,
+        // ragged ones included, and the elastic kernels keep them all.
+        RegionList all = L.inner;
+        L.inner_blocks = select_kinds(all, 1u << PM_Z, L.inner);
+        RegionList none;
+        select_kinds(all, 1u << PM_NONE, none);
+        const bool str = family >= 2, adj = family == 1 || family == 3;
+        const long sa = device_slots(acoustic_fn(str, adj), acoustic_smem(), dev);
+        for (int k = 0; k < none.n; ++k) {
+            const Region& r = none.r[k];
+            const long tiles = (long)(r.tx1 - r.tx0) * (r.ty1 - r.ty0);
+            add_region(L.ac, r.tx0, r.tx1, r.ty0, r.ty1, r.za, r.zb, chunk_planes(tiles, r.zb - r.za, sa), PM_NONE,
+                       L.ac_blocks);
+        }
+    }
     nplans = std::min(nplans + 1, 32);
     return L;
 }
@@ -1301,8 +1325,8 @@ long long region_points(const RegionList& rl, const StepParams& p) {
 // The frame launch goes to `aux` (when given) between a fork and a join
 // event, so that it overlaps the interior launch on `st`.
 template <bool ADJ>
-static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
-    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, fz);
+static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
+    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, mode);
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
     const bool split = ss.aux && nframe && L.inner_blocks;
@@ -1326,8 +1350,8 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
 }
 
 template <bool ADJ>
-static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
-    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, fz);
+static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
+    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, mode);
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
     const bool split = ss.aux && nframe && L.inner_blocks;
@@ -1405,12 +1429,19 @@ void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& 
     nouter = rechunk(outer);
 }
 
-int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
-    return adj ? launch_vel_impl<true>(p, tm, err, ss, fz) : launch_vel_impl<false>(p, tm, err, ss, fz);
+int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
+    return adj ? launch_vel_impl<true>(p, tm, err, ss, mode) : launch_vel_impl<false>(p, tm, err, ss, mode);
 }
 
-int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, bool fz) {
-    return adj ? launch_str_impl<true>(p, tm, err, ss, fz) : launch_str_impl<false>(p, tm, err, ss, fz);
+int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
+    return adj ? launch_str_impl<true>(p, tm, err, ss, mode) : launch_str_impl<false>(p, tm, err, ss, mode);
+}
+
+int launch_acoustic_step(bool str, bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {
+    const LaunchPlan L = plan_for((str ? 2 : 0) + (adj ? 1 : 0), p, STEP_ACOUSTIC);
+    if (L.ac_blocks <= 0) return 0;
+    launch_acoustic(str, adj, p, tm, L.ac, L.ac_blocks, err, st);
+    return 1;
 }
 
 // The fused region: one rectangle of tiles over the fused planes, in z
@@ -1469,13 +1500,14 @@ int launch_fused_step(bool adj, const StepParams& p, const FusedMaps& fm, int* e
     return 1;
 }
 
-long long role_points(int family, bool fz, const StepParams& p) {
+long long role_points(int family, int mode, const StepParams& p) {
     if (family == 2) {
         RegionList rl;
         int blocks = 0;
         return fused_plan(p, rl, blocks) ? region_points(rl, p) : 0;
     }
-    const LaunchPlan L = plan_for(family == 0 ? 0 : 2, p, fz);
+    if (family == 3) return mode == STEP_ACOUSTIC ? region_points(plan_for(0, p, STEP_ACOUSTIC).ac, p) : 0;
+    const LaunchPlan L = plan_for(family == 0 ? 0 : 2, p, mode);
     return region_points(L.inner, p) + region_points(L.edge, p) + region_points(L.corner, p);
 }
 

@@ -59,13 +59,31 @@ struct SplitStreams {
     cudaStream_t aux;
     cudaEvent_t fork, join;
 };
-// Both return the number of kernels launched.  With fz set the interior
-// tiles and planes that the single-pass kernel takes (fused_plan) are left
-// out: the step is then launch_vel_tiled, launch_fused_step, launch_str_tiled.
+// Step modes of the TMA-staged kernels:
+//   STEP_TWO_PASS  every tile runs the elastic velocity and stress kernels;
+//   STEP_FUSED     the interior tiles and planes that the single-pass kernel
+//                  takes (fused_plan) are left out: launch_vel_tiled,
+//                  launch_fused_step, launch_str_tiled;
+//   STEP_ACOUSTIC  (mu = 0 everywhere) the no-layer interior region runs the
+//                  acoustic kernels: launch_vel_tiled + launch_acoustic_step
+//                  (velocity), launch_str_tiled + launch_acoustic_step (stress).
+enum { STEP_TWO_PASS = 0, STEP_FUSED = 1, STEP_ACOUSTIC = 2 };
+// Both return the number of kernels launched.
 int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
-                     bool fz = false);
+                     int mode = STEP_TWO_PASS);
 int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
-                     bool fz = false);
+                     int mode = STEP_TWO_PASS);
+
+// Acoustic interior kernels (step_acoustic.cu): the elastic tensor maps (the
+// velocity kernel reads sigma^11, rho, alpha; the stress kernel u^1..u^3).
+size_t acoustic_smem();
+const void* acoustic_fn(bool str, bool adj);
+void launch_acoustic(bool str, bool adj, const StepParams& p, const TmaSet& tm, const RegionList& rl, int blocks,
+                     int* err, cudaStream_t st);
+// the acoustic half step over the interior region; returns 1 if launched
+int launch_acoustic_step(bool str, bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st);
+// out[0] |= 1 if any mu > 0
+void launch_any_shear(const float* mu, size_t n, unsigned int* out, cudaStream_t st);
 
 // Single-pass (velocity + stress) kernel of the interior tiles (step_fused.cu).
 // Its tensor maps: the six stress-like fields of the input buffer (Voigt
@@ -83,9 +101,9 @@ void launch_fused(bool adj, const StepParams& p, const FusedMaps& fm, const Regi
 bool fused_plan(const StepParams& p, RegionList& rl, int& blocks);
 // returns 1 if the fused kernel was launched (0: the grid has no fused region)
 int launch_fused_step(bool adj, const StepParams& p, const FusedMaps& fm, int* err, cudaStream_t st);
-// grid points one launch set of a role updates: family 0 velocity, 1 stress,
-// 2 fused; fz as above
-long long role_points(int family, bool fz, const StepParams& p);
+// grid points one launch set of a role updates: family 0 velocity (elastic
+// kernels), 1 stress (elastic kernels), 2 fused, 3 acoustic interior
+long long role_points(int family, int mode, const StepParams& p);
 // persistent multi-instance half step (str = stress family) over a device
 // table: four launches (two directions x frame / interior), launch k taking
 // its work items from the counter next[k], which must be zero beforehand

@@ -32,7 +32,7 @@ EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint"
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
-         "adj_fused"]
+         "adj_fused", "fwd_ac_vel", "fwd_ac_str", "adj_ac_a", "adj_ac_b"]
 
 
 class PactError(RuntimeError):
