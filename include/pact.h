@@ -203,6 +203,21 @@ int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const flo
                          const float* alpha, const float* p0, const float* rec_xyz, int L, int nsteps,
                          float* traces, void* stream);
 
+/* Proximal step of a total-variation penalty with non-negativity, for
+ * penalised least-squares reconstruction with H and H^T (the use the paper
+ * names in Sec. 8):  x = argmin_{x >= 0} 1/2 ||x - b||^2 + tau TV(x), with
+ * TV(x) = sum_i |grad x_i| (isotropic; forward differences, zero at the last
+ * index of each axis), by iters iterations of Beck and Teboulle's fast
+ * gradient projection on the dual field.  b, x: device arrays of
+ * N = nx*ny*nz floats, [z][y][x] (x fastest), x must not alias b; work: a
+ * device array of 6N floats owned by the caller (the dual field and its
+ * previous iterate; contents on entry are ignored).  tau >= 0 (tau = 0 or
+ * iters = 0 gives max(0, b)).  Queued on stream (cudaStream_t, NULL = legacy
+ * default), asynchronous.  Errors: PACT_EINVAL, PACT_ECUDA; message via
+ * pact_last_error(NULL). */
+int pact_tv_prox_nn(const float* b, float* x, int nx, int ny, int nz, float tau, int iters, float* work,
+                    void* stream);
+
 /* Measurement support (not part of the method).  Kernel roles counted and
  * timed by pact_profile / pact_profile_read. */
 #define PACT_K_FWD_VELOCITY 0 /* velocity + phi update of one forward step        */

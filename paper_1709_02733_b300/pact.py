@@ -28,7 +28,7 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
            "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
-           "pact_advance", "pact_poll"]
+           "pact_advance", "pact_poll", "pact_tv_prox_nn"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
@@ -85,6 +85,7 @@ def load(path: str = SO_PATH):
     lib.pact_profile.argtypes = [vp, i]
     lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
     lib.pact_role_points.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.pact_tv_prox_nn.argtypes = [fp, fp, i, i, i, ctypes.c_float, i, fp, vp]
     for name in EXPORTS:
         if name != "pact_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -103,6 +104,25 @@ def pact_query_bytes(desc: GridDesc, L: int = 0, nsteps: int = -1) -> int:
     _check(load().pact_query_bytes(ctypes.byref(pact_grid_desc.from_desc(desc)), int(L), int(nsteps),
                                    ctypes.byref(out)))
     return int(out.value)
+
+
+def pact_tv_prox_nn(b, tau: float, iters: int, out=None, work=None, stream=None):
+    """x = argmin_{x >= 0} 1/2 ||x - b||^2 + tau TV(x) for a float32 CUDA tensor b
+    of shape (nz, ny, nx) (pact_tv_prox_nn; work: 6N floats, allocated if None)."""
+    import torch
+    if b.dim() != 3:
+        raise ValueError("b must be (nz, ny, nx)")
+    nz, ny, nx = b.shape
+    N = b.numel()
+    out = torch.empty_like(b) if out is None else out
+    work = torch.empty(6 * N, device=b.device, dtype=torch.float32) if work is None else work
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(load().pact_tv_prox_nn(_dev_ptr(b, N), _dev_ptr(out, N), int(nx), int(ny), int(nz), float(tau),
+                                  int(iters), _dev_ptr(work, 6 * N), ctypes.c_void_p(st)))
+    return out
+
+
+tv_prox_nn = pact_tv_prox_nn
 
 
 def pact_advance(grids, ksteps: int, stream=None):

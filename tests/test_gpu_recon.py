@@ -51,3 +51,32 @@ def test_fista_ahead_of_projected_gd(case):
     reconstruct_gd(g, w.rec, w.nsteps, y, iters=12, eta=1.0 / L, callback=lambda k, x, loss: lg.append(loss))
     assert lf[-1] < lg[-1]
     assert min(x for x in lf) < lf[0]
+
+
+def test_tv_prox_kernel_matches_oracle():
+    """pact_tv_prox_nn (CUDA) against the oracle's fast gradient projection
+    (same iteration count) on a ragged 3-D array; tau = 0 is the projection."""
+    from oracle.fista import tv_prox_nn as oracle_tv
+    rng = np.random.default_rng(8)
+    b = (np.cumsum(rng.standard_normal((13, 17, 21)), axis=2) * 0.3 + 0.2).astype(np.float32)
+    got = pact.tv_prox_nn(torch.from_numpy(b).cuda(), 0.3, 60).cpu().numpy()
+    ref = oracle_tv(b.astype(np.float64), 0.3, 60)
+    assert (ref == 0).sum() > 0
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+    assert np.array_equal(pact.tv_prox_nn(torch.from_numpy(b).cuda(), 0.0, 5).cpu().numpy(), np.maximum(b, 0))
+
+
+def test_fista_tv_iterates_match_oracle(case):
+    from oracle.fista import fista_tv_nn as oracle_fista_tv
+
+    from paper_1709_02733_b300.recon import fista_tv
+    w, g, p_true, y, L = case
+    lam = 2e-3 * L
+    got = []
+    fista_tv(g, w.rec, w.nsteps, y, L, lam, iters=4, inner=30, callback=lambda k, x, loss: got.append(x.cpu().numpy()))
+    o = Oracle(w.desc.as_dict(), *w.medium)
+    yn = y.cpu().numpy().astype(np.float64)
+    ref = oracle_fista_tv(lambda p: o.forward(p, w.rec, w.nsteps), lambda r: o.adjoint(r, w.rec), yn,
+                          np.zeros(w.p0.shape), L, lam, 4, 30)
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-4, k

@@ -26,6 +26,10 @@ own formulas:
          x <-> y axis permutation equivariance
   FISTA with the non-negativity projection (oracle/fista.py)
       -> converges to scipy.optimize.nnls's solution on a dense problem
+  total-variation proximal step with non-negativity (oracle/fista.py)
+      -> equals a direct QP solve (scipy SLSQP on the split formulation) in 1-D,
+         and reduces to that 1-D solution when the 3-D input varies along one
+         axis only; the difference pair is an exact adjoint pair
 """
 import math
 
@@ -545,3 +549,55 @@ def test_fista_nn_reaches_nnls():
         x = np.maximum(0.0, x - A.T @ (A @ x - y) / L)
     f = lambda v: 0.5 * np.sum((A @ v - y) ** 2)  # noqa: E731
     assert f(it[99]) - f(ref) <= f(x) - f(ref)
+
+
+def _tv1d_qp(b, tau):
+    """argmin_{x >= 0} 1/2 ||x - b||^2 + tau sum |x_{i+1} - x_i| as the QP in
+    (x, t) with -t <= D x <= t, solved by SLSQP."""
+    from scipy.optimize import minimize
+    n = b.size
+    D = np.zeros((n - 1, n))
+    for i in range(n - 1):
+        D[i, i], D[i, i + 1] = -1.0, 1.0
+    f = lambda v: 0.5 * np.sum((v[:n] - b) ** 2) + tau * np.sum(v[n:])  # noqa: E731
+    g = lambda v: np.concatenate([v[:n] - b, tau * np.ones(n - 1)])  # noqa: E731
+    cons = [{"type": "ineq", "fun": lambda v: v[n:] - D @ v[:n], "jac": lambda v: np.hstack([-D, np.eye(n - 1)])},
+            {"type": "ineq", "fun": lambda v: v[n:] + D @ v[:n], "jac": lambda v: np.hstack([D, np.eye(n - 1)])}]
+    v0 = np.concatenate([np.maximum(b, 0), np.abs(D @ np.maximum(b, 0))])
+    res = minimize(f, v0, jac=g, constraints=cons, bounds=[(0, None)] * n + [(None, None)] * (n - 1),
+                   method="SLSQP", options={"ftol": 1e-13, "maxiter": 5000})
+    return res.x[:n]
+
+
+def test_tv_prox_matches_qp_1d():
+    from oracle.fista import tv_prox_nn
+    rng = np.random.default_rng(3)
+    b = np.cumsum(rng.standard_normal(16)) * 0.6 + rng.standard_normal(16) * 0.4 + 1.3
+    x = tv_prox_nn(b, 0.5, 20000)
+    ref = _tv1d_qp(b, 0.5)
+    assert (x == 0).sum() >= 2 and len(np.unique(np.round(x, 6))) >= 4   # active bound and plateaus
+    assert np.abs(x - ref).max() <= 1e-6
+
+
+def test_tv_prox_3d_reduces_to_1d():
+    """An input that varies along one axis only: every line is the same 1-D
+    problem, so the 3-D solution is the 1-D one broadcast (each axis in turn)."""
+    from oracle.fista import tv_prox_nn
+    rng = np.random.default_rng(5)
+    f = np.cumsum(rng.standard_normal(12)) * 0.5 + 0.2
+    ref = _tv1d_qp(f, 0.4)
+    for axis in range(3):
+        shape = [3, 4, 5]
+        shape[axis] = 12
+        b = np.broadcast_to(f.reshape([12 if a == axis else 1 for a in range(3)]), shape).copy()
+        x = tv_prox_nn(b, 0.4, 20000)
+        want = np.broadcast_to(ref.reshape([12 if a == axis else 1 for a in range(3)]), shape)
+        assert np.abs(x - want).max() <= 1e-6
+
+
+def test_difference_pair_is_adjoint():
+    from oracle.fista import div3, grad3
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((5, 6, 7))
+    p = rng.standard_normal((3, 5, 6, 7))
+    assert abs(np.sum(grad3(x) * p) + np.sum(x * div3(p))) <= 1e-12 * np.sum(np.abs(x)) * np.sum(np.abs(p))
