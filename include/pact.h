@@ -218,6 +218,17 @@ int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const flo
 int pact_tv_prox_nn(const float* b, float* x, int nx, int ny, int nz, float tau, int iters, float* work,
                     void* stream);
 
+/* Linear time resampling of receiver traces, for data simulated with one time
+ * step and reconstructed with another (the non-inverse-crime study of
+ * Sec. 6.2).  in: device, m_in x L floats (time-major, as pact_forward writes
+ * them); out: device, m_out x L floats, overwritten with
+ * out[k][l] = in(s0 + k * ratio)[l], linear between neighbouring input
+ * samples and zero outside [0, m_in - 1] (s0 and ratio in input samples).
+ * Queued on stream (cudaStream_t), asynchronous.  Errors: PACT_EINVAL,
+ * PACT_ECUDA; message via pact_last_error(NULL). */
+int pact_resample_traces(const float* in, int m_in, float* out, int m_out, int L, double s0, double ratio,
+                         void* stream);
+
 /* Measurement support (not part of the method).  Kernel roles counted and
  * timed by pact_profile / pact_profile_read. */
 #define PACT_K_FWD_VELOCITY 0 /* velocity + phi update of one forward step        */

@@ -28,7 +28,7 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
            "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
-           "pact_advance", "pact_poll", "pact_tv_prox_nn"]
+           "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
@@ -86,6 +86,7 @@ def load(path: str = SO_PATH):
     lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
     lib.pact_role_points.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.pact_tv_prox_nn.argtypes = [fp, fp, i, i, i, ctypes.c_float, i, fp, vp]
+    lib.pact_resample_traces.argtypes = [fp, i, fp, i, i, ctypes.c_double, ctypes.c_double, vp]
     for name in EXPORTS:
         if name != "pact_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -123,6 +124,21 @@ def pact_tv_prox_nn(b, tau: float, iters: int, out=None, work=None, stream=None)
 
 
 tv_prox_nn = pact_tv_prox_nn
+
+
+def pact_resample_traces(traces, m_out: int, s0: float, ratio: float, out=None, stream=None):
+    """out[k] = traces(s0 + k * ratio) (linear in time, zero outside) for an
+    (m_in, L) float32 CUDA tensor; returns an (m_out, L) tensor."""
+    import torch
+    m_in, L = traces.shape
+    out = torch.empty((m_out, L), device=traces.device, dtype=torch.float32) if out is None else out
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(load().pact_resample_traces(_dev_ptr(traces, m_in * L), int(m_in), _dev_ptr(out, m_out * L), int(m_out),
+                                       int(L), float(s0), float(ratio), ctypes.c_void_p(st)))
+    return out
+
+
+resample_traces = pact_resample_traces
 
 
 def pact_advance(grids, ksteps: int, stream=None):
