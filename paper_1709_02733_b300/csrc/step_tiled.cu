@@ -73,8 +73,12 @@ template <bool ADJ, int PM> struct VelCfg {
     // stage boxes 0..5: sigma (forward) or Q (adjoint), Voigt order; 6 rho,
     // 7 alpha.  Frame adjoint blocks form the layer-augmented fields F in
     // place and keep the x-differenced F^21, which differs from the
-    // y-differenced F^12 inside the layers, in one extra box.
-    static constexpr int NB = 8;
+    // y-differenced F^12 inside the layers, in one extra box.  The adjoint
+    // edge bodies read alpha through the cache instead (own point one plane
+    // ahead, +x / +y neighbours from L1), which brings their layout under the
+    // shared memory of three blocks per SM.
+    static constexpr bool ABOX = !(ADJ && (PM == PM_X || PM == PM_Y));
+    static constexpr int NB = ABOX ? 8 : 7;
     static constexpr int BRHO = 6, BALPHA = 7;
     static constexpr int NDER = (ADJ && PXY) ? 1 : 0;
     static constexpr int MV = ADJ ? mv_floats(PM) : 0;  // floats of the memory-variable buffer
@@ -398,7 +402,11 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     // own-point values of the next output plane, loaded one visit ahead
     float nu[3] = {0.f, 0.f, 0.f};
     float nph[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float na = 0.f;  // alpha of the own point on plane zn (bodies without the alpha box)
     auto prefetch = [&](int zn) {
+        if constexpr (!Cfg::ABOX) {
+            if (own && zn >= 0 && zn < p.nz) na = __ldg(p.alpha + (unsigned)zn * nxy + gxy);
+        }
         if (!own || zn < zc0 || zn >= zc1) return;
         const unsigned g = (unsigned)zn * nxy + gxy;
         nu[0] = p.u[0][g];
@@ -442,6 +450,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         const int z = pl - 2;
         const bool out = z >= zc0;
         const float cu[3] = {nu[0], nu[1], nu[2]};
+        const float ca = na;  // alpha of the own point on plane z (prefetched a visit ago)
         float cph[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -564,9 +573,18 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                 const float* r0 = sz + Cfg::BRHO * BOXS;
                 const float rb[3] = {0.5f * (r0[o] + r0[o + xc1]), 0.5f * (r0[o] + r0[o + yc1]),
                                      0.5f * (r0[o] + sz1[Cfg::BRHO * BOXS + o])};
-                const float* a0 = sz + Cfg::BALPHA * BOXS;
-                const float ab[3] = {0.5f * (a0[o] + a0[o + xc1]), 0.5f * (a0[o] + a0[o + yc1]),
-                                     0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o])};
+                float ab[3];
+                if constexpr (Cfg::ABOX) {
+                    const float* a0 = sz + Cfg::BALPHA * BOXS;
+                    ab[0] = 0.5f * (a0[o] + a0[o + xc1]);
+                    ab[1] = 0.5f * (a0[o] + a0[o + yc1]);
+                    ab[2] = 0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o]);
+                } else {
+                    const float* ag = p.alpha + (unsigned)z * nxy + gxy;
+                    ab[0] = 0.5f * (ca + __ldg(ag + xc1));
+                    ab[1] = 0.5f * (ca + __ldg(ag + (yc1 ? p.nx : 0)));
+                    ab[2] = 0.5f * (ca + (z + 1 < p.nz ? na : ca));
+                }
                 PmlZ pz{};
                 if constexpr (PML) pml_z_init(pz, p, z);
                 const unsigned gi = (unsigned)z * nxy + gxy;
@@ -929,7 +947,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 // (0: no minimum; the velocity family is limited by its shared memory)
 template <bool STR, bool ADJ, int PM>
 constexpr int min_blocks() {
-    return !STR ? 0 : (PM == PM_NONE ? 4 : (PM == PM_FULL ? 2 : 3));
+    return !STR ? ((ADJ && PM == PM_X) ? 3 : 0) : (PM == PM_NONE ? 4 : (PM == PM_FULL ? 2 : 3));
 }
 // the persistent kernels read their parameters from shared memory, which
 // costs registers: give their velocity-family C-PML bodies an explicit budget
