@@ -248,6 +248,15 @@ __device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy
     }
 }
 
+// Shared tables of the layer coefficients of the cross positions (per box
+// column: 4 floats, then per box row: 4 floats).  One allocation per kernel,
+// shared by all its C-PML bodies (a block runs one body at a time), so that a
+// kernel that carries both edge bodies pays for the tables once.
+__device__ __forceinline__ float* frame_coef_tables() {
+    __shared__ float t[4 * BW + 4 * BH];
+    return t;
+}
+
 __device__ __forceinline__ bool in_slab_plane(int k, int n, int P) {
     return P > 0 && (k < P || k >= n - P - 1);
 }
@@ -391,8 +400,11 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
     const int yc1 = (y + 1 < p.ny) ? BW : 0;  // clamped +y neighbour offset
     CrossPos cross{};
     CrossPml cpm{};
-    __shared__ float cxt[(ADJ && PXY) ? 4 * BW : 1], cyt[(ADJ && PXY) ? 4 * BH : 1];
+    float* cxt = nullptr;
+    float* cyt = nullptr;
     if constexpr (ADJ && PXY) {
+        cxt = frame_coef_tables();
+        cyt = cxt + 4 * BW;
         cross_init(cross, tid, x0, y0, p.nx, p.ny);
         __syncthreads();  // a persistent block may still read the tables of its previous item
         cross_pml_init<LX, LY>(cpm, cxt, cyt, cross, tid, x0, y0, p);
@@ -680,8 +692,11 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
     const int oxy = o + xc1 + yc1;
     CrossPos cross{};
     CrossPml cpm{};
-    __shared__ float cxt[(ADJ && PXY) ? 4 * BW : 1], cyt[(ADJ && PXY) ? 4 * BH : 1];
+    float* cxt = nullptr;
+    float* cyt = nullptr;
     if constexpr (ADJ && PXY) {
+        cxt = frame_coef_tables();
+        cyt = cxt + 4 * BW;
         cross_init(cross, tid, x0, y0, p.nx, p.ny);
         __syncthreads();  // a persistent block may still read the tables of its previous item
         cross_pml_init<LX, LY>(cpm, cxt, cyt, cross, tid, x0, y0, p);
