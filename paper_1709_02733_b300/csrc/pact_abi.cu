@@ -94,8 +94,8 @@ struct pact_grid {
     TmaSet tmp[2]{};
     FusedMaps fmp[2]{};
     // the C-PML frame launches overlap the interior launches on this stream
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t aux = nullptr, aux2 = nullptr;   // frame edges / frame corners
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     // serving state (pact_begin / pact_advance / pact_poll)
     bool sv_active = false;
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
@@ -390,7 +390,7 @@ static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj) {
     const bool fz = h->fused;
     const int mode = step_mode(h);
     const TmaSet& tm = fz ? h->tmp[c] : h->tm;
-    const SplitStreams ss{h->stream, fz ? nullptr : h->aux, h->ev_fork, h->ev_join};
+    const SplitStreams ss{h->stream, fz ? nullptr : h->aux, h->ev_fork, h->ev_join, fz ? nullptr : h->aux2, h->ev_join2};
     mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, mode));
     if (h->acoustic)
         mark(h, adj ? PACT_K_ADJ_AC_A : PACT_K_FWD_AC_VEL, launch_acoustic_step(false, adj, p, tm, err, h->stream));
@@ -593,8 +593,10 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
         const char* oenv = getenv("PACT_OVERLAP");
         if (h->tiled && !(oenv && std::strcmp(oenv, "0") == 0)) {
             if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+                cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
                 h->err = "creating the frame stream and its events failed";
                 return bail(PACT_ECUDA);
             }
@@ -727,7 +729,9 @@ int pact_destroy(pact_handle h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->aux2) cudaStreamDestroy(h->aux2);
     cudaFree(h->stage_a);
     cudaFree(h->stage_b);
     delete h;

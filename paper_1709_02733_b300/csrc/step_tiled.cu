@@ -1363,14 +1363,19 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
     const bool split = ss.aux && nframe && L.inner_blocks;
-    cudaStream_t so = ss.st;
+    cudaStream_t so = ss.st, sc = ss.st;
+    const bool split2 = split && ss.aux2 && L.corner_blocks && L.edge_blocks;
     if (split) {
         cudaEventRecord(ss.fork, ss.st);
         cudaStreamWaitEvent(ss.aux, ss.fork, 0);
-        so = ss.aux;
+        so = sc = ss.aux;
+        if (split2) {
+            cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+            sc = ss.aux2;
+        }
     }
     if (L.corner_blocks)
-        k_vel_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.corner, err);
+        k_vel_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, L.corner, err);
     if (L.edge_blocks)
         k_vel_tiled<ADJ, PM_X><<<L.edge_blocks, blk, VelCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
     if (L.inner_blocks)
@@ -1378,6 +1383,10 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
+        if (split2) {
+            cudaEventRecord(ss.join2, ss.aux2);
+            cudaStreamWaitEvent(ss.st, ss.join2, 0);
+        }
     }
     return nframe + (L.inner_blocks > 0);
 }
@@ -1388,14 +1397,19 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
     const bool split = ss.aux && nframe && L.inner_blocks;
-    cudaStream_t so = ss.st;
+    cudaStream_t so = ss.st, sc = ss.st;
+    const bool split2 = split && ss.aux2 && L.corner_blocks && L.edge_blocks;
     if (split) {
         cudaEventRecord(ss.fork, ss.st);
         cudaStreamWaitEvent(ss.aux, ss.fork, 0);
-        so = ss.aux;
+        so = sc = ss.aux;
+        if (split2) {
+            cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+            sc = ss.aux2;
+        }
     }
     if (L.corner_blocks)
-        k_str_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, so>>>(p, tm, L.corner, err);
+        k_str_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, L.corner, err);
     if (L.edge_blocks)
         k_str_tiled<ADJ, PM_X><<<L.edge_blocks, blk, StrCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
     if (L.inner_blocks)
@@ -1403,6 +1417,10 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
+        if (split2) {
+            cudaEventRecord(ss.join2, ss.aux2);
+            cudaStreamWaitEvent(ss.st, ss.join2, 0);
+        }
     }
     return nframe + (L.inner_blocks > 0);
 }

@@ -58,6 +58,8 @@ struct SplitStreams {
     cudaStream_t st;
     cudaStream_t aux;
     cudaEvent_t fork, join;
+    cudaStream_t aux2;           // optional: the corner launch runs here (join2 recorded after it)
+    cudaEvent_t join2;
 };
 // Step modes of the TMA-staged kernels:
 //   STEP_TWO_PASS  every tile runs the elastic velocity and stress kernels;
