@@ -101,8 +101,8 @@ struct pact_grid {
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
     const float* sv_in = nullptr;
     float* sv_out = nullptr;
-    RegionList sv_inner{}, sv_outer{};
-    int sv_ninner = 0, sv_nouter = 0;
+    RegionList sv_inner{}, sv_edge{}, sv_corner{};
+    int sv_ninner = 0, sv_nedge = 0, sv_ncorner = 0;
     std::string err;
 };
 
@@ -837,7 +837,7 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
         if (nsteps == 0) launch_readout(out, p, h->stream);
     }
-    plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_outer, h->sv_nouter);
+    plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_edge, h->sv_nedge, h->sv_corner, h->sv_ncorner);
     h->sv_active = nsteps > 0;
     CK(h, cudaGetLastError());
     return PACT_OK;
@@ -850,7 +850,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
     if (!T) T = new (std::nothrow) MultiTable();
     if (!T) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
     int dev = -1, ni = 0;
-    T->pre_inner[0] = T->pre_outer[0] = 0;
+    T->pre_inner[0] = T->pre_edge[0] = T->pre_corner[0] = 0;
     // forward instances first, then adjoint ones (each persistent kernel
     // serves one direction)
     for (int pass = 0; pass < 2; ++pass) {
@@ -864,7 +864,8 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             e.tm = h->tm;
             e.p = make_params(h);
             e.inner = h->sv_inner;
-            e.outer = h->sv_outer;
+            e.edge = h->sv_edge;
+            e.corner = h->sv_corner;
             e.rec = make_rec(h);
             e.src = h->sv_adj ? h->sv_in : nullptr;
             e.dst = h->sv_adj ? nullptr : h->sv_out;
@@ -873,7 +874,8 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             e.nsteps = h->sv_nsteps;
             e.L = h->L;
             T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
-            T->pre_outer[ni + 1] = T->pre_outer[ni] + h->sv_nouter;
+            T->pre_edge[ni + 1] = T->pre_edge[ni] + h->sv_nedge;
+            T->pre_corner[ni + 1] = T->pre_corner[ni] + h->sv_ncorner;
             ++ni;
         }
         if (pass == 0) T->n_fwd = ni;

@@ -64,9 +64,11 @@ constexpr bool has_y(int pm) { return pm == PM_FULL || pm == PM_Y; }
 
 // Frame adjoint blocks copy the memory variables at their threads' cross
 // positions (two positions, three values per layer axis) one plane ahead with
-// cp.async into two plane slots of shared memory: [slot][position][value][thread].
+// cp.async into two plane slots of shared memory.
 constexpr int mv_values(int pm) { return (has_x(pm) ? 3 : 0) + (has_y(pm) ? 3 : 0); }
-constexpr int mv_floats(int pm) { return 2 * 2 * mv_values(pm) * (TX * TY); }
+// Layout [slot][value][cross position]: a thread's positions are tid and
+// tid + TX*TY (the second exists for the first 160 threads only).
+constexpr int mv_floats(int pm) { return 2 * mv_values(pm) * ((TX + 4) * TY + 4 * TX); }
 
 template <bool ADJ, int PM> struct VelCfg {
     static constexpr bool PML = PM != PM_NONE, LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
@@ -477,20 +479,20 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         if constexpr (ADJ && PXY) {
             const int zn = z + 1;
             if (zn >= zc0 && zn < zc1) {
-                float* dst = mvb + (size_t)(zn & 1) * 2 * NV * NT + tid;
+                float* dst = mvb + (size_t)(zn & 1) * NV * NCROSS + tid;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (LX && cpm.sx[k] >= 0) {
                         const unsigned si = (unsigned)zn * p.ny * (2 * P + 1) + cpm.sx[k];
-                        cp_async_4(dst + (k * NV + 0) * NT, p.psi[0][0] + si);
-                        cp_async_4(dst + (k * NV + 1) * NT, p.psi[1][0] + si);
-                        cp_async_4(dst + (k * NV + 2) * NT, p.psi[2][0] + si);
+                        cp_async_4(dst + k * NT + 0 * NCROSS, p.psi[0][0] + si);
+                        cp_async_4(dst + k * NT + 1 * NCROSS, p.psi[1][0] + si);
+                        cp_async_4(dst + k * NT + 2 * NCROSS, p.psi[2][0] + si);
                     }
                     if (LY && cpm.sy[k] >= 0) {
                         const unsigned si = (unsigned)zn * (2 * P + 1) * p.nx + cpm.sy[k];
-                        cp_async_4(dst + (k * NV + YV + 0) * NT, p.psi[1][1] + si);
-                        cp_async_4(dst + (k * NV + YV + 1) * NT, p.psi[0][1] + si);
-                        cp_async_4(dst + (k * NV + YV + 2) * NT, p.psi[2][1] + si);
+                        cp_async_4(dst + k * NT + (YV + 0) * NCROSS, p.psi[1][1] + si);
+                        cp_async_4(dst + k * NT + (YV + 1) * NCROSS, p.psi[0][1] + si);
+                        cp_async_4(dst + k * NT + (YV + 2) * NCROSS, p.psi[2][1] + si);
                     }
                 }
             }
@@ -550,18 +552,18 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                         const float q11 = sz[q], q22 = sz[BOXS + q], q23 = sz[3 * BOXS + q];
                         const float q13 = sz[4 * BOXS + q], q12 = sz[5 * BOXS + q];
                         float f11 = q11, f21 = q12, f31 = q13, f22 = q22, f12 = q12, f32 = q23;
-                        const float* mv = mvb + (size_t)(((z & 1) * 2 + k) * NV) * NT + tid;
+                        const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
                             f11 += t[0] * (mv[0] + t[1] * q11);
-                            f21 += t[2] * (mv[NT] + t[3] * q12);
-                            f31 += t[2] * (mv[2 * NT] + t[3] * q13);
+                            f21 += t[2] * (mv[NCROSS] + t[3] * q12);
+                            f31 += t[2] * (mv[2 * NCROSS] + t[3] * q13);
                         }
                         if (LY && cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            f22 += t[0] * (mv[YV * NT] + t[1] * q22);
-                            f12 += t[2] * (mv[(YV + 1) * NT] + t[3] * q12);
-                            f32 += t[2] * (mv[(YV + 2) * NT] + t[3] * q23);
+                            f22 += t[0] * (mv[YV * NCROSS] + t[1] * q22);
+                            f12 += t[2] * (mv[(YV + 1) * NCROSS] + t[3] * q12);
+                            f32 += t[2] * (mv[(YV + 2) * NCROSS] + t[3] * q23);
                         }
                         if (f & CP_XB) {
                             szw[q] = f11;
@@ -765,20 +767,20 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         if constexpr (ADJ && PXY) {
             const int zn = z + 1;
             if (zn >= zc0 && zn < zc1) {
-                float* dst = mvb + (size_t)(zn & 1) * 2 * NV * NT + tid;
+                float* dst = mvb + (size_t)(zn & 1) * NV * NCROSS + tid;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (LX && cpm.sx[k] >= 0) {
                         const unsigned si = (unsigned)zn * p.ny * (2 * P + 1) + cpm.sx[k];
-                        cp_async_4(dst + (k * NV + 0) * NT, p.phi[0][0] + si);
-                        cp_async_4(dst + (k * NV + 1) * NT, p.phi[1][0] + si);
-                        cp_async_4(dst + (k * NV + 2) * NT, p.phi[2][0] + si);
+                        cp_async_4(dst + k * NT + 0 * NCROSS, p.phi[0][0] + si);
+                        cp_async_4(dst + k * NT + 1 * NCROSS, p.phi[1][0] + si);
+                        cp_async_4(dst + k * NT + 2 * NCROSS, p.phi[2][0] + si);
                     }
                     if (LY && cpm.sy[k] >= 0) {
                         const unsigned si = (unsigned)zn * (2 * P + 1) * p.nx + cpm.sy[k];
-                        cp_async_4(dst + (k * NV + YV + 0) * NT, p.phi[1][1] + si);
-                        cp_async_4(dst + (k * NV + YV + 1) * NT, p.phi[0][1] + si);
-                        cp_async_4(dst + (k * NV + YV + 2) * NT, p.phi[2][1] + si);
+                        cp_async_4(dst + k * NT + (YV + 0) * NCROSS, p.phi[1][1] + si);
+                        cp_async_4(dst + k * NT + (YV + 1) * NCROSS, p.phi[0][1] + si);
+                        cp_async_4(dst + k * NT + (YV + 2) * NCROSS, p.phi[2][1] + si);
                     }
                 }
             }
@@ -839,18 +841,18 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                         const int q = cross.q[k];
                         const float wx = sz[q], wy = sz[BOXS + q], wz = sz[2 * BOXS + q];
                         float exx = wx, eyx = wy, ezx = wz, eyy = wy, exy = wx, ezy = wz;
-                        const float* mv = mvb + (size_t)(((z & 1) * 2 + k) * NV) * NT + tid;
+                        const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
                             const float* t = cxt + 4 * (q % BW);
                             exx += t[2] * (mv[0] + t[3] * wx);
-                            eyx += t[0] * (mv[NT] + t[1] * wy);
-                            ezx += t[0] * (mv[2 * NT] + t[1] * wz);
+                            eyx += t[0] * (mv[NCROSS] + t[1] * wy);
+                            ezx += t[0] * (mv[2 * NCROSS] + t[1] * wz);
                         }
                         if (LY && cpm.sy[k] >= 0) {
                             const float* t = cyt + 4 * (q / BW);
-                            eyy += t[2] * (mv[YV * NT] + t[3] * wy);
-                            exy += t[0] * (mv[(YV + 1) * NT] + t[1] * wx);
-                            ezy += t[0] * (mv[(YV + 2) * NT] + t[1] * wz);
+                            eyy += t[2] * (mv[YV * NCROSS] + t[3] * wy);
+                            exy += t[0] * (mv[(YV + 1) * NCROSS] + t[1] * wx);
+                            ezy += t[0] * (mv[(YV + 2) * NCROSS] + t[1] * wz);
                         }
                         if (f & CP_XB) {
                             szw[q] = exx;
@@ -968,13 +970,13 @@ constexpr int min_blocks() {
 // costs registers: give their velocity-family C-PML bodies an explicit budget
 template <bool STR, bool ADJ, int PM>
 constexpr int multi_min_blocks() {
-    return !STR ? (PM == PM_NONE ? 0 : (ADJ ? 2 : 3)) : (PM == PM_NONE ? (ADJ ? 4 : 3) : 2);
+    return PM == PM_X ? 3 : (PM == PM_FULL ? 2 : (!STR ? 0 : (ADJ ? 4 : 3)));
 }
 
-// One work item; a block runs the body of its region's kind.  Single-grid
-// launches: the interior kernel (PM_NONE) runs PM_NONE or PM_Z bodies, the
-// edge kernel (PM_X) PM_X or PM_Y bodies, the corner kernel (PM_FULL) PM_FULL
-// bodies; the persistent frame kernels (DISPATCH) run any frame body.
+// One work item; a block runs the body of its region's kind.  The interior
+// kernels (PM_NONE) run PM_NONE or PM_Z bodies, the edge kernels (PM_X) PM_X
+// or PM_Y bodies, the corner kernels (PM_FULL) PM_FULL bodies; DISPATCH lets
+// one kernel run any frame body.
 template <bool ADJ, int PM, bool DISPATCH>
 __device__ __forceinline__ bool vel_item(const StepParams& p, const CUtensorMap* maps, int kind, int tile_x,
                                          int tile_y, int zc0, int zc1, int* err, float* sm) {
@@ -1046,7 +1048,7 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
     __shared__ int s_item;
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = ADJ ? T->n_fwd : 0, i1 = ADJ ? T->n_inst : T->n_fwd;
-    const int* pre = PM == PM_FULL ? T->pre_outer : T->pre_inner;
+    const int* pre = PM == PM_FULL ? T->pre_corner : (PM == PM_X ? T->pre_edge : T->pre_inner);
     const int first = pre[i0], total = pre[i1];
     for (;;) {
         __syncthreads();  // the previous item is finished with s_item and sp
@@ -1059,7 +1061,8 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
         const InstDev& I = T->inst[i];
         if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
         int tile_x, tile_y, zc0, zc1, kind;
-        locate(PM == PM_FULL ? I.outer : I.inner, item - pre[i], tile_x, tile_y, zc0, zc1, kind);
+        locate(PM == PM_FULL ? I.corner : (PM == PM_X ? I.edge : I.inner), item - pre[i], tile_x, tile_y, zc0, zc1,
+               kind);
         // a work item must lie inside its instance's grid and the instance
         // must be of this kernel's direction; otherwise record the
         // inconsistency and touch nothing
@@ -1073,8 +1076,8 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
         if (tid == 0)
             for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
         __syncthreads();
-        const bool ok = STR ? str_item<ADJ, PM, true>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)
-                            : vel_item<ADJ, PM, true>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
+        const bool ok = STR ? str_item<ADJ, PM, false>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)
+                            : vel_item<ADJ, PM, false>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
         if (!ok) return;
     }
 }
@@ -1452,8 +1455,10 @@ template <bool STR>
 static void launch_multi_family(const MultiTable* dT, int* err, int* next, cudaStream_t st) {
     launch_multi<STR, false, PM_FULL>(dT, err, next + 0, st);
     launch_multi<STR, true, PM_FULL>(dT, err, next + 1, st);
-    launch_multi<STR, false, PM_NONE>(dT, err, next + 2, st);
-    launch_multi<STR, true, PM_NONE>(dT, err, next + 3, st);
+    launch_multi<STR, false, PM_X>(dT, err, next + 2, st);
+    launch_multi<STR, true, PM_X>(dT, err, next + 3, st);
+    launch_multi<STR, false, PM_NONE>(dT, err, next + 4, st);
+    launch_multi<STR, true, PM_NONE>(dT, err, next + 5, st);
 }
 
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st) {
@@ -1463,9 +1468,13 @@ void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next,
 
 // Region plan of one instance for the persistent kernels: z chunks of about
 // `zc` planes so that work items of different instances are of similar size.
-void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
-                           int& nouter) {
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& edge,
+                           int& nedge, RegionList& corner, int& ncorner) {
+    RegionList outer;
+    int nouter = 0;
     make_regions(p, 1, 1, 1, inner, ninner, outer, nouter);
+    select_kinds(outer, (1u << PM_X) | (1u << PM_Y), edge);
+    select_kinds(outer, 1u << PM_FULL, corner);
     auto rechunk = [zc](RegionList& rl) {
         int blocks = 0;
         for (int k = 0; k < rl.n; ++k) {
@@ -1477,7 +1486,8 @@ void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& 
         return blocks;
     };
     ninner = rechunk(inner);
-    nouter = rechunk(outer);
+    nedge = rechunk(edge);
+    ncorner = rechunk(corner);
 }
 
 int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {

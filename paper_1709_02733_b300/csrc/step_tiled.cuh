@@ -30,7 +30,8 @@ struct alignas(128) InstDev {
     TmaSet tm;            // tensor maps of this instance's arrays
     StepParams p;
     RegionList inner;     // work items of the interior tiles (off and on the z slabs)
-    RegionList outer;     // work items of the C-PML frame tiles
+    RegionList edge;      // work items of the frame tiles with one layer (x or y)
+    RegionList corner;    // work items of the frame corner tiles (both layers)
     RecTable rec;
     const float* src;     // adjoint: traces to inject
     float* dst;           // forward: traces to sample into
@@ -45,7 +46,8 @@ struct MultiTable {
     int n_inst;
     int n_fwd;                     // instances [0, n_fwd) are forward, the rest adjoint
     int pre_inner[kMaxInst + 1];   // first work item of each instance
-    int pre_outer[kMaxInst + 1];
+    int pre_edge[kMaxInst + 1];
+    int pre_corner[kMaxInst + 1];
     InstDev inst[kMaxInst];
 };
 
@@ -107,9 +109,9 @@ int launch_fused_step(bool adj, const StepParams& p, const FusedMaps& fm, int* e
 // kernels), 1 stress (elastic kernels), 2 fused, 3 acoustic interior
 long long role_points(int family, int mode, const StepParams& p);
 // persistent multi-instance half step (str = stress family) over a device
-// table: four launches (two directions x frame / interior), launch k taking
-// its work items from the counter next[k], which must be zero beforehand
-constexpr int kMultiLaunches = 4;
+// table: six launches (two directions x corner / edge / interior), launch k
+// taking its work items from the counter next[k], which must be zero beforehand
+constexpr int kMultiLaunches = 6;
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st);
-void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& outer,
-                           int& nouter);
+void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& edge,
+                           int& nedge, RegionList& corner, int& ncorner);
