@@ -229,6 +229,16 @@ int pact_tv_prox_nn(const float* b, float* x, int nx, int ny, int nz, float tau,
 int pact_resample_traces(const float* in, int m_in, float* out, int m_out, int L, double s0, double ratio,
                          void* stream);
 
+/* Self-check of failure detection (not part of the method).  The TMA-staged
+ * kernels bound every wait on an mbarrier (2 s of wall time), record a timed-out
+ * wait in a status word and leave; the host reports it as PACT_ETIMEOUT.  This
+ * call runs the same bounded wait on an mbarrier that nothing ever completes,
+ * with a limit of limit_us microseconds (1 .. 2e6), on stream (cudaStream_t),
+ * and waits for the stream.  Returns PACT_ETIMEOUT when the wait gave up as it
+ * must (the context stays usable), PACT_OK if it did not, PACT_EINVAL for a
+ * limit out of range, PACT_ENOMEM / PACT_ECUDA on a CUDA failure. */
+int pact_check_bounded_wait(unsigned int limit_us, void* stream);
+
 /* Measurement support (not part of the method).  Kernel roles counted and
  * timed by pact_profile / pact_profile_read. */
 #define PACT_K_FWD_VELOCITY 0 /* velocity + phi update of one forward step        */

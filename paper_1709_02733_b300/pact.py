@@ -28,7 +28,7 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
            "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
-           "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces"]
+           "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces", "pact_check_bounded_wait"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
@@ -87,6 +87,7 @@ def load(path: str = SO_PATH):
     lib.pact_role_points.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.pact_tv_prox_nn.argtypes = [fp, fp, i, i, i, ctypes.c_float, i, fp, vp]
     lib.pact_resample_traces.argtypes = [fp, i, fp, i, i, ctypes.c_double, ctypes.c_double, vp]
+    lib.pact_check_bounded_wait.argtypes = [ctypes.c_uint, vp]
     for name in EXPORTS:
         if name != "pact_last_error":
             getattr(lib, name).restype = ctypes.c_int
