@@ -320,3 +320,63 @@ def skull_192():
 
 def skull_512():
     return skull(512, 0.2e-3, 20, 4000, 1024, seed=4, name="skull-512")
+
+
+@dataclass
+class HalfSpaceCase:
+    """y-invariant fluid / solid half-space (the validation set-up of Sec. 5).
+
+    The medium and p0 are given as 2-D (nz, nx) profiles; ``p0_y`` is the
+    range [j0, j1) of y planes that carry p0 (2 cells clear of the y layers);
+    the caller broadcasts them along y (on the device for the full-size grid).
+    Node plane k0 - 1 is the last solid plane and k0 the first fluid one, so
+    the interface lies at z = k0 - 1/2 (index units); heights above it are
+    (k - k0 + 1/2) dx.  The source line is at x index ``x_src``."""
+    desc: GridDesc
+    nsteps: int
+    k0: int
+    x_src: int
+    rho: np.ndarray = field(repr=False)
+    lam: np.ndarray = field(repr=False)
+    mu: np.ndarray = field(repr=False)
+    alpha: np.ndarray = field(repr=False)
+    p0: np.ndarray = field(repr=False)
+    p0_y: tuple = (0, 0)
+    rec: np.ndarray = field(repr=False, default=None)
+    params: dict = field(default_factory=dict)
+
+
+def halfspace(ny=2312, n_xz=388, dx=0.15e-3, npml=30, dt=12.5e-9, t_end=10e-6, h_t=2.1e-3, h_r=2.1e-3, d=2.1e-3,
+              sigma=1e-3, taper=0.75e-3):
+    """Sec. 5: water (rho 1000 kg/m^3, lambda 2.25 GPa) over a lossless solid
+    (rho 1200 kg/m^3, lambda 9.48 GPa, mu 2.352 GPa); box 58.2 x 346.8 x
+    58.2 mm (x, y, z) at dx 0.15 mm with a 4.5 mm C-PML; z normal to the
+    interface, y along the line source; line source at height h_t, receiver
+    at horizontal offset d and height h_r; p0 a Gaussian of std sigma in the
+    x-z plane times the C^2 taper u^3 (10 - 15 u + 6 u^2), u = height / taper
+    clipped to [0, 1] (zero at the interface, so p0 lies in the fluid).
+    dt 12.5 ns (two steps per 40 MHz sample; CFL 0.29 at c_p 3.44 mm/us)."""
+    nz = nx = n_xz
+    rho_f, lam_f = 1000.0, 2.25e9
+    rho_s, lam_s, mu_s = 1200.0, 9.48e9, 2.352e9
+    c_p = math.sqrt((lam_s + 2 * mu_s) / rho_s)
+    desc = GridDesc(nx, ny, nz, dx, dt, npml=npml, pml_vmax=c_p)
+    k0 = nz // 2
+    fluid = (np.arange(nz) >= k0)[:, None] & np.ones((1, nx), bool)
+    rho = np.where(fluid, rho_f, rho_s).astype(np.float32)
+    lam = np.where(fluid, lam_f, lam_s).astype(np.float32)
+    mu = np.where(fluid, 0.0, mu_s).astype(np.float32)
+    alpha = np.zeros((nz, nx), np.float32)
+    off = int(round(d / dx))
+    x_src = nx // 2 - off // 2
+    height = (np.arange(nz, dtype=np.float64) - k0 + 0.5) * dx
+    xo = (np.arange(nx, dtype=np.float64) - x_src) * dx
+    u = np.clip(height / taper, 0.0, 1.0)
+    T = u ** 3 * (10.0 - 15.0 * u + 6.0 * u * u)
+    g = np.exp(-(xo[None, :] ** 2 + (height[:, None] - h_t) ** 2) / (2.0 * sigma ** 2))
+    p0 = (g * T[:, None]).astype(np.float32)
+    rec = np.array([[x_src + d / dx, ny // 2, k0 - 0.5 + h_r / dx]], np.float32)
+    nsteps = int(round(t_end / dt))
+    params = dict(rho_f=rho_f, lam_f=lam_f, rho_s=rho_s, lam_s=lam_s, mu_s=mu_s, h_t=h_t, h_r=h_r, d=d,
+                  sigma=sigma, taper=taper)
+    return HalfSpaceCase(desc, nsteps, k0, x_src, rho, lam, mu, alpha, p0, (npml + 2, ny - npml - 2), rec, params)
