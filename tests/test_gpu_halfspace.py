@@ -12,7 +12,8 @@ window (c_p t_end below the distance to the end of the line), sampled at
 
 runs the comparison at a chosen y extent (2312 = the paper's 346.8 mm) and
 grid refinement (2 = dx / 2 on a correspondingly larger grid) and prints one
-JSON line.
+JSON line; at refine 1 a second line holds the inner-product test of H and
+H^T on the same grid.
 """
 import json
 import math
@@ -91,6 +92,41 @@ def compare(ny=544, refine=1, t_end=10e-6):
             "t_us": (t[::20] * 1e6).tolist(), "exact": exact[::20].tolist(), "fdtd": fd[::20].tolist()}
 
 
+def inner_product(ny=544, L=64, seed=5):
+    """Sec. 5's adjoint check on the validation problem: <H f, g> against
+    <f, H^T g> with f the validation p0 and g = H f + 10 % white noise (so
+    that <H f, g> is not small), L seeded receivers in the water; both sums in
+    FP64 on the host."""
+    import torch
+    from paper_1709_02733_b300 import pact
+    case = synth.halfspace(ny=ny)
+    d = case.desc
+    rng = np.random.default_rng(seed)
+    lo, hi = d.npml + 2, d.nx - d.npml - 3
+    rec = np.stack([rng.uniform(lo, hi, L), rng.uniform(lo, d.ny - d.npml - 3, L),
+                    rng.uniform(case.k0 + 1, hi, L)], axis=1).astype(np.float32)
+    g = pact.Grid(d)
+
+    def ex(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()[:, None, :].expand(d.nz, d.ny, d.nx).contiguous()
+
+    g.set_medium(ex(case.rho), ex(case.lam), ex(case.mu), ex(case.alpha))
+    p0 = torch.zeros(d.shape, device="cuda")
+    j0, j1 = case.p0_y
+    p0[:, j0:j1, :] = torch.from_numpy(case.p0).cuda()[:, None, :]
+    tr = g.forward(p0, rec, case.nsteps).cpu().numpy().astype(np.float64)
+    y = (tr + 0.1 * np.sqrt(np.mean(tr ** 2)) * rng.standard_normal(tr.shape)).astype(np.float32)
+    img = g.adjoint(torch.from_numpy(y).cuda(), rec)
+    # <f, H^T g> over the grid in FP64 on the device, summed per plane on the host
+    rhs = float(sum(torch.sum(p0[k].double() * img[k].double()).item() for k in range(d.nz)))
+    lhs = float(np.sum(tr * y.astype(np.float64)))
+    g.close()
+    del p0, img
+    torch.cuda.empty_cache()
+    return {"grid": [d.nx, d.ny, d.nz], "receivers": L, "nsteps": case.nsteps, "lhs": lhs, "rhs": rhs,
+            "rel_diff": abs(lhs - rhs) / abs(lhs)}
+
+
 _RESULTS = {}
 
 
@@ -123,9 +159,22 @@ def test_halfspace_error_falls_under_refinement():
     assert r2["max_err_over_peak"] < r1["max_err_over_peak"] / 2, (r1["max_err_over_peak"], r2["max_err_over_peak"])
 
 
+@pytest.mark.gpu
+def test_halfspace_inner_product():
+    """The paper reports agreement to 6 digits; FP32 on the validation grid
+    (388 x 544 x 388, 800 steps, 64 receivers) is held to 1e-5, the bound of
+    the other FP32 inner-product tests."""
+    from paper_1709_02733_b300 import build
+    build.build()
+    r = inner_product(ny=544)
+    assert r["rel_diff"] <= 1e-5, r
+
+
 if __name__ == "__main__":
     from paper_1709_02733_b300 import build
     build.build()
     ny = int(sys.argv[1]) if len(sys.argv) > 1 else 2312
     refine = int(sys.argv[2]) if len(sys.argv) > 2 else 1
     print(json.dumps(compare(ny=ny, refine=refine)), flush=True)
+    if refine == 1:
+        print(json.dumps(inner_product(ny=ny)), flush=True)
