@@ -123,6 +123,17 @@ int pact_adjoint(pact_handle h, const float* traces, const float* rec_xyz, int L
 int pact_forward_host(pact_handle h, const float* p0, const float* rec_xyz, int L, int nsteps, float* traces);
 int pact_adjoint_host(pact_handle h, const float* traces, const float* rec_xyz, int L, int nsteps, float* image);
 
+/* Warning, not an error, about the p0 of the last forward solve started on h
+ * (pact_forward, pact_forward_host, or pact_begin with is_adjoint = 0): the
+ * number of nonzero p0 entries at nodes within npml + 2 nodes of a face
+ * (min(x, nx-1-x, y, ny-1-y, z, nz-1-z) < npml + 2).  The C-PML memory
+ * variables start at zero (Appendix A.3), so the support of p0 should stay at
+ * least 2 grid positions away from the layer; a nonzero count says it does not
+ * (the solve ran regardless).  Always 0 when npml = 0.  The count is taken by
+ * the source kernel in the same pass.  n_points: host.  Waits for the
+ * handle's stream.  Errors: PACT_EINVAL (NULL argument), PACT_ECUDA. */
+int pact_support_warning(pact_handle h, long long* n_points);
+
 /* Release everything the handle owns (waits for its stream first). */
 int pact_destroy(pact_handle h);
 

@@ -32,7 +32,7 @@
 // launchers of the step kernels (step_direct.cu) and host helpers (pact_abi.cu)
 void launch_fwd_velocity(const StepParams& p, cudaStream_t st);
 void launch_fwd_stress(const StepParams& p, cudaStream_t st);
-void launch_source(const float* p0, const StepParams& p, cudaStream_t st);
+void launch_source(const float* p0, const StepParams& p, cudaStream_t st, unsigned long long* band_count);
 void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStream_t st);
 void launch_medium_check(const float* rho, const float* lam, const float* mu, const float* alpha, size_t n,
                          unsigned int* out, cudaStream_t st);
@@ -227,7 +227,7 @@ extern "C" int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho
     r.corner = dcorner;
     r.weight = dweight;
 
-    launch_source(p0, p, st);
+    launch_source(p0, p, st, nullptr);
     launch_sample(p, r, traces, st);
     for (int m = 1; m <= nsteps; ++m) {
         launch_fwd_velocity(p, st);

@@ -23,7 +23,7 @@ void launch_fwd_velocity(const StepParams& p, cudaStream_t st);
 void launch_fwd_stress(const StepParams& p, cudaStream_t st);
 void launch_adj_a(const StepParams& p, cudaStream_t st);
 void launch_adj_b(const StepParams& p, cudaStream_t st);
-void launch_source(const float* p0, const StepParams& p, cudaStream_t st);
+void launch_source(const float* p0, const StepParams& p, cudaStream_t st, unsigned long long* band_count);
 void launch_readout(float* img, const StepParams& p, cudaStream_t st);
 void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStream_t st);
 void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st);
@@ -53,7 +53,8 @@ struct pact_grid {
     int nmax = 0;
     float* slabs[3] = {nullptr, nullptr, nullptr};  // 6 x slab size per axis
     size_t slab_n[3] = {0, 0, 0};
-    unsigned int* scratch_u32 = nullptr;            // [0..2] medium check, [3] error word, [4] any mu > 0
+    unsigned int* scratch_u32 = nullptr;            // [0..2] medium check, [3] error word, [4] any mu > 0,
+                                                    // [6..7] p0-near-the-layer count (64 bit)
     bool medium_set = false;
     double cmax = 0.0;
     // receivers
@@ -452,6 +453,11 @@ static int ensure_pingpong(pact_handle h) {
     return PACT_OK;
 }
 
+// 64-bit counter of nonzero p0 entries near the faces, in scratch words 6..7 (8-byte aligned)
+static unsigned long long* band_counter(pact_handle h) {
+    return reinterpret_cast<unsigned long long*>(h->scratch_u32 + 6);
+}
+
 static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps) {
     int rc = ensure_pingpong(h);
     if (rc) return rc;
@@ -461,7 +467,8 @@ static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps
     const RecTable r = make_rec(h);
     StepParams p = make_params(h, 0);
     mark(h, -1);
-    launch_source(p0, p, h->stream);
+    CK(h, cudaMemsetAsync(h->scratch_u32 + 6, 0, sizeof(unsigned long long), h->stream));
+    launch_source(p0, p, h->stream, band_counter(h));
     mark(h, PACT_K_SOURCE);
     launch_sample(p, r, traces, h->stream);
     mark(h, PACT_K_SAMPLE);
@@ -831,7 +838,8 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
     h->sv_in = in;
     h->sv_out = out;
     if (!is_adjoint) {
-        launch_source(in, p, h->stream);
+        CK(h, cudaMemsetAsync(h->scratch_u32 + 6, 0, sizeof(unsigned long long), h->stream));
+        launch_source(in, p, h->stream, band_counter(h));
         launch_sample(p, r, out, h->stream);
     } else {
         launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
@@ -900,6 +908,15 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
         }
     }
     if (cudaGetLastError() != cudaSuccess) return fail(nullptr, PACT_ECUDA, "pact_advance: launch failed");
+    return PACT_OK;
+}
+
+int pact_support_warning(pact_handle h, long long* n_points) {
+    if (!h || !n_points) return fail(h, PACT_EINVAL, "pact_support_warning: NULL argument");
+    unsigned long long c = 0;
+    CK(h, cudaMemcpyAsync(&c, band_counter(h), sizeof c, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *n_points = (long long)c;
     return PACT_OK;
 }
 

@@ -300,12 +300,37 @@ __global__ void k_adj_b(StepParams p) {
 // ===========================================================================
 
 // tau (Eq. (initialp0)): sigma^ii = -p0 / 3 (other fields already zero)
-__global__ void k_source(const float* __restrict__ p0, float* s0, float* s1, float* s2, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float v = -__ldg(p0 + i) * (1.0f / 3.0f);
-        s0[i] = v;
-        s1[i] = v;
-        s2[i] = v;
+// With band_count set, the same pass counts the nonzero p0 entries at nodes
+// within `band` nodes of a face: the C-PML memory variables start at zero
+// (Appendix A.3), so the support of p0 should stay 2 nodes clear of the layer.
+// The loop advances whole warps (blockDim is a multiple of 32) so that every
+// lane takes part in the ballot; one atomic per warp with a hit.
+__global__ void k_source(const float* __restrict__ p0, float* s0, float* s1, float* s2, size_t n, int nx, int ny,
+                         int nz, int band, unsigned long long* band_count) {
+    const unsigned lane = threadIdx.x & 31u;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = blockIdx.x * (size_t)blockDim.x + (threadIdx.x - lane); base < n; base += stride) {
+        const size_t i = base + lane;
+        bool hit = false;
+        if (i < n) {
+            const float q = __ldg(p0 + i);
+            const float v = -q * (1.0f / 3.0f);
+            s0[i] = v;
+            s1[i] = v;
+            s2[i] = v;
+            if (band_count && q != 0.0f) {
+                const int x = (int)(i % (size_t)nx);
+                const size_t r = i / (size_t)nx;
+                const int y = (int)(r % (size_t)ny);
+                const int z = (int)(r / (size_t)ny);
+                const int dmin = min(min(min(x, nx - 1 - x), min(y, ny - 1 - y)), min(z, nz - 1 - z));
+                hit = dmin < band;
+            }
+        }
+        if (band_count) {
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m && lane == 0) atomicAdd(band_count, (unsigned long long)__popc(m));
+        }
     }
 }
 
@@ -420,9 +445,12 @@ static int ew_blocks(size_t n) {
     return (int)(b < 148 * 16 ? b : 148 * 16);
 }
 
-void launch_source(const float* p0, const StepParams& p, cudaStream_t st) {
+// band_count: nullptr, or a zeroed device counter for the p0-near-the-layer warning
+// (only counted when the grid has a C-PML: band = P + 2).
+void launch_source(const float* p0, const StepParams& p, cudaStream_t st, unsigned long long* band_count) {
     const size_t n = (size_t)p.nx * p.ny * p.nz;
-    k_source<<<ew_blocks(n), 256, 0, st>>>(p0, p.s[0], p.s[1], p.s[2], n);
+    unsigned long long* c = p.P > 0 ? band_count : nullptr;
+    k_source<<<ew_blocks(n), 256, 0, st>>>(p0, p.s[0], p.s[1], p.s[2], n, p.nx, p.ny, p.nz, p.P + 2, c);
 }
 
 void launch_readout(float* img, const StepParams& p, cudaStream_t st) {

@@ -28,7 +28,8 @@ _NAMES = {1: "EINVAL", 2: "ECFL", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ES
 EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint", "pact_forward_host",
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
            "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
-           "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces", "pact_check_bounded_wait"]
+           "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces", "pact_check_bounded_wait",
+           "pact_support_warning"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
@@ -81,6 +82,7 @@ def load(path: str = SO_PATH):
     lib.pact_begin.argtypes = [vp, i, fp, fp, i, i, fp]
     lib.pact_advance.argtypes = [ctypes.POINTER(vp), i, i, vp]
     lib.pact_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.pact_support_warning.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.pact_forward_noalloc.argtypes = [D, fp, fp, fp, fp, fp, fp, i, i, fp, vp]
     lib.pact_profile.argtypes = [vp, i]
     lib.pact_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
@@ -288,6 +290,15 @@ class Grid:
                                    r.ctypes.data_as(ctypes.c_void_p), L, int(nsteps), _dev_ptr(out, n_out)), self._h)
 
     begin = pact_begin
+
+    def pact_support_warning(self) -> int:
+        """Nonzero p0 entries within npml + 2 nodes of a face in the last forward
+        solve (0 = the paper's support rule holds); waits for the stream."""
+        n = ctypes.c_longlong(0)
+        _check(self.lib.pact_support_warning(self._h, ctypes.byref(n)), self._h)
+        return int(n.value)
+
+    support_warning = pact_support_warning
 
     def pact_poll(self) -> int:
         n = ctypes.c_int(0)

@@ -348,3 +348,45 @@ def test_fused_inner_product_and_oracle(monkeypatch):
     assert rel_l2(tr, o.forward(p0, rec, 37)) <= TOL
     y = np.random.default_rng(10).standard_normal(tr.shape).astype(np.float32)
     assert rel_l2(g.adjoint(cuda(y), rec).cpu().numpy(), o.adjoint(y, rec)) <= TOL
+
+
+def _band_count(p0, band):
+    nz, ny, nx = p0.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    dmin = np.minimum.reduce([x, nx - 1 - x, y, ny - 1 - y, z, nz - 1 - z])
+    return int(np.count_nonzero((p0 != 0) & (dmin < band)))
+
+
+@pytest.mark.parametrize("shape,npml", [((40, 44, 52), 4), ((21, 19, 35), 3)])
+def test_p0_support_warning_counts(shape, npml):
+    """The source pass counts the nonzero p0 entries within npml + 2 nodes of a
+    face (the paper's support rule, a warning only): exact against numpy for a
+    dense p0, 0 for a p0 kept clear of the band, and reset by every solve."""
+    d, med, p0, rec = _random_case(shape, npml, 13, L=4)
+    g = make_grid(d, med)
+    band = npml + 2
+    g.forward(cuda(p0), rec, 3)
+    assert g.support_warning() == _band_count(p0, band) > 0
+    inner = np.zeros_like(p0)
+    inner[band:-band, band:-band, band:-band] = p0[band:-band, band:-band, band:-band]
+    g.forward(cuda(inner), rec, 3)
+    assert g.support_warning() == 0
+    # single points at distance band - 1 (counted) and band (not counted) from each face
+    pts = np.zeros_like(p0)
+    nz, ny, nx = shape
+    cz, cy, cx = nz // 2, ny // 2, nx // 2
+    for dist, val in ((band - 1, 1.0), (band, 2.0)):
+        pts[cz, cy, dist] = pts[cz, cy, nx - 1 - dist] = val
+        pts[cz, dist, cx] = pts[cz, ny - 1 - dist, cx] = val
+        pts[dist, cy, cx] = pts[nz - 1 - dist, cy, cx] = val
+    g.forward(cuda(pts), rec, 0)
+    assert g.support_warning() == 6 == _band_count(pts, band)
+    g.close()
+
+
+def test_p0_support_warning_without_layer():
+    d, med, p0, rec = _random_case((20, 18, 36), 0, 14, L=4)
+    g = make_grid(d, med)
+    g.forward(cuda(p0), rec, 2)
+    assert g.support_warning() == 0
+    g.close()
