@@ -72,3 +72,26 @@ def test_rigid_solid_is_an_image_source():
     ref = np.array([hs.gaussian_free_space(2.1e-3, t, 1e-3, 1500.0) + hs.gaussian_free_space(r_img, t, 1e-3, 1500.0)
                     for t in times])
     assert np.max(np.abs(p - ref)) < 1e-6, (p, ref)
+
+
+def test_synth_halfspace_rasterises_the_same_source():
+    """The input generator's p0 and geometry agree with the oracle's continuous
+    definition (two independent writings of the same set-up)."""
+    from paper_1709_02733_b300 import synth
+    c = synth.halfspace(ny=96)
+    d, p = c.desc, c.params
+    src = hs.LineSource(0.0, p["h_t"], p["sigma"], p["taper"])
+    x = (np.arange(d.nx) - c.x_src) * d.dx
+    z = (np.arange(d.nz) - c.k0 + 0.5) * d.dx                 # height above the interface
+    ref, _, _ = src.value_and_grad(x[None, :], z[:, None])
+    np.testing.assert_allclose(c.p0, ref, rtol=2e-7, atol=1e-30)
+    assert not c.p0[:c.k0].any()                               # nothing in the solid
+    m = hs.HalfSpace.from_lame(p["rho_f"], p["lam_f"], p["rho_s"], p["lam_s"], p["mu_s"])
+    assert m == hs.PAPER_MEDIUM
+    assert np.all(c.mu[c.k0:] == 0) and np.all(c.mu[:c.k0] == np.float32(p["mu_s"]))
+    # receiver at (d, h_R) from the source line, on the centre y plane
+    assert c.rec[0, 0] * d.dx == pytest.approx(c.x_src * d.dx + p["d"], rel=1e-6)
+    assert (c.rec[0, 2] - (c.k0 - 0.5)) * d.dx == pytest.approx(p["h_r"], rel=1e-6)
+    j0, j1 = c.p0_y
+    assert j0 == d.npml + 2 and d.ny - j1 == d.npml + 2         # p0 planes 2 nodes clear of the y layers
+    assert m.c_p * d.dt / d.dx < 6 / (7 * math.sqrt(3))
