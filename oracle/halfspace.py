@@ -62,7 +62,10 @@ in the fluid-fluid limit; the Cagniard-path Green's function against the
 Laplace-domain plane-wave integral of step 2 evaluated on the real q axis
 (sub- and supercritical, so that the head-wave loop is checked); the direct
 term against the Hankel-transform solution of a Gaussian in free space; a
-rigid solid (R = 1) against the same Hankel solution at the image distance.
+rigid solid (R = 1) against the same Hankel solution at the image distance;
+the Laplace transform of the whole reflected trace (hyperbolic and head-wave
+terms, source integral and time derivative) against the plane-wave integral
+over real q with the Gaussian's x-integral done exactly.
 """
 from __future__ import annotations
 
@@ -201,13 +204,14 @@ def _radial_D(src: LineSource, cx, cz, rho, cosphi, sinphi):
 
 
 def pressure_trace(times, x_r, h_r, src: LineSource, m: HalfSpace, n_phi_direct=256, n_phi_image=2048,
-                   n_beta=256, n_w=48, reflected=True):
+                   n_beta=256, n_w=48, reflected=True, direct=True, head=True):
     """Exact pressure p(x_r, h_r, t) of the 2-D initial-value problem at the given
     times [s] (step 5).  The direct-term phi integral is periodic (trapezoid
     rule); the image-term phi integral runs over (0, pi) with an integrand that
     vanishes at both ends (trapezoid rule); beta and w use Gauss-Legendre, with
     w = w_h (1 - zeta^2) so that the square-root behaviour of R at the branch
-    point i/c_p is integrated exactly."""
+    point i/c_p is integrated exactly.  direct / reflected / head select the
+    terms (all by default)."""
     times = np.asarray(times, dtype=np.float64)
     c = m.c_f
     xb, wb = np.polynomial.legendre.leggauss(n_beta)
@@ -232,15 +236,55 @@ def pressure_trace(times, x_r, h_r, src: LineSource, m: HalfSpace, n_phi_direct=
     out = np.empty(times.shape)
     for i, t in enumerate(times.ravel()):
         rho_b = c * t * np.cos(beta)[None, :]
-        Dd = _radial_D(src, x_r, h_r, rho_b, cpd, spd)
-        val = (Dd * wbeta[None, :]).sum() * (2.0 * math.pi / n_phi_direct)
+        val = 0.0
+        if direct:
+            Dd = _radial_D(src, x_r, h_r, rho_b, cpd, spd)
+            val += (Dd * wbeta[None, :]).sum() * (2.0 * math.pi / n_phi_direct)
         if reflected:
             Di = _radial_D(src, x_r, -h_r, rho_b, cpi, spi)
             val += (ReR * Di * wbeta[None, :]).sum() * (math.pi / n_phi_image)
-            Dh = _radial_D(src, x_r, -h_r, c * t / np.cos(w), cpi, spi)
-            val += (head_weight * Dh).sum() * (math.pi / n_phi_image)
+            if head:
+                Dh = _radial_D(src, x_r, -h_r, c * t / np.cos(w), cpi, spi)
+                val += (head_weight * Dh).sum() * (math.pi / n_phi_image)
         out.ravel()[i] = val / (2.0 * math.pi)
     return out
+
+
+def reflected_pressure_laplace(s, x_r, h_r, src: LineSource, m: HalfSpace, n_q=1500, n_z=400):
+    """Laplace transform of the reflected pressure at (x_r, h_r) computed
+    without any contour deformation (step 1 with G^_reflected of step 2):
+        P_r(s) = (s/c_f^2) (1/2pi) int R(q)/(2 gamma_f) e^{-s gamma_f h_r}
+                 e^{i s q (x_r - x_s)} Fx(q) Fz(q) dq,
+    Fx(q) = int e^{-i s q x'} exp(-x'^2/(2 sigma^2)) dx' = sqrt(2pi) sigma exp(-(s q sigma)^2/2)
+    (the Gaussian's x-profile, exactly), Fz(q) = int_0^inf T(z'/a)
+    exp(-(z'-h_t)^2/(2 sigma^2)) e^{-s gamma_f z'} dz' (Gauss-Legendre).  On
+    real q the integrand is real and even, so the integral is twice the one
+    over q > 0."""
+    c = m.c_f
+    qmax = 9.0 / (s * src.sigma)
+    xq, wq = np.polynomial.legendre.leggauss(n_q)
+    q = 0.5 * qmax * (xq + 1.0)
+    wq = 0.5 * qmax * wq
+    gf = np.sqrt(1.0 / c ** 2 + q * q)
+    R = np.real(reflection_coefficient(q, m))
+    zmax = src.h_t + 9.0 * src.sigma
+    xz, wz = np.polynomial.legendre.leggauss(n_z)
+    z = 0.5 * zmax * (xz + 1.0)
+    wz = 0.5 * zmax * wz
+    prof, _, _ = src.value_and_grad(np.full_like(z, src.x_s), z)          # T(z/a) exp(-(z-h_t)^2 / 2 sigma^2)
+    Fz = (np.exp(-s * gf[:, None] * z[None, :]) * prof[None, :] * wz[None, :]).sum(axis=1)
+    Fx = math.sqrt(2.0 * math.pi) * src.sigma * np.exp(-0.5 * (s * q * src.sigma) ** 2)
+    integrand = R / (2.0 * gf) * np.exp(-s * gf * h_r) * np.cos(s * q * (x_r - src.x_s)) * Fx * Fz
+    return (s / c ** 2) * (2.0 * (integrand * wq).sum()) / (2.0 * math.pi)
+
+
+def laplace_of_trace(f, s, t_end, panels=40, nodes=16):
+    """int_0^t_end e^{-s t} f(t) dt by panel Gauss-Legendre (f vectorised)."""
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    edges = np.linspace(0.0, t_end, panels + 1)
+    t = (0.5 * (edges[1:, None] - edges[:-1, None]) * (x[None, :] + 1.0) + edges[:-1, None]).ravel()
+    wt = (0.5 * (edges[1:, None] - edges[:-1, None]) * w[None, :]).ravel()
+    return float((np.exp(-s * t) * f(t) * wt).sum())
 
 
 def gaussian_free_space(r, t, sigma, c):

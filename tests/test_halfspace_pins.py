@@ -95,3 +95,19 @@ def test_synth_halfspace_rasterises_the_same_source():
     j0, j1 = c.p0_y
     assert j0 == d.npml + 2 and d.ny - j1 == d.npml + 2         # p0 planes 2 nodes clear of the y layers
     assert m.c_p * d.dt / d.dx < 6 / (7 * math.sqrt(3))
+
+
+def test_reflected_trace_laplace_transform():
+    """The Laplace transform of the oracle's reflected trace (Cagniard path,
+    head-wave loop, source integral in image-polar coordinates, time derivative
+    moved onto p0) equals the plane-wave integral over real q, where the
+    Gaussian's x-integral is exact and nothing is deformed.  At s = 1.2 /us the
+    head-wave term carries 9 % of the transform; the bound is 2e-4 (the
+    reduced quadrature used here agrees to 2e-5)."""
+    src = hs.LineSource(0.0, 2.1e-3, 1e-3, 0.75e-3)
+    kw = dict(n_phi_direct=64, n_phi_image=512, n_beta=128, n_w=32)
+    s = 1.2e6
+    a = hs.laplace_of_trace(lambda t: hs.pressure_trace(t, 2.1e-3, 2.1e-3, src, M, direct=False, **kw), s,
+                            40.0 / s, panels=34, nodes=12)
+    b = hs.reflected_pressure_laplace(s, 2.1e-3, 2.1e-3, src, M)
+    assert abs(a - b) <= 2e-4 * abs(b), (a, b)
