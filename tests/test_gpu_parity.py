@@ -195,13 +195,39 @@ def _crop_check(w, g, nsteps, centers):
     return max(errs)
 
 
+def _layer_crop_check(w, p0, fields, nsteps, m, high, points):
+    """Oracle on the m^3 corner crop at the grid's low (or high) corner, with
+    the grid's C-PML: a layer's profile depends only on the depth into it, so
+    the crop's layers on the grid's own faces are the grid's.  A point after k
+    steps depends on the data within 4k cells; the points must keep that reach
+    clear of the crop's other three faces and their (artificial) layers."""
+    d = w.desc
+    P, reach = d.npml, 4 * nsteps
+    lo = [d.nz - m, d.ny - m, d.nx - m] if high else [0, 0, 0]
+    for (x, y, z) in points:
+        for c, l in zip((z, y, x), lo):
+            assert (c - reach >= l + P + 1) if high else (c + reach + 2 <= m - P - 1), (x, y, z)
+    sl = tuple(slice(l, l + m) for l in lo)
+    dd = dict(nx=m, ny=m, nz=m, dx=d.dx, dt=d.dt, npml=P, pml_R0=d.pml_R0, pml_f0=d.pml_f0, pml_vmax=d.pml_vmax)
+    o = Oracle(dd, *[np.ascontiguousarray(a[sl]) for a in w.medium])
+    v = Oracle.views(o.run_state(np.ascontiguousarray(p0[sl]), nsteps))
+    errs = []
+    for (x, y, z) in points:
+        cz, cy, cx = z - lo[0], y - lo[1], x - lo[2]
+        ref = np.concatenate([v["u"][:, cz, cy, cx], v["sigma"][:, cz, cy, cx]])
+        got = fields[:, z, y, x].astype(np.float64)
+        errs.append(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30))
+    return max(errs)
+
+
 def test_full_size_512_sampled():
     """The 512^3 skull workload in the launch configuration the bench times:
     (a) p_hat_0 equals the trilinear interpolation of p0 at every receiver;
     (b) the wavefield after 2 steps matches the oracle at sampled interior
         points (oracle on a crop);
     (c) inner-product test over 12 steps at full size, with a seeded random p0
-        over the whole grid so that the receivers see it from the first sample."""
+        over the whole grid so that the receivers see it from the first sample;
+    (d) the C-PML frame kernels at full size against oracle corner crops."""
     from scipy.ndimage import map_coordinates
     w = synth.skull_512()
     g = make_grid(w.desc, w.medium)
@@ -219,6 +245,19 @@ def test_full_size_512_sampled():
         centers.append((int(c[2]), int(c[1]), int(c[0])))
     assert _crop_check(w, g, 2, centers) <= 1e-4
     pr = np.random.default_rng(11).standard_normal(w.p0.shape).astype(np.float32)
+    # (d) the C-PML frame at full size (corner, edge and z-slab tiles, both
+    #     ends of every axis) after 2 steps of a p0 that fills the grid, against
+    #     the oracle on 64^3 corner crops that carry the grid's own layers
+    g.forward(cuda(pr), w.rec, 2)
+    fields = g.get_wavefield()
+    n = w.desc.nx
+    # corner tiles, x-edge tiles (layer and non-layer points), interior tiles on a z slab and next to the y layer
+    low = [(10, 10, 10), (3, 30, 30), (30, 12, 30), (30, 30, 19), (21, 30, 30), (19, 19, 30), (40, 40, 10),
+           (36, 25, 41)]
+    high = [(n - 1 - x, n - 1 - y, n - 1 - z) for (x, y, z) in low]
+    assert _layer_crop_check(w, pr, fields, 2, 72, False, low) <= 1e-4
+    assert _layer_crop_check(w, pr, fields, 2, 72, True, high) <= 1e-4
+    del fields
     assert _dot_test(g, pr, w.rec, 12) <= DOT_TOL
 
 
