@@ -429,3 +429,32 @@ def test_p0_support_warning_without_layer():
     g.forward(cuda(p0), rec, 2)
     assert g.support_warning() == 0
     g.close()
+
+
+def test_degenerate_inputs_and_rejected_calls():
+    """Zero p0 gives exactly zero traces and zero traces exactly zero image; the
+    raw ABI rejects L = 0, nsteps < 0 and NULL data pointers with PACT_EINVAL
+    and the handle then solves exactly as a fresh one."""
+    import ctypes
+    d, med, p0, rec = _random_case((18, 17, 20), 2, 21, L=5)
+    g = make_grid(d, med)
+    assert g.support_warning() == 0                      # no forward solve yet
+    zero = torch.zeros(d.shape, device="cuda")
+    tr = g.forward(zero, rec, 7)
+    assert torch.count_nonzero(tr).item() == 0
+    assert torch.count_nonzero(g.adjoint(torch.zeros_like(tr), rec)).item() == 0
+    vp = ctypes.c_void_p
+    r = np.ascontiguousarray(rec, np.float32)
+    out = torch.empty((8, 5), device="cuda")
+    img = torch.empty(d.shape, device="cuda")
+    lib = g.lib
+    assert lib.pact_forward(g._h, vp(zero.data_ptr()), r.ctypes.data_as(vp), 0, 7, vp(out.data_ptr())) == pact.PACT_EINVAL
+    assert lib.pact_forward(g._h, vp(zero.data_ptr()), r.ctypes.data_as(vp), 5, -1, vp(out.data_ptr())) == pact.PACT_EINVAL
+    assert lib.pact_forward(g._h, None, r.ctypes.data_as(vp), 5, 7, vp(out.data_ptr())) == pact.PACT_EINVAL
+    assert lib.pact_forward(g._h, vp(zero.data_ptr()), None, 5, 7, vp(out.data_ptr())) == pact.PACT_EINVAL
+    assert lib.pact_adjoint(g._h, vp(out.data_ptr()), r.ctypes.data_as(vp), 5, 7, None) == pact.PACT_EINVAL
+    assert lib.pact_adjoint(g._h, None, r.ctypes.data_as(vp), 5, 7, vp(img.data_ptr())) == pact.PACT_EINVAL
+    assert lib.pact_last_error(g._h)
+    a = g.forward(cuda(p0), rec, 7).cpu().numpy()
+    b = make_grid(d, med).forward(cuda(p0), rec, 7).cpu().numpy()
+    assert np.array_equal(a, b)
