@@ -167,16 +167,16 @@ def source_sha():
     return sha()
 
 
-def traffic_for(kind):
+def traffic_for(kind, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current kernel sources and on this workload (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(path))
     except Exception:
         return None
     e = t.get(kind)
-    if not e or e.get("source_sha") != source_sha():
+    if not e or e.get("source_sha") != source_sha() or e.get("workload") != workload:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -383,7 +383,8 @@ def run_ours(args):
     achieved = alg / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "peak_source": which + " (hbm_gbs, STREAM-style copy)",
-                "traffic": traffic_for(dom), "algorithmic_bytes_per_launch": alg,
+                "traffic": traffic_for(dom, args.workload + (" mu=0" if args.mu0 else "")),
+                "algorithmic_bytes_per_launch": alg,
                 "avg_launch_ms": avg_s * 1e3, "bytes_per_update": alg / max(1, pts[dom][0]),
                 "grid_points_per_launch": pts[dom][0]}
     # the whole step: algorithmic bytes of every role over the step's device time

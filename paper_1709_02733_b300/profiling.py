@@ -6,10 +6,12 @@
         key counters of a full-set capture (``ncu -i rep --page raw --csv``):
         duration, DRAM bytes and throughput, occupancy, issue activity and the
         top warp-stall reasons of every captured launch (markdown)
-    python -m paper_1709_02733_b300.profiling traffic <ncu.csv> <out.json> [--scale F]
+    python -m paper_1709_02733_b300.profiling traffic <ncu.csv> <out.json> [--scale F] [--workload W]
         DRAM bytes (read + write) per half step of each kernel role, as read by
         bench.py for the roofline "traffic" field; F scales a capture of a
-        smaller grid to the full one (ratio of grid points)
+        smaller grid to the full one (ratio of grid points); W names the bench
+        workload the capture ran (default skull-512; " mu=0" appended for the
+        acoustic ablation), and bench.py only reports the figure for that one
 
 The CSV is ``ncu --csv --log-file`` output with one row per (launch, metric).
 A kernel role of bench.py (fwd_velocity, fwd_stress, adj_a, adj_b) is one
@@ -73,7 +75,7 @@ def launch_table(path) -> str:
     return "\n".join(out)
 
 
-def traffic(path, scale: float = 1.0) -> dict:
+def traffic(path, scale: float = 1.0, workload: str = "skull-512") -> dict:
     """DRAM bytes per half step of each role: every kernel of a role runs once
     per half step, so the role's figure is the sum over its kernels of their
     mean bytes per launch."""
@@ -87,7 +89,8 @@ def traffic(path, scale: float = 1.0) -> dict:
     for name, (n, b) in per_kernel.items():
         acc[role_of(name)] += b / n * scale
     sha = source_sha()
-    return {role: {"dram_bytes_per_launch": b, "source_sha": sha, "scale": scale} for role, b in acc.items()}
+    return {role: {"dram_bytes_per_launch": b, "source_sha": sha, "scale": scale, "workload": workload}
+            for role, b in acc.items()}
 
 
 FULLSET_KEYS = [
@@ -153,8 +156,9 @@ def main(argv):
         print(fullset_table(argv[1]))
     elif len(argv) >= 3 and argv[0] == "traffic":
         scale = float(argv[argv.index("--scale") + 1]) if "--scale" in argv else 1.0
+        workload = argv[argv.index("--workload") + 1] if "--workload" in argv else "skull-512"
         with open(argv[2], "w") as f:
-            json.dump(traffic(argv[1], scale), f, indent=1)
+            json.dump(traffic(argv[1], scale, workload), f, indent=1)
     else:
         print(__doc__)
         return 2

@@ -62,21 +62,25 @@ def test_roles_and_traffic_per_half_step(tmp_path, monkeypatch):
     assert t["fwd_stress"]["dram_bytes_per_launch"] == pytest.approx(9000)
     assert t["adj_a"]["dram_bytes_per_launch"] == pytest.approx(8500)
     assert t["adj_b"]["dram_bytes_per_launch"] == pytest.approx(3900)
-    assert all(v["source_sha"] == "abc" for v in t.values())
+    assert all(v["source_sha"] == "abc" and v["workload"] == "skull-512" for v in t.values())
+    assert profiling.traffic(p, workload="skull-256")["adj_b"]["workload"] == "skull-256"
     assert profiling.traffic(p, scale=8.0)["adj_b"]["dram_bytes_per_launch"] == pytest.approx(31200)
 
 
-def test_traffic_is_dropped_when_sources_change(tmp_path, monkeypatch):
+def test_traffic_is_dropped_when_sources_or_workload_change(tmp_path, monkeypatch):
     prof = tmp_path / "profiles"
     prof.mkdir()
-    json.dump({"adj_b": {"dram_bytes_per_launch": 5.0, "source_sha": "old", "scale": 1.0}},
+    json.dump({"adj_b": {"dram_bytes_per_launch": 5.0, "source_sha": "old", "scale": 1.0, "workload": "skull-512"}},
               open(prof / "traffic.json", "w"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "source_sha", lambda: "old")
-    assert bench.traffic_for("adj_b") == 5.0
-    assert bench.traffic_for("adj_a") is None
+    assert bench.traffic_for("adj_b", "skull-512") == 5.0
+    assert bench.traffic_for("adj_a", "skull-512") is None
+    # another workload (or the acoustic ablation) never takes the skull-512 figure
+    assert bench.traffic_for("adj_b", "skull-256") is None
+    assert bench.traffic_for("adj_b", "skull-512 mu=0") is None
     monkeypatch.setattr(bench, "source_sha", lambda: "new")
-    assert bench.traffic_for("adj_b") is None
+    assert bench.traffic_for("adj_b", "skull-512") is None
 
 
 class _Done:
