@@ -175,7 +175,12 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
  * min(ksteps, steps left) time steps, queued on `stream` (cudaStream_t) as one
  * replay of a captured CUDA graph of ksteps multi-instance steps; a solve that
  * finishes gets its read-out.  pact_begin of these handles must be ordered
- * before it (use the same stream).  Errors: PACT_EINVAL, PACT_ECUDA,
+ * before it (use the same stream).  All advances on one device share one
+ * device table of solves and one set of work counters, so the library orders
+ * them: an advance queued on a different stream than the previous advance on
+ * that device first waits (cudaStreamWaitEvent) for the previous replay, and
+ * advances on one device therefore never run concurrently.  Errors:
+ * PACT_EINVAL, PACT_ECUDA,
  * PACT_ETIMEOUT (an earlier advance on this device reported a timed-out
  * wait); message via pact_last_error(NULL). */
 int pact_advance(pact_handle* hs, int n, int ksteps, void* stream);
@@ -189,25 +194,33 @@ int pact_poll(pact_handle h, int* steps_done);
  * counterpart: this is a deployment variant of pact_forward for callers that
  * cannot call cudaMalloc -- code inside a host application that owns all device
  * memory through its own pool and forbids outside allocations (they would escape
- * its accounting, or fail once the pool has reserved the device), and
- * latency-critical loops where cudaMalloc / cudaFree would add implicit device
- * synchronisation.
+ * its accounting, or fail once the pool has reserved the device).
  * All working memory (wavefield 9N floats, C-PML slabs, profile tables,
  * receiver tables: about 36 bytes per grid point plus the slabs) comes from one
- * fixed file-scope device array of PACT_NOALLOC_SCRATCH_BYTES (64 MiB), which
- * every GPU that loads the library holds until the process exits; a grid too
- * large for it is rejected with PACT_EINVAL and a message giving the bytes it
- * would need (roughly up to 110^3 points with a thin layer).  Inputs and outputs
- * are the caller's: desc as for pact_create_grid; rho, lambda, mu, alpha and p0
- * device arrays of N floats (read only); rec_xyz a HOST array of L triples;
- * traces a device array of (nsteps+1)*L floats, overwritten, with the same
- * values pact_forward produces.  stream: cudaStream_t (NULL = legacy default).
- * The medium is checked first (one 16-byte read back that waits for the
- * stream); the steps are then queued asynchronously.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call
- * reuses the same array and clears what must start at zero; calls that overlap
- * on the GPU (two streams or two host threads) race and corrupt each other.
+ * fixed file-scope device array of PACT_NOALLOC_SCRATCH_BYTES (64 MiB); a grid
+ * too large for it is rejected with PACT_EINVAL and a message giving the bytes
+ * it would need (roughly up to 110^3 points with a thin layer).  The array is
+ * committed on a device when the library's module holding it is loaded there;
+ * under CUDA's default lazy module loading that is the first call of this
+ * entry point on the device (with that device current), unless other work of
+ * the library came first.  Make that first call at set-up time, before a pool
+ * reserves the device; from then on the device holds the array until the
+ * process exits, and later calls commit no device memory.
+ * Inputs and outputs are the caller's: desc as for pact_create_grid; rho,
+ * lambda, mu, alpha and p0 device arrays of N floats (read only); rec_xyz a
+ * HOST array of L triples; traces a device array of (nsteps+1)*L floats,
+ * overwritten, with the same values pact_forward produces.  stream:
+ * cudaStream_t (NULL = legacy default).
+ * Synchronisation: every call checks the medium on the device and reads the
+ * result back (16 bytes), which waits for the stream, and copies the C-PML and
+ * receiver tables from pageable host memory; so every call blocks the host
+ * until the stream reaches that point, and a call cannot be captured in a CUDA
+ * graph.  The steps are then queued asynchronously.  The array's device
+ * address is looked up (cudaGetSymbolAddress) on every call in the current
+ * context.  Every call reuses the same array and clears what must start at
+ * zero; calls that overlap on the GPU (two streams or two host threads) race
+ * and corrupt each other.  Unlike pact_forward, no count of p0 entries near
+ * the absorbing layer is kept (pact_support_warning has no counterpart here).
  * Errors: PACT_EINVAL, PACT_ECFL, PACT_ECUDA; message via pact_last_error(NULL). */
 #define PACT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho, const float* lambda, const float* mu,

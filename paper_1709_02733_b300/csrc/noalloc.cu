@@ -7,10 +7,15 @@
 // the device), and latency-critical loops in which cudaMalloc / cudaFree would
 // add implicit device synchronisation.  The regular entry points allocate a
 // handle's working memory; this one takes all of it from one fixed array that
-// the library declares at file scope, so it allocates nothing.
+// the library declares at file scope, so it allocates nothing.  Each call reads
+// the medium check back (it waits for the stream) and copies small tables from
+// pageable host memory, so a call blocks the host until its stream reaches the
+// check and cannot be captured in a CUDA graph.
 //
-// The array (PACT_NOALLOC_SCRATCH_BYTES, 64 MiB) exists on every GPU that loads
-// the library and stays there until the process exits.  It holds the wavefield,
+// The array (PACT_NOALLOC_SCRATCH_BYTES, 64 MiB) is committed on a GPU when the
+// module that holds it is loaded there -- at the latest by the first call of
+// this entry point on that device, under CUDA's default lazy module loading --
+// and stays there until the process exits.  It holds the wavefield,
 // the C-PML memory variables, the C-PML profile tables, the receiver tables and
 // a four-word medium reduction.  The medium, p0 and the traces stay in the
 // caller's buffers.  All calls share the array: each call clears what must
@@ -22,7 +27,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -48,31 +52,22 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[PACT_NOALLOC_SC
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
-
 int nerr(int code, const std::string& msg) {
     pact_note_error(msg);
     return code;
 }
 
-// Device address of the scratch array on the current device; looked up once
-// per device (the first call on a device does it, with that device current).
+// Device address of the scratch array in the current context, looked up on
+// every call (a cheap lookup) rather than cached per device ordinal: a host
+// that binds its own CUDA context gets its own copy of the module, and with it
+// another address.  The first lookup in a context loads the module that holds
+// the array, which commits its 64 MiB on that device.
 int scratch_address(unsigned char** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return nerr(PACT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return nerr(PACT_EINVAL, "device ordinal out of range for the scratch table");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return nerr(PACT_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return nerr(PACT_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    *out = static_cast<unsigned char*>(p);
     return PACT_OK;
 }
 
@@ -165,7 +160,13 @@ extern "C" int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho
     unsigned int hred[4] = {0, 0, 0, 0};
     NCK(cudaMemcpyAsync(hred, red, sizeof hred, cudaMemcpyDeviceToHost, st));
     NCK(cudaStreamSynchronize(st));
-    if (hred[2] != 0) return nerr(PACT_EINVAL, "medium: nodes violate rho > 0, mu >= 0, lambda + 2 mu > 0, alpha >= 0");
+    if (hred[2] != 0) {
+        char buf[192];
+        snprintf(buf, sizeof buf,
+                 "medium: %u nodes violate rho > 0, mu >= 0, lambda + 2 mu > 0, 3 lambda + 2 mu > 0, alpha >= 0",
+                 hred[2]);
+        return nerr(PACT_EINVAL, buf);
+    }
     float c2, amax;
     memcpy(&c2, &hred[0], 4);
     memcpy(&amax, &hred[1], 4);

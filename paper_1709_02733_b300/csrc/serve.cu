@@ -63,6 +63,10 @@ struct Server {
     int* err = nullptr;
     unsigned int* host_err = nullptr;  // pinned copy of the status word
     cudaStream_t cap = nullptr;
+    // the last replay queued on this device: an advance queued on another
+    // stream waits for it, since every replay reads the one table at dT
+    cudaEvent_t last = nullptr;
+    bool have_last = false;
     struct Graph {
         cudaGraphExec_t exec = nullptr;
         int* next = nullptr;  // work-item counters of the graph's launches
@@ -99,6 +103,7 @@ int serve_run(const MultiTable& T, int ksteps, cudaStream_t st, std::string& why
         SCK(cudaMallocHost(&S.host_err, sizeof(unsigned int)));
         *S.host_err = 0;
         SCK(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
+        SCK(cudaEventCreateWithFlags(&S.last, cudaEventDisableTiming));
     }
     if (*S.host_err) {
         why = *S.host_err == 2 ? "serve: a multi-instance work item fell outside its grid (skipped)"
@@ -126,8 +131,12 @@ int serve_run(const MultiTable& T, int ksteps, cudaStream_t st, std::string& why
         it = S.graphs.emplace(ksteps, G).first;
     }
     const size_t bytes = offsetof(MultiTable, inst) + (size_t)T.n_inst * sizeof(InstDev);
+    // the table copy must not overtake a replay still reading the table
+    if (S.have_last) SCK(cudaStreamWaitEvent(st, S.last, 0));
     SCK(cudaMemcpyAsync(S.dT, &T, bytes, cudaMemcpyHostToDevice, st));
     SCK(cudaGraphLaunch(it->second.exec, st));
+    SCK(cudaEventRecord(S.last, st));
+    S.have_last = true;
     SCK(cudaMemcpyAsync(S.host_err, S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
 #undef SCK
     return PACT_OK;

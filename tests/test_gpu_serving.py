@@ -1,5 +1,6 @@
 """Serving on the GPU: solves advanced together by the persistent
-multi-instance kernels give the same results as the same solves alone, and a
+multi-instance kernels give the same results as the same solves alone and as
+the FP64 oracle's H and H^T (Appendix A.3, Eqs. (HPML) and (AdjupPML)), and a
 queued stream served with continuous batching completes with correct results."""
 import numpy as np
 import pytest
@@ -12,6 +13,7 @@ from paper_1709_02733_b300.serving import InputCache, make_stream, run_continuou
 from paper_1709_02733_b300.synth import GridDesc  # noqa: E402
 
 TOL_MIX = 1e-6
+TOL_ORACLE = 1e-4  # FP32 kernels against the FP64 oracle, relative L2
 
 
 def rel_l2(a, b):
@@ -38,7 +40,7 @@ def _random(shape, npml, seed, L):
     return d, (rho, lam, mu, al), rng.standard_normal(shape).astype(np.float32), synth.random_receivers(L, shape, seed)
 
 
-def test_mixed_solves_match_solo():
+def _mix_cases():
     w = synth.skull(48, 1.2e-3, 6, 60, 40, seed=21)
     cases = [("fwd", w.desc, w.medium, w.p0, w.rec, 60)]
     d, med, p0, rec = _random((36, 44, 40), 3, 22, 17)
@@ -52,7 +54,14 @@ def test_mixed_solves_match_solo():
     cases.append(("fwd", d, med, p0, rec, 41))
     d, med, p0, rec = _random((52, 37, 100), 5, 25, 23)
     cases.append(("adj", d, med, p0, rec, 47))
-    grids, bufs, solo = [], [], []
+    return cases
+
+
+def _serve_mix(cases, k=7):
+    """Begin every case on its own handle, advance them all together with
+    pact_advance (k steps per call) and return, per case, the input, the
+    served result and the same solve run alone."""
+    grids, out = [], []
     rng = np.random.default_rng(3)
     for kind, d, med, p0, rec, ns in cases:
         g = pact.Grid(d)
@@ -60,25 +69,49 @@ def test_mixed_solves_match_solo():
         if kind == "fwd":
             inp = cuda(p0)
             ref = g.forward(inp, rec, ns).cpu().numpy()
-            out = torch.full((ns + 1, rec.shape[0]), float("nan"), device="cuda")
+            res = torch.full((ns + 1, rec.shape[0]), float("nan"), device="cuda")
         else:
             inp = cuda(rng.standard_normal((ns + 1, rec.shape[0])))
             ref = g.adjoint(inp, rec).cpu().numpy()
-            out = torch.full(d.shape, float("nan"), device="cuda")
-        g.begin(kind == "adj", inp, rec, ns, out)
+            res = torch.full(d.shape, float("nan"), device="cuda")
+        g.begin(kind == "adj", inp, rec, ns, res)
         grids.append(g)
-        bufs.append((inp, out))
-        solo.append(ref)
-    k = 7
+        out.append((inp, res, ref))
     for _ in range(100):
         if all(g.poll() >= c[5] for g, c in zip(grids, cases)):
             break
         pact.pact_advance(grids, k)
     torch.cuda.synchronize()
-    for (kind, *_rest), (inp, out), ref in zip(cases, bufs, solo):
-        got = out.cpu().numpy()
+    served = [(inp.cpu().numpy(), res.cpu().numpy(), ref) for inp, res, ref in out]
+    for g in grids:
+        g.close()
+    return served
+
+
+def test_mixed_solves_match_solo():
+    cases = _mix_cases()
+    for (kind, *_rest), (_inp, got, ref) in zip(cases, _serve_mix(cases)):
         assert np.all(np.isfinite(got)), kind
         assert rel_l2(got, ref) <= TOL_MIX, kind
+
+
+def test_served_results_match_oracle():
+    """Every solve of a served mix (forward and adjoint instances, on grids
+    holding interior, z-slab, edge and corner work items) against the FP64
+    oracle's H p0 / H^T y on the same inputs: this covers the persistent
+    multi-instance step kernels and the multi-instance receiver kernel
+    (sampling, and injection weighted by 3 lambda + 2 mu in the adjoint's
+    variables)."""
+    from oracle import Oracle
+    cases = _mix_cases()
+    kinds = {c[0] for c in cases}
+    assert kinds == {"fwd", "adj"}
+    for (kind, d, med, p0, rec, ns), (inp, got, _ref) in zip(cases, _serve_mix(cases, k=5)):
+        o = Oracle(d.as_dict(), *med)
+        want = o.forward(p0, rec, ns) if kind == "fwd" else o.adjoint(inp, rec)
+        assert np.all(np.isfinite(got)), kind
+        assert np.linalg.norm(want) > 0, kind
+        assert rel_l2(got, want) <= TOL_ORACLE, (kind, d.shape, rel_l2(got, want))
 
 
 def test_continuous_batching_stream():

@@ -120,3 +120,18 @@ def test_algorithmic_bytes_of_the_step():
     assert total == 37155241984
     assert total / (2 * N) == pytest.approx(138.414, abs=1e-3)
     assert bench.algorithmic_bytes("fwd_velocity", synth.GridDesc(8, 8, 8, 1e-3, 1e-7, npml=0), 0) == 56 * 512
+
+
+def test_compulsory_bytes_of_the_single_pass_step():
+    """The roofline's bytes: 88 B per grid point (nine fields read and written,
+    four medium arrays read) plus 48 B per C-PML slab point of each axis (six
+    memory variables read and written).  At 512^3 with a 20-cell layer (41
+    slab planes per axis) that is 99.53 B per update, 26.7 GB per forward +
+    adjoint step pair; a 7.581 ms step pair then runs at 0.554 of 6429 GB/s."""
+    d = synth.GridDesc(512, 512, 512, 0.2e-3, 19.7e-9, npml=20)
+    b = bench.survey_bytes_per_step(d)
+    assert b == 88 * d.N + 48 * 3 * 512 * 512 * 41
+    assert b / d.N == pytest.approx(99.53, abs=5e-3)
+    assert 2 * b / 7.581e-3 / 1e9 / 6429.0 == pytest.approx(0.548, abs=2e-3)
+    d0 = synth.GridDesc(64, 64, 64, 0.5e-3, 1e-7, npml=0)
+    assert bench.survey_bytes_per_step(d0) == 88 * 64 ** 3

@@ -2,9 +2,10 @@
 device memory.
 
 Some hosts own every byte of device memory through their own pool and forbid
-outside cudaMalloc / cudaFree; some latency-critical loops cannot afford the
-implicit synchronisation those calls bring.  The no-allocation entry point
-serves them from a fixed 64 MiB array inside the library.  These tests call it
+outside cudaMalloc / cudaFree (such an allocation escapes the pool's accounting
+or fails once the pool has reserved the device).  The no-allocation entry point
+serves them from a fixed 64 MiB array inside the library, committed on a device
+by the first call there; later calls commit no device memory.  These tests call it
 through the C ABI and check its traces against the regular entry point
 pact_forward, within the parity tolerance used everywhere else (relative L2
 <= 1e-4), on two calls in a row with different inputs (the second call must not
@@ -94,3 +95,24 @@ def test_noalloc_rejects_grid_beyond_the_fixed_array(lib):
     assert rc == pact.PACT_EINVAL
     msg = lib.pact_last_error(None).decode()
     assert "scratch" in msg and "bytes" in msg
+
+
+def test_noalloc_later_calls_commit_no_device_memory(lib):
+    """Once the first call on the device has loaded the array, a further call
+    changes the device's free memory by nothing (cudaMemGetInfo)."""
+    shape = (20, 24, 28)
+    rho, lam, mu, al, vmax = synth.random_medium(shape, 81)
+    desc = GridDesc(shape[2], shape[1], shape[0], 1e-3, 0.3e-3 / vmax, npml=2, pml_vmax=vmax)
+    med = [cuda(m) for m in (rho, lam, mu, al)]
+    p0 = cuda(np.random.default_rng(82).standard_normal(shape))
+    rec = synth.random_receivers(8, shape, 83)
+    outs = [torch.empty((31, 8), device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    assert noalloc_call(lib, desc, med, p0, rec, 30, outs[0]) == pact.PACT_OK, lib.pact_last_error(None)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert noalloc_call(lib, desc, med, p0, rec, 30, outs[1]) == pact.PACT_OK, lib.pact_last_error(None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(outs[0], outs[1])
