@@ -90,6 +90,10 @@ struct pact_grid {
     bool fused = false;
     // mu = 0 at every node: the interior runs the acoustic kernels
     bool acoustic = false;
+    // mu > 0 somewhere: the fluid interior work items run the acoustic
+    // kernels, the rest the elastic ones (plan built from the medium)
+    bool mixed = false;
+    MixedPlan mixed_plan{};
     float* fields2 = nullptr;
     int cur = 0;
     TmaSet tmp[2]{};
@@ -383,7 +387,7 @@ static int device_status(pact_handle h) {
 // launches, with the single-pass interior launch between them when the
 // handle runs on two buffers (the step then reads buffer c and writes 1-c).
 static int step_mode(pact_handle h) {
-    return h->fused ? STEP_FUSED : (h->acoustic ? STEP_ACOUSTIC : STEP_TWO_PASS);
+    return h->fused ? STEP_FUSED : (h->acoustic ? STEP_ACOUSTIC : (h->mixed ? STEP_MIXED : STEP_TWO_PASS));
 }
 
 static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj) {
@@ -392,11 +396,12 @@ static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj) {
     const int mode = step_mode(h);
     const TmaSet& tm = fz ? h->tmp[c] : h->tm;
     const SplitStreams ss{h->stream, fz ? nullptr : h->aux, h->ev_fork, h->ev_join, fz ? nullptr : h->aux2, h->ev_join2};
-    mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, mode));
+    const MixedPlan* mp = h->mixed ? &h->mixed_plan : nullptr;
+    mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, mode, mp));
     if (h->acoustic)
         mark(h, adj ? PACT_K_ADJ_AC_A : PACT_K_FWD_AC_VEL, launch_acoustic_step(false, adj, p, tm, err, h->stream));
     if (fz) mark(h, adj ? PACT_K_ADJ_FUSED : PACT_K_FWD_FUSED, launch_fused_step(adj, p, h->fmp[c], err, h->stream));
-    mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, tm, err, ss, mode));
+    mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, tm, err, ss, mode, mp));
     if (h->acoustic)
         mark(h, adj ? PACT_K_ADJ_AC_B : PACT_K_FWD_AC_STR, launch_acoustic_step(true, adj, p, tm, err, h->stream));
 }
@@ -672,8 +677,17 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     // mu = 0 everywhere (the acoustic operator pair of the paper's ablation):
     // the interior runs the acoustic kernels unless PACT_ACOUSTIC=0
     const char* aenv = getenv("PACT_ACOUSTIC");
-    h->acoustic = h->tiled && !h->fused && red[4] == 0 && !(aenv && std::strcmp(aenv, "0") == 0) &&
-                  role_points(3, STEP_ACOUSTIC, make_params(h)) > 0;  // needs a layer (see plan_for)
+    const bool ac_ok = h->tiled && !h->fused && !(aenv && std::strcmp(aenv, "0") == 0);
+    h->acoustic = ac_ok && red[4] == 0 && role_points(3, STEP_ACOUSTIC, make_params(h)) > 0;  // needs a layer (see plan_for)
+    // mu > 0 somewhere: the interior work items whose reach is all fluid run
+    // the acoustic kernels (the same operator there); PACT_ACOUSTIC=0 keeps
+    // the elastic kernels everywhere
+    h->mixed = false;
+    if (ac_ok && red[4] != 0) {
+        if (build_mixed_plan(make_params(h), h->medium + 2 * h->N, s, &h->mixed_plan) != 0)
+            return fail(h, PACT_ECUDA, "building the fluid / solid work lists of the medium failed");
+        h->mixed = h->mixed_plan.acoustic_points > 0;
+    }
     h->medium_set = true;
     return PACT_OK;
 }
@@ -727,6 +741,7 @@ int pact_destroy(pact_handle h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->fields);
+free_mixed_plan(&h->mixed_plan);
     cudaFree(h->fields2);
     cudaFree(h->medium);
     cudaFree(h->tables);
@@ -809,10 +824,12 @@ int pact_role_points(pact_handle h, int kind, long long* points, long long* slab
     if (fz || ac) {
         // the single-pass and acoustic regions lie off the slabs
         *points = fz ? (h->fused ? role_points(2, STEP_FUSED, p) : 0)
-                     : (h->acoustic ? role_points(3, STEP_ACOUSTIC, p) : 0);
+                     : (h->acoustic ? role_points(3, STEP_ACOUSTIC, p)
+                                    : (h->mixed ? h->mixed_plan.acoustic_points : 0));
         *slab_points = 0;
     } else if (h->tiled) {
-        *points = role_points(vel ? 0 : 1, step_mode(h), p);
+        *points = h->mixed ? (long long)h->N - h->mixed_plan.acoustic_points
+                           : role_points(vel ? 0 : 1, step_mode(h), p);
         *slab_points = slabs;
     } else {
         *points = (long long)h->N;

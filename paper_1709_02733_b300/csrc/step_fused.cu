@@ -150,16 +150,8 @@ __device__ __forceinline__ void drain(uint64_t* bar, int pfrom, int pto, int pfi
 }
 
 __device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1) {
-    int r = 0;
-    while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
-    const Region& R = rl.r[r];
-    const int lb = b - R.bstart;
-    const int ntx = R.tx1 - R.tx0, nt = ntx * (R.ty1 - R.ty0);
-    const int t = lb % nt, ch = lb / nt;
-    tile_x = R.tx0 + t % ntx;
-    tile_y = R.ty0 + t / ntx;
-    zc0 = R.za + ch * R.zc;
-    zc1 = min(zc0 + R.zc, R.zb);
+    int kind;
+    locate_item(rl, b, tile_x, tile_y, zc0, zc1, kind);
 }
 
 template <int P>

@@ -34,6 +34,7 @@
 // Requirements: nx % 4 == 0 (TMA global strides are multiples of 16 bytes).
 #include <algorithm>
 #include <mutex>
+#include <vector>
 #include <type_traits>
 
 #include "pact_internal.cuh"
@@ -59,6 +60,9 @@ constexpr int D = 4;            // stage ring depth (planes)
 // The frame tiles run in three launches (PM_X, PM_Y, PM_FULL); the interior
 // launch (PM_NONE) runs, per block, the PM_NONE or the PM_Z body.
 constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2, PM_X = 3, PM_Y = 4;
+// A fluid work item of a medium-adaptive step (no layer code, the reach all
+// fluid): the acoustic kernels run it.
+constexpr int PM_AC = 5;
 constexpr bool has_x(int pm) { return pm == PM_FULL || pm == PM_X; }
 constexpr bool has_y(int pm) { return pm == PM_FULL || pm == PM_Y; }
 
@@ -122,6 +126,11 @@ static_assert(VelCfg<true, PM_FULL>::SMEM >= VelCfg<true, PM_X>::SMEM &&
 
 __device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1,
                                        int& kind) {
+    locate_item(rl, b, tile_x, tile_y, zc0, zc1, kind);
+}
+// the same for a list held inline (the persistent multi-instance kernels)
+__device__ __forceinline__ void locate_inline(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0,
+                                              int& zc1, int& kind) {
     int r = 0;
     while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
     const Region& R = rl.r[r];
@@ -1061,8 +1070,8 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
         const InstDev& I = T->inst[i];
         if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
         int tile_x, tile_y, zc0, zc1, kind;
-        locate(PM == PM_FULL ? I.corner : (PM == PM_X ? I.edge : I.inner), item - pre[i], tile_x, tile_y, zc0, zc1,
-               kind);
+        locate_inline(PM == PM_FULL ? I.corner : (PM == PM_X ? I.edge : I.inner), item - pre[i], tile_x, tile_y, zc0,
+                      zc1, kind);
         // a work item must lie inside its instance's grid and the instance
         // must be of this kernel's direction; otherwise record the
         // inconsistency and touch nothing
@@ -1361,11 +1370,16 @@ long long region_points(const RegionList& rl, const StepParams& p) {
 // The frame launch goes to `aux` (when given) between a fork and a join
 // event, so that it overlaps the interior launch on `st`.
 template <bool ADJ>
-static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
-    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, mode);
+static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode,
+                            const MixedPlan* mp) {
+    const bool mixed = mode == STEP_MIXED && mp;
+    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, mixed ? STEP_TWO_PASS : mode);
+    const RegionList& inner = mixed ? mp->elastic : L.inner;
+    const int inner_blocks = mixed ? mp->elastic_blocks : L.inner_blocks;
+    const int ac_blocks = mixed ? mp->acoustic_blocks : 0;
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
-    const bool split = ss.aux && nframe && L.inner_blocks;
+    const bool split = ss.aux && nframe && (inner_blocks || ac_blocks);
     cudaStream_t so = ss.st, sc = ss.st;
     const bool split2 = split && ss.aux2 && L.corner_blocks && L.edge_blocks;
     if (split) {
@@ -1381,8 +1395,9 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
         k_vel_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, VelCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, L.corner, err);
     if (L.edge_blocks)
         k_vel_tiled<ADJ, PM_X><<<L.edge_blocks, blk, VelCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
-    if (L.inner_blocks)
-        k_vel_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
+    if (inner_blocks)
+        k_vel_tiled<ADJ, PM_NONE><<<inner_blocks, blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, inner, err);
+    if (ac_blocks) launch_acoustic(false, ADJ, p, tm, mp->acoustic, ac_blocks, err, ss.st);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
@@ -1391,15 +1406,20 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
             cudaStreamWaitEvent(ss.st, ss.join2, 0);
         }
     }
-    return nframe + (L.inner_blocks > 0);
+    return nframe + (inner_blocks > 0) + (ac_blocks > 0);
 }
 
 template <bool ADJ>
-static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
-    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, mode);
+static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode,
+                            const MixedPlan* mp) {
+    const bool mixed = mode == STEP_MIXED && mp;
+    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, mixed ? STEP_TWO_PASS : mode);
+    const RegionList& inner = mixed ? mp->elastic : L.inner;
+    const int inner_blocks = mixed ? mp->elastic_blocks : L.inner_blocks;
+    const int ac_blocks = mixed ? mp->acoustic_blocks : 0;
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
-    const bool split = ss.aux && nframe && L.inner_blocks;
+    const bool split = ss.aux && nframe && (inner_blocks || ac_blocks);
     cudaStream_t so = ss.st, sc = ss.st;
     const bool split2 = split && ss.aux2 && L.corner_blocks && L.edge_blocks;
     if (split) {
@@ -1415,8 +1435,9 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
         k_str_tiled<ADJ, PM_FULL><<<L.corner_blocks, blk, StrCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, L.corner, err);
     if (L.edge_blocks)
         k_str_tiled<ADJ, PM_X><<<L.edge_blocks, blk, StrCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
-    if (L.inner_blocks)
-        k_str_tiled<ADJ, PM_NONE><<<L.inner_blocks, blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, L.inner, err);
+    if (inner_blocks)
+        k_str_tiled<ADJ, PM_NONE><<<inner_blocks, blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, inner, err);
+    if (ac_blocks) launch_acoustic(true, ADJ, p, tm, mp->acoustic, ac_blocks, err, ss.st);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
@@ -1425,7 +1446,7 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
             cudaStreamWaitEvent(ss.st, ss.join2, 0);
         }
     }
-    return nframe + (L.inner_blocks > 0);
+    return nframe + (inner_blocks > 0) + (ac_blocks > 0);
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
@@ -1490,12 +1511,128 @@ void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& 
     ncorner = rechunk(corner);
 }
 
-int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
-    return adj ? launch_vel_impl<true>(p, tm, err, ss, mode) : launch_vel_impl<false>(p, tm, err, ss, mode);
+int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode,
+                     const MixedPlan* mp) {
+    return adj ? launch_vel_impl<true>(p, tm, err, ss, mode, mp) : launch_vel_impl<false>(p, tm, err, ss, mode, mp);
 }
 
-int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode) {
-    return adj ? launch_str_impl<true>(p, tm, err, ss, mode) : launch_str_impl<false>(p, tm, err, ss, mode);
+int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode,
+                     const MixedPlan* mp) {
+    return adj ? launch_str_impl<true>(p, tm, err, ss, mode, mp) : launch_str_impl<false>(p, tm, err, ss, mode, mp);
+}
+
+// ---- medium-adaptive interior (STEP_MIXED) ---------------------------------
+// out[z * ntiles + t] = 1 if mu > 0 at any node of interior tile t's x-y reach
+// (x0-3 .. x0+TX+2, y0-3 .. y0+TY+2, clipped to the grid) on plane z.
+__global__ void k_tile_solid(const float* __restrict__ mu, int nx, int ny, int txlo, int tylo, int ntx, int nty,
+                             unsigned char* __restrict__ out) {
+    const int t = blockIdx.x, z = blockIdx.y;
+    const int x0 = (txlo + t % ntx) * TX, y0 = (tylo + t / ntx) * TY;
+    constexpr int RW = TX + 6, RH = TY + 6;
+    bool any = false;
+    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
+        const int x = x0 - 3 + i % RW, y = y0 - 3 + i / RW;
+        if (x >= 0 && x < nx && y >= 0 && y < ny) any |= __ldg(mu + ((size_t)z * ny + y) * nx + x) > 0.0f;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) out[(size_t)z * ntx * nty + t] = any ? 1 : 0;
+}
+
+void free_mixed_plan(MixedPlan* mp) {
+    cudaFree(mp->mem);
+    *mp = MixedPlan{};
+}
+
+int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, MixedPlan* mp) {
+    free_mixed_plan(mp);
+    int txlo, txhi, tylo, tyhi;
+    if (p.P <= 0 || !interior_tiles(p, txlo, txhi, tylo, tyhi)) return 0;
+    const int ntx = txhi + 1 - txlo, nty = tyhi + 1 - tylo, ntiles = ntx * nty;
+    // the no-layer planes of the interior tiles (as in make_regions)
+    const int za = std::min(p.P + 2, p.nz), zb = std::max(za, p.nz - p.P - 3);
+    if (zb <= za) return 0;
+    unsigned char* d_flag = nullptr;
+    const size_t nflag = (size_t)p.nz * ntiles;
+    if (cudaMalloc(&d_flag, nflag) != cudaSuccess) return 1;
+    k_tile_solid<<<dim3(ntiles, p.nz), 256, 0, st>>>(mu, p.nx, p.ny, txlo, tylo, ntx, nty, d_flag);
+    std::vector<unsigned char> flag(nflag);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, nflag, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_flag);
+    if (e != cudaSuccess) return 1;
+    // Segments of each tile column over [za, zb): fluid where no plane of
+    // z-3 .. z+3 has a solid node in the tile's reach.  The work items are cut
+    // at a common grid of z chunks and ordered chunk by chunk, so that the
+    // blocks resident at one time work on the same planes of neighbouring
+    // tiles and find each other's halo rows in L2.
+    // Two lists, each ordered by z chunk so that the blocks resident at one
+    // time work on the same planes of neighbouring tiles: the elastic items
+    // (the no-layer segments with solid in reach, and the z-slab planes of
+    // the interior tiles) for the elastic interior kernels, and the fluid
+    // segments for the acoustic kernels (which keep their own, higher
+    // occupancy).
+    std::vector<Region> el, ac;
+    int el_blocks = 0, ac_blocks = 0;
+    long long el_pts = 0, ac_pts = 0;
+    constexpr int kChunk = 48;  // planes per work item at most
+    auto add = [&](int tx0, int tx1, int ty0, int ty1, int a, int b, int kind) {
+        if (b <= a) return;
+        const bool fluid = kind == PM_AC;
+        std::vector<Region>& v = fluid ? ac : el;
+        int& blocks = fluid ? ac_blocks : el_blocks;
+        v.push_back(Region{tx0, tx1, ty0, ty1, a, b, b - a, blocks, kind});
+        const long long tiles = (long long)(tx1 - tx0) * (ty1 - ty0);
+        blocks += (int)tiles;
+        (fluid ? ac_pts : el_pts) += tiles * TX * TY * (b - a);
+    };
+    std::vector<unsigned char> solid((size_t)p.nz * ntiles);
+    for (int t = 0; t < ntiles; ++t)
+        for (int z = 0; z < p.nz; ++z) {
+            unsigned char any = 0;
+            for (int k = std::max(0, z - 3); k <= std::min(p.nz - 1, z + 3); ++k) any |= flag[(size_t)k * ntiles + t];
+            solid[(size_t)z * ntiles + t] = any;
+        }
+    // the z-slab planes of the interior tiles (z-layer code) below and above
+    add(txlo, txhi + 1, tylo, tyhi + 1, 0, za, PM_Z);
+    const int nchunk = (zb - za + kChunk - 1) / kChunk;
+    const int zc = (zb - za + nchunk - 1) / nchunk;
+    for (int c0 = za; c0 < zb; c0 += zc) {
+        const int c1 = std::min(zb, c0 + zc);
+        for (int t = 0; t < ntiles; ++t) {
+            const int tx = txlo + t % ntx, ty = tylo + t / ntx;
+            int a = c0;
+            while (a < c1) {
+                const unsigned char f = solid[(size_t)a * ntiles + t];
+                int b = a + 1;
+                while (b < c1 && solid[(size_t)b * ntiles + t] == f) ++b;
+                add(tx, tx + 1, ty, ty + 1, a, b, f ? PM_NONE : PM_AC);
+                a = b;
+            }
+        }
+    }
+    add(txlo, txhi + 1, tylo, tyhi + 1, zb, p.nz, PM_Z);
+    const size_t n = el.size() + ac.size();
+    if (cudaMalloc(&mp->mem, n * sizeof(Region)) != cudaSuccess) return 1;
+    std::vector<Region> all(el);
+    all.insert(all.end(), ac.begin(), ac.end());
+    e = cudaMemcpyAsync(mp->mem, all.data(), n * sizeof(Region), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_mixed_plan(mp);
+        return 1;
+    }
+    mp->elastic.n = 0;
+    mp->elastic.dev = el.empty() ? nullptr : mp->mem;
+    mp->elastic.dn = (int)el.size();
+    mp->acoustic.n = 0;
+    mp->acoustic.dev = ac.empty() ? nullptr : mp->mem + el.size();
+    mp->acoustic.dn = (int)ac.size();
+    mp->elastic_blocks = el_blocks;
+    mp->acoustic_blocks = ac_blocks;
+    mp->elastic_points = el_pts;
+    mp->acoustic_points = ac_pts;
+    return 0;
 }
 
 int launch_acoustic_step(bool str, bool adj, const StepParams& p, const TmaSet& tm, int* err, cudaStream_t st) {

@@ -19,10 +19,44 @@ struct Region {
     int tx0, tx1, ty0, ty1, za, zb, zc, bstart, kind;
 };
 constexpr int kMaxRegions = 8;
+// Up to kMaxRegions regions inline, or (dev set) dn regions in device memory,
+// ordered by bstart.
 struct RegionList {
     int n;
     Region r[kMaxRegions];
+    const Region* dev = nullptr;
+    int dn = 0;
 };
+
+// The region holding work item b: the last region whose first block is <= b.
+__device__ __forceinline__ Region region_of(const RegionList& rl, int b) {
+    if (rl.dev) {
+        int lo = 0, hi = rl.dn - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&rl.dev[mid].bstart) <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        return rl.dev[lo];
+    }
+    int r = 0;
+    while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
+    return rl.r[r];
+}
+
+// tile, z chunk [zc0, zc1) and C-PML kind of work item b
+__device__ __forceinline__ void locate_item(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0,
+                                            int& zc1, int& kind) {
+    const Region R = region_of(rl, b);
+    const int lb = b - R.bstart;
+    const int ntx = R.tx1 - R.tx0, nt = ntx * (R.ty1 - R.ty0);
+    const int t = lb % nt, ch = lb / nt;
+    tile_x = R.tx0 + t % ntx;
+    tile_y = R.ty0 + t / ntx;
+    zc0 = R.za + ch * R.zc;
+    zc1 = min(zc0 + R.zc, R.zb);
+    kind = R.kind;
+}
 
 // One instance (a forward or adjoint solve on its own grid) of the
 // persistent multi-instance step kernels.
@@ -71,12 +105,38 @@ struct SplitStreams {
 //   STEP_ACOUSTIC  (mu = 0 everywhere) the no-layer interior region runs the
 //                  acoustic kernels: launch_vel_tiled + launch_acoustic_step
 //                  (velocity), launch_str_tiled + launch_acoustic_step (stress).
-enum { STEP_TWO_PASS = 0, STEP_FUSED = 1, STEP_ACOUSTIC = 2 };
-// Both return the number of kernels launched.
+//   STEP_MIXED     (mu > 0 somewhere) the interior work items whose whole
+//                  reach is fluid run the acoustic kernels, the others the
+//                  elastic ones, from a per-medium plan (MixedPlan).
+enum { STEP_TWO_PASS = 0, STEP_FUSED = 1, STEP_ACOUSTIC = 2, STEP_MIXED = 3 };
+
+// Interior work lists of a medium (STEP_MIXED), in device memory.  An
+// interior tile and plane is fluid if mu = 0 at every integer node of its
+// reach (x0-3 .. x0+TX+2, y0-3 .. y0+TY+2, z-3 .. z+3): there every stress
+// and velocity the elastic update reads has sigma^11 = sigma^22 = sigma^33
+// and zero shear, so the acoustic update is the same operator.
+struct MixedPlan {
+    RegionList elastic;      // elastic interior items (no-layer segments and the z-slab planes)
+    int elastic_blocks = 0;
+    RegionList acoustic;     // fluid no-layer segments
+    int acoustic_blocks = 0;
+    long long elastic_points = 0, acoustic_points = 0;
+    Region* mem = nullptr;   // device allocation behind both lists
+};
+// Build the plan of the grid of p for the medium's mu (device array);
+// returns 0 on success (mp->acoustic_points may be 0), nonzero on a CUDA
+// error.  Synchronises st.
+int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, MixedPlan* mp);
+void free_mixed_plan(MixedPlan* mp);
+
+// Both return the number of kernels launched.  With mode STEP_MIXED, mp
+// gives the interior work lists: the elastic items replace the interior
+// launch and the fluid items run the acoustic kernels after it on the main
+// stream, beside the frame launches.
 int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
-                     int mode = STEP_TWO_PASS);
+                     int mode = STEP_TWO_PASS, const MixedPlan* mp = nullptr);
 int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
-                     int mode = STEP_TWO_PASS);
+                     int mode = STEP_TWO_PASS, const MixedPlan* mp = nullptr);
 
 // Acoustic interior kernels (step_acoustic.cu): the elastic tensor maps (the
 // velocity kernel reads sigma^11, rho, alpha; the stress kernel u^1..u^3).
