@@ -686,7 +686,8 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     if (ac_ok && red[4] != 0) {
         if (build_mixed_plan(make_params(h), h->medium + 2 * h->N, s, &h->mixed_plan) != 0)
             return fail(h, PACT_ECUDA, "building the fluid / solid work lists of the medium failed");
-        h->mixed = h->mixed_plan.acoustic_points > 0;
+        const long long* np = h->mixed_plan.points;
+        h->mixed = np[MX_INT_AC] + np[MX_INT_FZ] + np[MX_EDGE_FL] + np[MX_CORNER_FL] > 0;
     }
     h->medium_set = true;
     return PACT_OK;
@@ -825,10 +826,10 @@ int pact_role_points(pact_handle h, int kind, long long* points, long long* slab
         // the single-pass and acoustic regions lie off the slabs
         *points = fz ? (h->fused ? role_points(2, STEP_FUSED, p) : 0)
                      : (h->acoustic ? role_points(3, STEP_ACOUSTIC, p)
-                                    : (h->mixed ? h->mixed_plan.acoustic_points : 0));
+                                    : (h->mixed ? h->mixed_plan.points[MX_INT_AC] : 0));
         *slab_points = 0;
     } else if (h->tiled) {
-        *points = h->mixed ? (long long)h->N - h->mixed_plan.acoustic_points
+        *points = h->mixed ? (long long)h->N - h->mixed_plan.points[MX_INT_AC]
                            : role_points(vel ? 0 : 1, step_mode(h), p);
         *slab_points = slabs;
     } else {

@@ -41,324 +41,7 @@
 #include "step_tiled.cuh"
 #include "tma.cuh"
 
-namespace tiled {
-
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int BW = TX + 8;      // box columns x0-4 .. x0+TX+3
-constexpr int BH = TY + 5;      // box rows    y0-2 .. y0+TY+2
-constexpr int BOX = BW * BH;    // 520 floats
-constexpr int BOXS = 544;       // box stride in floats (2176 B, 128-B aligned)
-constexpr int OX = 4, OY = 2;   // own point offset inside the box
-constexpr int D = 4;            // stage ring depth (planes)
-
-// C-PML code of a work-item body:
-//   PM_NONE  no layer (tiles and planes whose reach stays off every slab, or P = 0)
-//   PM_FULL  x, y and z layers (corner tiles: halo on an x and a y slab)
-//   PM_X     x and z layers (tiles whose halo touches an x slab only)
-//   PM_Y     y and z layers (tiles whose halo touches a y slab only)
-//   PM_Z     z layer only (the other tiles, planes on the z slabs)
-// The frame tiles run in three launches (PM_X, PM_Y, PM_FULL); the interior
-// launch (PM_NONE) runs, per block, the PM_NONE or the PM_Z body.
-constexpr int PM_NONE = 0, PM_FULL = 1, PM_Z = 2, PM_X = 3, PM_Y = 4;
-// A fluid work item of a medium-adaptive step (no layer code, the reach all
-// fluid): the acoustic kernels run it.
-constexpr int PM_AC = 5;
-constexpr bool has_x(int pm) { return pm == PM_FULL || pm == PM_X; }
-constexpr bool has_y(int pm) { return pm == PM_FULL || pm == PM_Y; }
-
-// Frame adjoint blocks copy the memory variables at their threads' cross
-// positions (two positions, three values per layer axis) one plane ahead with
-// cp.async into two plane slots of shared memory.
-constexpr int mv_values(int pm) { return (has_x(pm) ? 3 : 0) + (has_y(pm) ? 3 : 0); }
-// Layout [slot][value][cross position]: a thread's positions are tid and
-// tid + TX*TY (the second exists for the first 160 threads only).
-constexpr int mv_floats(int pm) { return 2 * mv_values(pm) * ((TX + 4) * TY + 4 * TX); }
-
-template <bool ADJ, int PM> struct VelCfg {
-    static constexpr bool PML = PM != PM_NONE, LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
-    // stage boxes 0..5: sigma (forward) or Q (adjoint), Voigt order; 6 rho,
-    // 7 alpha.  Frame adjoint blocks form the layer-augmented fields F in
-    // place and keep the x-differenced F^21, which differs from the
-    // y-differenced F^12 inside the layers, in one extra box.  The adjoint
-    // edge bodies read alpha through the cache instead (own point one plane
-    // ahead, +x / +y neighbours from L1), which brings their layout under the
-    // shared memory of three blocks per SM.
-    static constexpr bool ABOX = !(ADJ && (PM == PM_X || PM == PM_Y));
-    static constexpr int NB = ABOX ? 8 : 7;
-    static constexpr int BRHO = 6, BALPHA = 7;
-    static constexpr int NDER = (ADJ && PXY) ? 1 : 0;
-    static constexpr int MV = ADJ ? mv_floats(PM) : 0;  // floats of the memory-variable buffer
-    static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
-    __host__ __device__ static constexpr int tm(int b) { return b < 6 ? TM_S0 + b : (b == BRHO ? TM_RHO : TM_ALPHA); }
-};
-
-template <bool ADJ, int PM> struct StrCfg {
-    static constexpr bool PML = PM != PM_NONE, LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
-    // stage boxes 0..2: u (forward) or w (adjoint); 3 lambda, 4 1/mu.  Full
-    // C-PML adjoint blocks form the layer-augmented fields E in place (the
-    // x-differenced ones) and keep the y-differenced ones, which differ inside
-    // the layers, in three extra boxes.
-    static constexpr int NB = 5;
-    static constexpr int NDER = (ADJ && PXY) ? 3 : 0;
-    static constexpr int MV = ADJ ? mv_floats(PM) : 0;  // floats of the memory-variable buffer
-    static constexpr int BLAM = 3, BMU = 4;
-    static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
-    __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : (b == 3 ? TM_LAM : TM_MU); }
-};
-
-// the edge kernel runs PM_X and PM_Y bodies with one shared-memory layout;
-// the interior kernel runs PM_NONE and PM_Z bodies
-static_assert(VelCfg<true, PM_X>::SMEM == VelCfg<true, PM_Y>::SMEM && StrCfg<true, PM_X>::SMEM == StrCfg<true, PM_Y>::SMEM &&
-                  VelCfg<false, PM_X>::SMEM == VelCfg<false, PM_Y>::SMEM &&
-                  StrCfg<false, PM_X>::SMEM == StrCfg<false, PM_Y>::SMEM,
-              "edge bodies share one layout");
-static_assert(VelCfg<true, PM_NONE>::SMEM == VelCfg<true, PM_Z>::SMEM &&
-                  StrCfg<true, PM_NONE>::SMEM == StrCfg<true, PM_Z>::SMEM &&
-                  VelCfg<false, PM_NONE>::SMEM == VelCfg<false, PM_Z>::SMEM &&
-                  StrCfg<false, PM_NONE>::SMEM == StrCfg<false, PM_Z>::SMEM,
-              "interior bodies share one layout");
-// the persistent frame kernels run every frame body with the corner layout
-static_assert(VelCfg<true, PM_FULL>::SMEM >= VelCfg<true, PM_X>::SMEM &&
-                  StrCfg<true, PM_FULL>::SMEM >= StrCfg<true, PM_X>::SMEM &&
-                  VelCfg<false, PM_FULL>::SMEM >= VelCfg<false, PM_X>::SMEM &&
-                  StrCfg<false, PM_FULL>::SMEM >= StrCfg<false, PM_X>::SMEM,
-              "corner layout covers the edge bodies");
-
-__device__ __forceinline__ void locate(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0, int& zc1,
-                                       int& kind) {
-    locate_item(rl, b, tile_x, tile_y, zc0, zc1, kind);
-}
-// the same for a list held inline (the persistent multi-instance kernels)
-__device__ __forceinline__ void locate_inline(const RegionList& rl, int b, int& tile_x, int& tile_y, int& zc0,
-                                              int& zc1, int& kind) {
-    int r = 0;
-    while (r + 1 < rl.n && b >= rl.r[r + 1].bstart) ++r;
-    const Region& R = rl.r[r];
-    const int lb = b - R.bstart;
-    const int ntx = R.tx1 - R.tx0, nt = ntx * (R.ty1 - R.ty0);
-    const int t = lb % nt, ch = lb / nt;
-    tile_x = R.tx0 + t % ntx;
-    tile_y = R.ty0 + t / ntx;
-    zc0 = R.za + ch * R.zc;
-    zc1 = min(zc0 + R.zc, R.zb);
-    kind = R.kind;
-}
-
-// differences on a box (own index o) and on a register queue
-__device__ __forceinline__ float dpx(const float* v, int o) {
-    return PACT_C1 * (v[o + 1] - v[o]) - PACT_C2 * (v[o + 2] - v[o - 1]);
-}
-__device__ __forceinline__ float dmx(const float* v, int o) {
-    return PACT_C1 * (v[o] - v[o - 1]) - PACT_C2 * (v[o + 1] - v[o - 2]);
-}
-__device__ __forceinline__ float dpy(const float* v, int o) {
-    return PACT_C1 * (v[o + BW] - v[o]) - PACT_C2 * (v[o + 2 * BW] - v[o - BW]);
-}
-__device__ __forceinline__ float dmy(const float* v, int o) {
-    return PACT_C1 * (v[o] - v[o - BW]) - PACT_C2 * (v[o + BW] - v[o - 2 * BW]);
-}
-// queue q[0..3] holds planes (z-2..z+1) for a half->integer difference or
-// (z-1..z+2) for an integer->half difference; both reduce to this form
-__device__ __forceinline__ float dq(const float* q) {
-    return PACT_C1 * (q[2] - q[1]) - PACT_C2 * (q[3] - q[0]);
-}
-__device__ __forceinline__ void push(float* q, float h) {
-    q[0] = q[1];
-    q[1] = q[2];
-    q[2] = q[3];
-    q[3] = h;
-}
-
-__device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
-
-// The TMA-staged kernels read r = 1/mu (+inf at fluid nodes).
-// mu = 1/r (0 at fluid nodes); the harmonic mean of four mu is 4 / (r1+r2+r3+r4),
-// which is 0 as soon as one node is fluid (the sum is +inf).
-__device__ __forceinline__ float mu_of(float r) { return frcp(r); }
-__device__ __forceinline__ float harm_inv(float a, float b, float c, float d) {
-    return __fdividef(4.0f, a + b + c + d);
-}
-
-// The cross-shaped region the x and y differences read: the x band (rows
-// OY..OY+TY-1, columns OX-2..OX+TX+1) and four y rows (OY-2, OY-1, OY+TY,
-// OY+TY+1; columns OX..OX+TX-1): 416 positions, at most two per thread.  The
-// positions a thread owns are the same on every plane, so their box index,
-// clamped +x / +y neighbour offsets and band flags are computed once.
-constexpr int NCROSS = (TX + 4) * TY + 4 * TX;
-constexpr unsigned char CP_EXISTS = 1, CP_IN = 2, CP_XB = 4, CP_YB = 8;
-struct CrossPos {
-    int q[2];
-    short dx[2], dy[2];
-    unsigned char f[2];
-};
-
-__device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0, int nx, int ny) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * NT;
-        c.q[k] = 0;
-        c.dx[k] = c.dy[k] = 0;
-        c.f[k] = 0;
-        if (i >= NCROSS) continue;
-        int bx, by;
-        bool inx, iny;
-        if (i < (TX + 4) * TY) {
-            bx = OX - 2 + i % (TX + 4);
-            by = OY + i / (TX + 4);
-            inx = true;
-            iny = bx >= OX && bx < OX + TX;
-        } else {
-            const int j = i - (TX + 4) * TY, r = j / TX;
-            bx = OX + j % TX;
-            by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
-            inx = false;
-            iny = true;
-        }
-        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        c.q[k] = by * BW + bx;
-        c.dx[k] = (gx + 1 < nx) ? 1 : 0;
-        c.dy[k] = (gy + 1 < ny) ? BW : 0;
-        c.f[k] = CP_EXISTS | (in ? CP_IN : 0) | (inx ? CP_XB : 0) | (iny ? CP_YB : 0);
-    }
-}
-
-// C-PML data of the cross positions: per box column / row the layer
-// coefficients (a and chi on the integer and half lattice) and, per position,
-// the slab index base of the x slab (x-band positions) and y slab (y-band
-// positions), -1 off the layer.
-struct CrossPml {
-    int sx[2], sy[2];
-};
-
-template <bool LX, bool LY>
-__device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy, const CrossPos& cp, int tid,
-                                               int x0, int y0, const StepParams& p) {
-    const int W = 2 * p.P + 1;
-    for (int i = tid; i < BW + BH; i += NT) {
-        float* t = i < BW ? cx + 4 * i : cy + 4 * (i - BW);
-        const int axis = i < BW ? 0 : 1;
-        const int g = i < BW ? x0 - 4 + i : y0 - 2 + (i - BW);
-        const int n = axis == 0 ? p.nx : p.ny;
-        const bool in = g >= 0 && g < n && slab_local(g, n, p.P) >= 0;
-        t[0] = in ? __ldg(p.tab[axis][0][0] + g) : 0.f;  // a, integer lattice
-        t[1] = in ? __ldg(p.tab[axis][0][2] + g) : 0.f;  // chi, integer lattice
-        t[2] = in ? __ldg(p.tab[axis][1][0] + g) : 0.f;  // a, half lattice
-        t[3] = in ? __ldg(p.tab[axis][1][2] + g) : 0.f;  // chi, half lattice
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        c.sx[k] = c.sy[k] = -1;
-        const unsigned char f = cp.f[k];
-        if (!(f & CP_IN)) continue;
-        const int bx = cp.q[k] % BW, by = cp.q[k] / BW;
-        const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
-        const int lx = slab_local(gx, p.nx, p.P), ly = slab_local(gy, p.ny, p.P);
-        if (LX && (f & CP_XB) && lx >= 0) c.sx[k] = gy * W + lx;
-        if (LY && (f & CP_YB) && ly >= 0) c.sy[k] = ly * p.nx + gx;
-    }
-}
-
-// Shared tables of the layer coefficients of the cross positions (per box
-// column: 4 floats, then per box row: 4 floats).  One allocation per kernel,
-// shared by all its C-PML bodies (a block runs one body at a time), so that a
-// kernel that carries both edge bodies pays for the tables once.
-__device__ __forceinline__ float* frame_coef_tables() {
-    __shared__ float t[4 * BW + 4 * BH];
-    return t;
-}
-
-__device__ __forceinline__ bool in_slab_plane(int k, int n, int P) {
-    return P > 0 && (k < P || k >= n - P - 1);
-}
-
-// C-PML table entry, runtime axis: which = 0 (a), 1 (b), 2 (chi)
-__device__ __forceinline__ float tabv(const StepParams& p, int axis, int half, int which, int k) {
-    return __ldg(p.tab[axis][half][which] + k);
-}
-
-// position (axis coordinate k) inside the slab of `axis`? returns slab index or -1
-__device__ __forceinline__ long slab_at(const StepParams& p, int axis, int gx, int gy, int gz) {
-    const int k = axis == 0 ? gx : (axis == 1 ? gy : gz);
-    const int n = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-    const int l = slab_local(k, n, p.P);
-    if (l < 0) return -1;
-    return (long)slab_index(axis, gx, gy, gz, l, p);
-}
-
-struct Ring {
-    float* base;
-    int NB;
-    int pfirst;
-    __device__ __forceinline__ float* stage(int plane) const {
-        return base + (size_t)(((plane - pfirst) & (D - 1)) * NB) * BOXS;
-    }
-};
-
-// bounded drain of loads still in flight after a failed wait
-__device__ __forceinline__ void drain(uint64_t* bar, int pfrom, int pto, int pfirst) {
-    for (int pl = pfrom; pl <= pto; ++pl) {
-        const int k = pl - pfirst;
-        mbar_wait_bounded(&bar[k & (D - 1)], (k / D) & 1);
-    }
-}
-
-}  // namespace tiled
-
-using namespace tiled;
-
-// per-thread C-PML constants of the own column along x and y
-struct PmlXY {
-    int lx, ly;          // slab coordinate along x / y, -1 outside the layer
-    float c[2][2][3];    // [axis x, y][lattice integer, half][a, b, chi]
-};
-
-template <bool LX, bool LY>
-__device__ __forceinline__ void pml_xy_init(PmlXY& q, const StepParams& p, int x, int y, bool own) {
-    q.lx = (LX && own) ? slab_local(x, p.nx, p.P) : -1;
-    q.ly = (LY && own) ? slab_local(y, p.ny, p.P) : -1;
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-        for (int w = 0; w < 3; ++w) {
-            q.c[0][hh][w] = (LX && q.lx >= 0) ? tabv(p, 0, hh, w, x) : 0.f;
-            q.c[1][hh][w] = (LY && q.ly >= 0) ? tabv(p, 1, hh, w, y) : 0.f;
-        }
-}
-
-// C-PML coefficients of plane z along the z axis
-struct PmlZ {
-    int lz;
-    float c[2][3];
-};
-
-__device__ __forceinline__ void pml_z_init(PmlZ& q, const StepParams& p, int z) {
-    q.lz = (z >= 0 && z < p.nz) ? slab_local(z, p.nz, p.P) : -1;
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-        for (int w = 0; w < 3; ++w) q.c[hh][w] = q.lz >= 0 ? tabv(p, 2, hh, w, z) : 0.f;
-}
-
-// slab index of the own point (x, y, z) on the slab of `axis`
-__device__ __forceinline__ unsigned own_slab(int axis, const PmlXY& q, int lz, int x, int y, int z,
-                                             const StepParams& p) {
-    const unsigned W = 2 * p.P + 1;
-    if (axis == 0) return ((unsigned)z * p.ny + y) * W + q.lx;
-    if (axis == 1) return ((unsigned)z * W + q.ly) * p.nx + x;
-    return ((unsigned)lz * p.ny + y) * p.nx + x;
-}
-
-// own point on the layer of axis j?  Layers without code in the body (LX or
-// LY false) are absent, which the compiler sees for an unrolled j.
-template <bool LX, bool LY>
-__device__ __forceinline__ bool in_axis(int j, const PmlXY& q, int lz) {
-    return j == 2 ? lz >= 0 : (j == 0 ? (LX && q.lx >= 0) : (LY && q.ly >= 0));
-}
-
-__device__ __forceinline__ float coef(int j, int hh, int w, const PmlXY& q, const PmlZ& qz) {
-    return j < 2 ? q.c[j][hh][w] : qz.c[hh][w];
-}
+#include "tiled_common.cuh"
 
 // ===========================================================================
 // velocity family
@@ -1367,19 +1050,90 @@ long long region_points(const RegionList& rl, const StepParams& p) {
 
 }  // namespace
 
+// One half step of a medium-adaptive step: the frame items (edge and corner
+// lists, elastic and fluid) on the frame streams between a fork and a join,
+// the interior items (elastic, fluid z-slab, acoustic) on the main stream.
+template <bool STR, bool ADJ>
+static int launch_mixed_half(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
+                             const MixedPlan& mp) {
+    // the two-pass plan of the grid (cached) raises the dynamic shared-memory
+    // limit of the elastic kernels launched below
+    plan_for((STR ? 2 : 0) + (ADJ ? 1 : 0), p, STEP_TWO_PASS);
+    const dim3 blk(TX, TY, 1);
+    const int* nb = mp.blocks;
+    const bool frame = nb[MX_EDGE_EL] || nb[MX_EDGE_FL] || nb[MX_CORNER_EL] || nb[MX_CORNER_FL];
+    const bool inner = nb[MX_INT_EL] || nb[MX_INT_AC] || nb[MX_INT_FZ];
+    const bool split = ss.aux && frame && inner;
+    cudaStream_t se = ss.st, sc = ss.st;
+    const bool split2 = split && ss.aux2;
+    if (split) {
+        cudaEventRecord(ss.fork, ss.st);
+        cudaStreamWaitEvent(ss.aux, ss.fork, 0);
+        se = sc = ss.aux;
+        if (split2) {
+            cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+            sc = ss.aux2;
+        }
+    }
+    int n = 0;
+    if (nb[MX_CORNER_EL]) {
+        if (STR)
+            k_str_tiled<ADJ, PM_FULL><<<nb[MX_CORNER_EL], blk, StrCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, mp.list[MX_CORNER_EL], err);
+        else
+            k_vel_tiled<ADJ, PM_FULL><<<nb[MX_CORNER_EL], blk, VelCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, mp.list[MX_CORNER_EL], err);
+        ++n;
+    }
+    if (nb[MX_CORNER_FL]) {
+        launch_fluid(STR, ADJ, PM_FULL, p, tm, mp.list[MX_CORNER_FL], nb[MX_CORNER_FL], err, sc);
+        ++n;
+    }
+    if (nb[MX_EDGE_EL]) {
+        if (STR) k_str_tiled<ADJ, PM_X><<<nb[MX_EDGE_EL], blk, StrCfg<ADJ, PM_X>::SMEM, se>>>(p, tm, mp.list[MX_EDGE_EL], err);
+        else k_vel_tiled<ADJ, PM_X><<<nb[MX_EDGE_EL], blk, VelCfg<ADJ, PM_X>::SMEM, se>>>(p, tm, mp.list[MX_EDGE_EL], err);
+        ++n;
+    }
+    if (nb[MX_EDGE_FL]) {
+        launch_fluid(STR, ADJ, PM_X, p, tm, mp.list[MX_EDGE_FL], nb[MX_EDGE_FL], err, se);
+        ++n;
+    }
+    if (nb[MX_INT_EL]) {
+        if (STR)
+            k_str_tiled<ADJ, PM_NONE><<<nb[MX_INT_EL], blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, mp.list[MX_INT_EL], err);
+        else
+            k_vel_tiled<ADJ, PM_NONE><<<nb[MX_INT_EL], blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, mp.list[MX_INT_EL], err);
+        ++n;
+    }
+    if (nb[MX_INT_FZ]) {
+        launch_fluid(STR, ADJ, PM_Z, p, tm, mp.list[MX_INT_FZ], nb[MX_INT_FZ], err, ss.st);
+        ++n;
+    }
+    if (nb[MX_INT_AC]) {
+        launch_acoustic(STR, ADJ, p, tm, mp.list[MX_INT_AC], nb[MX_INT_AC], err, ss.st);
+        ++n;
+    }
+    if (split) {
+        cudaEventRecord(ss.join, ss.aux);
+        cudaStreamWaitEvent(ss.st, ss.join, 0);
+        if (split2) {
+            cudaEventRecord(ss.join2, ss.aux2);
+            cudaStreamWaitEvent(ss.st, ss.join2, 0);
+        }
+    }
+    return n;
+}
+
 // The frame launch goes to `aux` (when given) between a fork and a join
 // event, so that it overlaps the interior launch on `st`.
 template <bool ADJ>
 static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode,
                             const MixedPlan* mp) {
-    const bool mixed = mode == STEP_MIXED && mp;
-    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, mixed ? STEP_TWO_PASS : mode);
-    const RegionList& inner = mixed ? mp->elastic : L.inner;
-    const int inner_blocks = mixed ? mp->elastic_blocks : L.inner_blocks;
-    const int ac_blocks = mixed ? mp->acoustic_blocks : 0;
+    if (mode == STEP_MIXED && mp) return launch_mixed_half<false, ADJ>(p, tm, err, ss, *mp);
+    const LaunchPlan L = plan_for(ADJ ? 1 : 0, p, mode);
+    const RegionList& inner = L.inner;
+    const int inner_blocks = L.inner_blocks;
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
-    const bool split = ss.aux && nframe && (inner_blocks || ac_blocks);
+    const bool split = ss.aux && nframe && inner_blocks;
     cudaStream_t so = ss.st, sc = ss.st;
     const bool split2 = split && ss.aux2 && L.corner_blocks && L.edge_blocks;
     if (split) {
@@ -1397,7 +1151,6 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
         k_vel_tiled<ADJ, PM_X><<<L.edge_blocks, blk, VelCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
     if (inner_blocks)
         k_vel_tiled<ADJ, PM_NONE><<<inner_blocks, blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, inner, err);
-    if (ac_blocks) launch_acoustic(false, ADJ, p, tm, mp->acoustic, ac_blocks, err, ss.st);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
@@ -1406,20 +1159,19 @@ static int launch_vel_impl(const StepParams& p, const TmaSet& tm, int* err, cons
             cudaStreamWaitEvent(ss.st, ss.join2, 0);
         }
     }
-    return nframe + (inner_blocks > 0) + (ac_blocks > 0);
+    return nframe + (inner_blocks > 0);
 }
 
 template <bool ADJ>
 static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss, int mode,
                             const MixedPlan* mp) {
-    const bool mixed = mode == STEP_MIXED && mp;
-    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, mixed ? STEP_TWO_PASS : mode);
-    const RegionList& inner = mixed ? mp->elastic : L.inner;
-    const int inner_blocks = mixed ? mp->elastic_blocks : L.inner_blocks;
-    const int ac_blocks = mixed ? mp->acoustic_blocks : 0;
+    if (mode == STEP_MIXED && mp) return launch_mixed_half<true, ADJ>(p, tm, err, ss, *mp);
+    const LaunchPlan L = plan_for(ADJ ? 3 : 2, p, mode);
+    const RegionList& inner = L.inner;
+    const int inner_blocks = L.inner_blocks;
     const dim3 blk(TX, TY, 1);
     const int nframe = (L.edge_blocks > 0) + (L.corner_blocks > 0);
-    const bool split = ss.aux && nframe && (inner_blocks || ac_blocks);
+    const bool split = ss.aux && nframe && inner_blocks;
     cudaStream_t so = ss.st, sc = ss.st;
     const bool split2 = split && ss.aux2 && L.corner_blocks && L.edge_blocks;
     if (split) {
@@ -1437,7 +1189,6 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
         k_str_tiled<ADJ, PM_X><<<L.edge_blocks, blk, StrCfg<ADJ, PM_X>::SMEM, so>>>(p, tm, L.edge, err);
     if (inner_blocks)
         k_str_tiled<ADJ, PM_NONE><<<inner_blocks, blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, inner, err);
-    if (ac_blocks) launch_acoustic(true, ADJ, p, tm, mp->acoustic, ac_blocks, err, ss.st);
     if (split) {
         cudaEventRecord(ss.join, ss.aux);
         cudaStreamWaitEvent(ss.st, ss.join, 0);
@@ -1446,7 +1197,7 @@ static int launch_str_impl(const StepParams& p, const TmaSet& tm, int* err, cons
             cudaStreamWaitEvent(ss.st, ss.join2, 0);
         }
     }
-    return nframe + (inner_blocks > 0) + (ac_blocks > 0);
+    return nframe + (inner_blocks > 0);
 }
 
 // ---- multi-instance (persistent) launches --------------------------------
@@ -1547,91 +1298,101 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
     free_mixed_plan(mp);
     int txlo, txhi, tylo, tyhi;
     if (p.P <= 0 || !interior_tiles(p, txlo, txhi, tylo, tyhi)) return 0;
-    const int ntx = txhi + 1 - txlo, nty = tyhi + 1 - tylo, ntiles = ntx * nty;
+    const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY, ntiles = ntx * nty;
     // the no-layer planes of the interior tiles (as in make_regions)
     const int za = std::min(p.P + 2, p.nz), zb = std::max(za, p.nz - p.P - 3);
-    if (zb <= za) return 0;
     unsigned char* d_flag = nullptr;
     const size_t nflag = (size_t)p.nz * ntiles;
     if (cudaMalloc(&d_flag, nflag) != cudaSuccess) return 1;
-    k_tile_solid<<<dim3(ntiles, p.nz), 256, 0, st>>>(mu, p.nx, p.ny, txlo, tylo, ntx, nty, d_flag);
+    k_tile_solid<<<dim3(ntiles, p.nz), 256, 0, st>>>(mu, p.nx, p.ny, 0, 0, ntx, nty, d_flag);
     std::vector<unsigned char> flag(nflag);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, nflag, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_flag);
     if (e != cudaSuccess) return 1;
-    // Segments of each tile column over [za, zb): fluid where no plane of
-    // z-3 .. z+3 has a solid node in the tile's reach.  The work items are cut
-    // at a common grid of z chunks and ordered chunk by chunk, so that the
-    // blocks resident at one time work on the same planes of neighbouring
-    // tiles and find each other's halo rows in L2.
-    // Two lists, each ordered by z chunk so that the blocks resident at one
-    // time work on the same planes of neighbouring tiles: the elastic items
-    // (the no-layer segments with solid in reach, and the z-slab planes of
-    // the interior tiles) for the elastic interior kernels, and the fluid
-    // segments for the acoustic kernels (which keep their own, higher
-    // occupancy).
-    std::vector<Region> el, ac;
-    int el_blocks = 0, ac_blocks = 0;
-    long long el_pts = 0, ac_pts = 0;
-    constexpr int kChunk = 48;  // planes per work item at most
-    auto add = [&](int tx0, int tx1, int ty0, int ty1, int a, int b, int kind) {
-        if (b <= a) return;
-        const bool fluid = kind == PM_AC;
-        std::vector<Region>& v = fluid ? ac : el;
-        int& blocks = fluid ? ac_blocks : el_blocks;
-        v.push_back(Region{tx0, tx1, ty0, ty1, a, b, b - a, blocks, kind});
-        const long long tiles = (long long)(tx1 - tx0) * (ty1 - ty0);
-        blocks += (int)tiles;
-        (fluid ? ac_pts : el_pts) += tiles * TX * TY * (b - a);
-    };
-    std::vector<unsigned char> solid((size_t)p.nz * ntiles);
+    // solid[z][t]: a solid node within planes z-3 .. z+3 of tile t's reach
+    std::vector<unsigned char> solid(nflag);
     for (int t = 0; t < ntiles; ++t)
         for (int z = 0; z < p.nz; ++z) {
             unsigned char any = 0;
             for (int k = std::max(0, z - 3); k <= std::min(p.nz - 1, z + 3); ++k) any |= flag[(size_t)k * ntiles + t];
             solid[(size_t)z * ntiles + t] = any;
         }
-    // the z-slab planes of the interior tiles (z-layer code) below and above
-    add(txlo, txhi + 1, tylo, tyhi + 1, 0, za, PM_Z);
-    const int nchunk = (zb - za + kChunk - 1) / kChunk;
-    const int zc = (zb - za + nchunk - 1) / nchunk;
-    for (int c0 = za; c0 < zb; c0 += zc) {
-        const int c1 = std::min(zb, c0 + zc);
+    // Segments of every tile over common z chunks (the z-slab planes below
+    // and above the interior planes, then chunks of the interior planes),
+    // chunk by chunk, so that the blocks resident at one time work on the
+    // same planes of neighbouring tiles and find each other's halos in L2.
+    std::vector<Region> lists[MX_N];
+    long long pts[MX_N] = {};
+    int blocks[MX_N] = {};
+    auto add = [&](int li, int tx, int ty, int a, int b, int kind) {
+        lists[li].push_back(Region{tx, tx + 1, ty, ty + 1, a, b, b - a, blocks[li], kind});
+        blocks[li] += 1;
+        const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);
+        pts[li] += (long long)ex * ey * (b - a);
+    };
+    constexpr int kChunk = 48;  // planes per work item at most
+    std::vector<int> cuts{0};
+    if (za > 0) cuts.push_back(za);
+    if (zb > za) {
+        const int nchunk = (zb - za + kChunk - 1) / kChunk;
+        const int zc = (zb - za + nchunk - 1) / nchunk;
+        for (int c = za + zc; c < zb; c += zc) cuts.push_back(c);
+        cuts.push_back(zb);
+    }
+    if (cuts.back() != p.nz) cuts.push_back(p.nz);
+    for (size_t ci = 0; ci + 1 < cuts.size(); ++ci) {
+        const int c0 = cuts[ci], c1 = cuts[ci + 1];
+        const bool zslab = c0 < za || c0 >= zb;
         for (int t = 0; t < ntiles; ++t) {
-            const int tx = txlo + t % ntx, ty = tylo + t / ntx;
+            const int tx = t % ntx, ty = t / ntx;
+            const bool inx = tx >= txlo && tx <= txhi, iny = ty >= tylo && ty <= tyhi;
+            int kind, li_el, li_fl;
+            if (inx && iny) {
+                kind = zslab ? PM_Z : PM_NONE;
+                li_el = MX_INT_EL;
+                li_fl = zslab ? MX_INT_FZ : MX_INT_AC;
+            } else if (inx || iny) {
+                kind = iny ? PM_X : PM_Y;
+                li_el = MX_EDGE_EL;
+                li_fl = MX_EDGE_FL;
+            } else {
+                kind = PM_FULL;
+                li_el = MX_CORNER_EL;
+                li_fl = MX_CORNER_FL;
+            }
             int a = c0;
             while (a < c1) {
                 const unsigned char f = solid[(size_t)a * ntiles + t];
                 int b = a + 1;
                 while (b < c1 && solid[(size_t)b * ntiles + t] == f) ++b;
-                add(tx, tx + 1, ty, ty + 1, a, b, f ? PM_NONE : PM_AC);
+                add(f ? li_el : li_fl, tx, ty, a, b, kind);
                 a = b;
             }
         }
     }
-    add(txlo, txhi + 1, tylo, tyhi + 1, zb, p.nz, PM_Z);
-    const size_t n = el.size() + ac.size();
+    size_t n = 0;
+    for (int l = 0; l < MX_N; ++l) n += lists[l].size();
     if (cudaMalloc(&mp->mem, n * sizeof(Region)) != cudaSuccess) return 1;
-    std::vector<Region> all(el);
-    all.insert(all.end(), ac.begin(), ac.end());
+    std::vector<Region> all;
+    all.reserve(n);
+    for (int l = 0; l < MX_N; ++l) all.insert(all.end(), lists[l].begin(), lists[l].end());
     e = cudaMemcpyAsync(mp->mem, all.data(), n * sizeof(Region), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         free_mixed_plan(mp);
         return 1;
     }
-    mp->elastic.n = 0;
-    mp->elastic.dev = el.empty() ? nullptr : mp->mem;
-    mp->elastic.dn = (int)el.size();
-    mp->acoustic.n = 0;
-    mp->acoustic.dev = ac.empty() ? nullptr : mp->mem + el.size();
-    mp->acoustic.dn = (int)ac.size();
-    mp->elastic_blocks = el_blocks;
-    mp->acoustic_blocks = ac_blocks;
-    mp->elastic_points = el_pts;
-    mp->acoustic_points = ac_pts;
+    size_t off = 0;
+    for (int l = 0; l < MX_N; ++l) {
+        mp->list[l].n = 0;
+        mp->list[l].dev = lists[l].empty() ? nullptr : mp->mem + off;
+        mp->list[l].dn = (int)lists[l].size();
+        mp->blocks[l] = blocks[l];
+        mp->points[l] = pts[l];
+        off += lists[l].size();
+    }
     return 0;
 }
 

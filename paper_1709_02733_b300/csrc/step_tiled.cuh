@@ -110,33 +110,48 @@ struct SplitStreams {
 //                  elastic ones, from a per-medium plan (MixedPlan).
 enum { STEP_TWO_PASS = 0, STEP_FUSED = 1, STEP_ACOUSTIC = 2, STEP_MIXED = 3 };
 
-// Interior work lists of a medium (STEP_MIXED), in device memory.  An
-// interior tile and plane is fluid if mu = 0 at every integer node of its
-// reach (x0-3 .. x0+TX+2, y0-3 .. y0+TY+2, z-3 .. z+3): there every stress
-// and velocity the elastic update reads has sigma^11 = sigma^22 = sigma^33
-// and zero shear, so the acoustic update is the same operator.
+// Work lists of a medium (STEP_MIXED), in device memory.  A tile and plane
+// is fluid if mu = 0 at every integer node of its reach (x0-3 .. x0+TX+2,
+// y0-3 .. y0+TY+2, z-3 .. z+3): there every stress and velocity the elastic
+// update reads has sigma^11 = sigma^22 = sigma^33 and zero shear, so the
+// acoustic update (no layer) or the fluid C-PML update (step_fluid.cu)
+// computes the same operator.  Every list is one tile per region, ordered by
+// z chunk.
+enum {
+    MX_INT_EL = 0,   // interior tiles with solid in reach: no-layer and z-slab planes (elastic)
+    MX_INT_AC,       // interior tiles, fluid, no-layer planes (acoustic kernels)
+    MX_INT_FZ,       // interior tiles, fluid, z-slab planes (fluid C-PML kernels)
+    MX_EDGE_EL,      // frame edges (x or y layer) with solid in reach (elastic)
+    MX_EDGE_FL,      // frame edges, fluid
+    MX_CORNER_EL,    // frame corners (x and y layers), solid in reach (elastic)
+    MX_CORNER_FL,    // frame corners, fluid
+    MX_N
+};
 struct MixedPlan {
-    RegionList elastic;      // elastic interior items (no-layer segments and the z-slab planes)
-    int elastic_blocks = 0;
-    RegionList acoustic;     // fluid no-layer segments
-    int acoustic_blocks = 0;
-    long long elastic_points = 0, acoustic_points = 0;
-    Region* mem = nullptr;   // device allocation behind both lists
+    RegionList list[MX_N];
+    int blocks[MX_N] = {};
+    long long points[MX_N] = {};
+    Region* mem = nullptr;   // device allocation behind the lists
 };
 // Build the plan of the grid of p for the medium's mu (device array);
-// returns 0 on success (mp->acoustic_points may be 0), nonzero on a CUDA
-// error.  Synchronises st.
+// returns 0 on success (with no fluid item every list but the elastic ones is
+// empty), nonzero on a CUDA error.  Synchronises st.
 int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, MixedPlan* mp);
 void free_mixed_plan(MixedPlan* mp);
 
 // Both return the number of kernels launched.  With mode STEP_MIXED, mp
-// gives the interior work lists: the elastic items replace the interior
-// launch and the fluid items run the acoustic kernels after it on the main
-// stream, beside the frame launches.
+// gives the work lists: on the main stream the elastic interior items, the
+// fluid z-slab items and the acoustic items; on the frame streams the elastic
+// and fluid edge and corner items.
 int launch_vel_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
                      int mode = STEP_TWO_PASS, const MixedPlan* mp = nullptr);
 int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, const SplitStreams& ss,
                      int mode = STEP_TWO_PASS, const MixedPlan* mp = nullptr);
+
+// Fluid C-PML kernels (step_fluid.cu): items of kind pm (PM_Z items with
+// pm = 2, edge items (PM_X or PM_Y) with pm = 3, corner items with pm = 1).
+void launch_fluid(bool str, bool adj, int pm, const StepParams& p, const TmaSet& tm, const RegionList& rl, int blocks,
+                  int* err, cudaStream_t st);
 
 // Acoustic interior kernels (step_acoustic.cu): the elastic tensor maps (the
 // velocity kernel reads sigma^11, rho, alpha; the stress kernel u^1..u^3).

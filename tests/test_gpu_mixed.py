@@ -51,14 +51,15 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def _inclusion_case(shape=(60, 40, 104), npml=4, seed=31, L=15):
+def _inclusion_case(shape=(60, 40, 104), npml=4, seed=31, L=15, cx=0.8, rx=12.0):
     """Water with a solid ellipsoid (absorbing, +-5 % noise) off-centre in x:
-    the interior tiles on one side see only fluid, those on the other side
-    the solid."""
+    the tiles on one side see only fluid, those on the other side the solid
+    (with cx near 1 the solid reaches into the x layer, so that elastic and
+    fluid C-PML work items neighbour each other)."""
     nz, ny, nx = shape
     rng = np.random.default_rng(seed)
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    inside = ((x - 0.8 * nx) / 12.0) ** 2 + ((y - ny / 2) / 9.0) ** 2 + ((z - nz / 2) / 12.0) ** 2 <= 1.0
+    inside = ((x - cx * nx) / rx) ** 2 + ((y - ny / 2) / 9.0) ** 2 + ((z - nz / 2) / 12.0) ** 2 <= 1.0
     cp = np.where(inside, 2900.0, 1480.0) * (1 + 0.05 * inside * rng.uniform(-1, 1, shape))
     cs = np.where(inside, 1400.0, 0.0)
     rho = np.where(inside, 1850.0, 1000.0) * (1 + 0.05 * inside * rng.uniform(-1, 1, shape))
@@ -85,8 +86,9 @@ def _paths(d, med, monkeypatch):
     return g_m, g_e, n_ac
 
 
-def test_mixed_against_oracle_and_elastic_path(monkeypatch):
-    d, med, p0, rec = _inclusion_case()
+@pytest.mark.parametrize("cx,rx", [(0.8, 12.0), (0.95, 10.0)])
+def test_mixed_against_oracle_and_elastic_path(cx, rx, monkeypatch):
+    d, med, p0, rec = _inclusion_case(cx=cx, rx=rx)
     g_m, g_e, n_ac = _paths(d, med, monkeypatch)
     # fluid and solid interior work items both present
     assert 0 < n_ac < d.N
