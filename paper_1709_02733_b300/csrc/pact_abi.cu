@@ -106,8 +106,8 @@ struct pact_grid {
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
     const float* sv_in = nullptr;
     float* sv_out = nullptr;
-    RegionList sv_inner{}, sv_edge{}, sv_corner{};
-    int sv_ninner = 0, sv_nedge = 0, sv_ncorner = 0;
+    RegionList sv_inner{}, sv_edge{}, sv_corner{}, sv_ac{}, sv_fl{};
+    int sv_ninner = 0, sv_nedge = 0, sv_ncorner = 0, sv_nac = 0, sv_nfl = 0;
     std::string err;
 };
 
@@ -863,7 +863,27 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
         if (nsteps == 0) launch_readout(out, p, h->stream);
     }
-    plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_edge, h->sv_nedge, h->sv_corner, h->sv_ncorner);
+    if (h->mixed) {
+        // a medium-adaptive handle serves its per-medium work lists
+        const MixedPlan& mp = h->mixed_plan;
+        h->sv_inner = mp.list[MX_INT_EL];
+        h->sv_ninner = mp.blocks[MX_INT_EL];
+        h->sv_edge = mp.list[MX_EDGE_EL];
+        h->sv_nedge = mp.blocks[MX_EDGE_EL];
+        h->sv_corner = mp.list[MX_CORNER_EL];
+        h->sv_ncorner = mp.blocks[MX_CORNER_EL];
+        h->sv_ac = mp.list[MX_INT_AC];
+        h->sv_nac = mp.blocks[MX_INT_AC];
+        h->sv_fl = mp.fluid_frame;
+        h->sv_nfl = mp.fluid_frame_blocks;
+    } else {
+        plan_instance_regions(p, 64, h->sv_inner, h->sv_ninner, h->sv_edge, h->sv_nedge, h->sv_corner,
+                              h->sv_ncorner);
+        h->sv_ac = RegionList{};
+        h->sv_ac.n = 0;
+        h->sv_fl = h->sv_ac;
+        h->sv_nac = h->sv_nfl = 0;
+    }
     h->sv_active = nsteps > 0;
     CK(h, cudaGetLastError());
     return PACT_OK;
@@ -876,7 +896,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
     if (!T) T = new (std::nothrow) MultiTable();
     if (!T) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
     int dev = -1, ni = 0;
-    T->pre_inner[0] = T->pre_edge[0] = T->pre_corner[0] = 0;
+    T->pre_inner[0] = T->pre_edge[0] = T->pre_corner[0] = T->pre_ac[0] = T->pre_fl[0] = 0;
     // forward instances first, then adjoint ones (each persistent kernel
     // serves one direction)
     for (int pass = 0; pass < 2; ++pass) {
@@ -892,6 +912,8 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             e.inner = h->sv_inner;
             e.edge = h->sv_edge;
             e.corner = h->sv_corner;
+            e.ac = h->sv_ac;
+            e.fl = h->sv_fl;
             e.rec = make_rec(h);
             e.src = h->sv_adj ? h->sv_in : nullptr;
             e.dst = h->sv_adj ? nullptr : h->sv_out;
@@ -902,6 +924,8 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             T->pre_inner[ni + 1] = T->pre_inner[ni] + h->sv_ninner;
             T->pre_edge[ni + 1] = T->pre_edge[ni] + h->sv_nedge;
             T->pre_corner[ni + 1] = T->pre_corner[ni] + h->sv_ncorner;
+            T->pre_ac[ni + 1] = T->pre_ac[ni] + h->sv_nac;
+            T->pre_fl[ni + 1] = T->pre_fl[ni] + h->sv_nfl;
             ++ni;
         }
         if (pass == 0) T->n_fwd = ni;

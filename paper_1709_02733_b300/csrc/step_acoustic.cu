@@ -34,6 +34,19 @@ __global__ void __launch_bounds__(NT) k_ac_str(StepParams p, const __grid_consta
     ac_str_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
+// Persistent multi-instance kernel over the fluid no-layer items of the
+// medium-adaptive instances in a serving table (ADJ: the direction).
+template <bool STR, bool ADJ>
+__global__ void __launch_bounds__(NT) k_multi_ac(const MultiTable* __restrict__ T, int* err, int* next) {
+    extern __shared__ __align__(128) float sm[];
+    multi_loop<ADJ, ML_AC>(T, err, next, sm,
+                           [](const StepParams& sp, const CUtensorMap* maps, int, int tile_x, int tile_y, int zc0,
+                              int zc1, int* e, float* smem) {
+                               return STR ? ac_str_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                          : ac_vel_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                           });
+}
+
 // any mu > 0?  (out[0] |= 1)
 __global__ void k_any_shear(const float* __restrict__ mu, size_t n, unsigned int* out) {
     bool any = false;
@@ -67,4 +80,30 @@ void launch_acoustic(bool str, bool adj, const StepParams& p, const TmaSet& tm, 
 void launch_any_shear(const float* mu, size_t n, unsigned int* out, cudaStream_t st) {
     const size_t b = std::min<size_t>((n + 255) / 256, 148 * 8);
     k_any_shear<<<(unsigned)std::max<size_t>(b, 1), 256, 0, st>>>(mu, n, out);
+}
+
+template <bool STR, bool ADJ>
+static int multi_ac_grid() {
+    static int grid[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!grid[dev]) {
+        int sms = 148, per_sm = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_ac<STR, ADJ>, NT, SMEM);
+        grid[dev] = sms * std::max(1, per_sm);
+    }
+    return grid[dev];
+}
+
+void launch_multi_ac(bool str, bool adj, const MultiTable* dT, int* err, int* next, cudaStream_t st) {
+    const dim3 blk(TX, TY, 1);
+    if (str) {
+        if (adj) k_multi_ac<true, true><<<multi_ac_grid<true, true>(), blk, SMEM, st>>>(dT, err, next);
+        else k_multi_ac<true, false><<<multi_ac_grid<true, false>(), blk, SMEM, st>>>(dT, err, next);
+    } else {
+        if (adj) k_multi_ac<false, true><<<multi_ac_grid<false, true>(), blk, SMEM, st>>>(dT, err, next);
+        else k_multi_ac<false, false><<<multi_ac_grid<false, false>(), blk, SMEM, st>>>(dT, err, next);
+    }
 }

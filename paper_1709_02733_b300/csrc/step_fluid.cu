@@ -58,6 +58,13 @@ template <bool ADJ, int PM> struct StrFl {
     __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : TM_LAM; }
 };
 
+// the persistent kernel runs every fluid body with the corner layout
+static_assert(VelFl<true, PM_FULL>::SMEM >= VelFl<true, PM_X>::SMEM && VelFl<true, PM_FULL>::SMEM >= VelFl<true, PM_Z>::SMEM &&
+                  StrFl<true, PM_FULL>::SMEM >= StrFl<true, PM_X>::SMEM &&
+                  StrFl<true, PM_FULL>::SMEM >= StrFl<true, PM_Z>::SMEM &&
+                  VelFl<false, PM_FULL>::SMEM >= VelFl<false, PM_X>::SMEM &&
+                  StrFl<false, PM_FULL>::SMEM >= StrFl<false, PM_X>::SMEM,
+              "corner layout covers the other fluid bodies");
 // the edge kernels run the PM_X and PM_Y bodies with one layout
 static_assert(VelFl<true, PM_X>::SMEM == VelFl<true, PM_Y>::SMEM && StrFl<true, PM_X>::SMEM == StrFl<true, PM_Y>::SMEM,
               "edge bodies share one layout");
@@ -497,6 +504,52 @@ void launch_fl(int pm, const StepParams& p, const TmaSet& tm, const RegionList& 
         k_fluid<STR, ADJ, PM_FULL><<<blocks, blk, fluid_smem_of<STR, ADJ, PM_FULL>(), st>>>(p, tm, rl, err);
 }
 
+// Persistent multi-instance kernel over the fluid C-PML items (z-slab, edge
+// and corner kinds, one list) of the medium-adaptive instances in a serving
+// table; the dynamic shared memory covers the corner layout, the largest.
+template <bool STR, bool ADJ>
+__global__ void __launch_bounds__(NT) k_multi_fl(const MultiTable* __restrict__ T, int* err, int* next) {
+    extern __shared__ __align__(128) float sm[];
+    multi_loop<ADJ, ML_FL>(T, err, next, sm,
+                           [](const StepParams& sp, const CUtensorMap* maps, int kind, int tile_x, int tile_y, int zc0,
+                              int zc1, int* e, float* smem) {
+                               if (kind == PM_Z)
+                                   return STR ? str_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                              : vel_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                               if (kind == PM_X)
+                                   return STR ? str_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                              : vel_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                               if (kind == PM_Y)
+                                   return STR ? str_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                              : vel_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                               return STR ? str_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                          : vel_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                           });
+}
+
+template <bool STR, bool ADJ>
+int multi_fl_grid() {
+    static int grid[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!grid[dev]) {
+        const size_t smem = fluid_smem_of<STR, ADJ, PM_FULL>();
+        cudaFuncSetAttribute(k_multi_fl<STR, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int sms = 148, per_sm = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_fl<STR, ADJ>, NT, smem);
+        grid[dev] = sms * std::max(1, per_sm);
+    }
+    return grid[dev];
+}
+
+template <bool STR, bool ADJ>
+void launch_mfl(const MultiTable* dT, int* err, int* next, cudaStream_t st) {
+    k_multi_fl<STR, ADJ><<<multi_fl_grid<STR, ADJ>(), dim3(TX, TY, 1), fluid_smem_of<STR, ADJ, PM_FULL>(), st>>>(dT, err,
+                                                                                                            next);
+}
+
 }  // namespace
 
 // Fluid C-PML items of kind pm (PM_Z, PM_X for the edges, PM_FULL) of one
@@ -510,5 +563,15 @@ void launch_fluid(bool str, bool adj, int pm, const StepParams& p, const TmaSet&
     } else {
         if (adj) launch_fl<false, true>(pm, p, tm, rl, blocks, err, st);
         else launch_fl<false, false>(pm, p, tm, rl, blocks, err, st);
+    }
+}
+
+void launch_multi_fl(bool str, bool adj, const MultiTable* dT, int* err, int* next, cudaStream_t st) {
+    if (str) {
+        if (adj) launch_mfl<true, true>(dT, err, next, st);
+        else launch_mfl<true, false>(dT, err, next, st);
+    } else {
+        if (adj) launch_mfl<false, true>(dT, err, next, st);
+        else launch_mfl<false, false>(dT, err, next, st);
     }
 }

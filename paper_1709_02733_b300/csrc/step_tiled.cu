@@ -736,42 +736,13 @@ template <bool STR, bool ADJ, int PM>
 __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_multi(const MultiTable* __restrict__ T,
                                                                                  int* err, int* next) {
     extern __shared__ __align__(128) float sm[];
-    __shared__ StepParams sp;
-    __shared__ int s_item;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    const int i0 = ADJ ? T->n_fwd : 0, i1 = ADJ ? T->n_inst : T->n_fwd;
-    const int* pre = PM == PM_FULL ? T->pre_corner : (PM == PM_X ? T->pre_edge : T->pre_inner);
-    const int first = pre[i0], total = pre[i1];
-    for (;;) {
-        __syncthreads();  // the previous item is finished with s_item and sp
-        if (tid == 0) s_item = first + atomicAdd(next, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) return;
-        int i = i0;
-        while (i + 1 < i1 && item >= pre[i + 1]) ++i;
-        const InstDev& I = T->inst[i];
-        if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
-        int tile_x, tile_y, zc0, zc1, kind;
-        locate_inline(PM == PM_FULL ? I.corner : (PM == PM_X ? I.edge : I.inner), item - pre[i], tile_x, tile_y, zc0,
-                      zc1, kind);
-        // a work item must lie inside its instance's grid and the instance
-        // must be of this kernel's direction; otherwise record the
-        // inconsistency and touch nothing
-        if (tile_x < 0 || tile_x * TX >= I.p.nx || tile_y < 0 || tile_y * TY >= I.p.ny || zc0 < 0 || zc0 >= zc1 ||
-            zc1 > I.p.nz || (I.adj != 0) != ADJ) {
-            if (tid == 0) atomicExch(err, 2);
-            continue;
-        }
-        for (int w = tid; w < (int)(sizeof(StepParams) / sizeof(int)); w += NT)
-            reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&I.p)[w];
-        if (tid == 0)
-            for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
-        __syncthreads();
-        const bool ok = STR ? str_item<ADJ, PM, false>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)
-                            : vel_item<ADJ, PM, false>(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm);
-        if (!ok) return;
-    }
+    constexpr int WHICH = PM == PM_FULL ? ML_CORNER : (PM == PM_X ? ML_EDGE : ML_INNER);
+    multi_loop<ADJ, WHICH>(T, err, next, sm,
+                           [](const StepParams& sp, const CUtensorMap* maps, int kind, int tile_x, int tile_y, int zc0,
+                              int zc1, int* e, float* smem) {
+                               return STR ? str_item<ADJ, PM, false>(sp, maps, kind, tile_x, tile_y, zc0, zc1, e, smem)
+                                          : vel_item<ADJ, PM, false>(sp, maps, kind, tile_x, tile_y, zc0, zc1, e, smem);
+                           });
 }
 
 // ---------------------------------------------------------------------------
@@ -1233,9 +1204,16 @@ static void launch_multi_family(const MultiTable* dT, int* err, int* next, cudaS
     launch_multi<STR, true, PM_NONE>(dT, err, next + 5, st);
 }
 
+// the elastic corner / edge / interior launches of both directions, then
+// the fluid C-PML and acoustic ones (which find no items for instances
+// without a medium-adaptive plan)
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st) {
     if (str) launch_multi_family<true>(dT, err, next, st);
     else launch_multi_family<false>(dT, err, next, st);
+    launch_multi_fl(str, false, dT, err, next + 6, st);
+    launch_multi_fl(str, true, dT, err, next + 7, st);
+    launch_multi_ac(str, false, dT, err, next + 8, st);
+    launch_multi_ac(str, true, dT, err, next + 9, st);
 }
 
 // Region plan of one instance for the persistent kernels: z chunks of about
@@ -1372,12 +1350,20 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
             }
         }
     }
-    size_t n = 0;
+    // the fluid C-PML items once more in one list, for the persistent kernels
+    std::vector<Region> ff;
+    for (int l : {(int)MX_INT_FZ, (int)MX_EDGE_FL, (int)MX_CORNER_FL})
+        for (Region r : lists[l]) {
+            r.bstart = (int)ff.size();
+            ff.push_back(r);
+        }
+    size_t n = ff.size();
     for (int l = 0; l < MX_N; ++l) n += lists[l].size();
     if (cudaMalloc(&mp->mem, n * sizeof(Region)) != cudaSuccess) return 1;
     std::vector<Region> all;
     all.reserve(n);
     for (int l = 0; l < MX_N; ++l) all.insert(all.end(), lists[l].begin(), lists[l].end());
+    all.insert(all.end(), ff.begin(), ff.end());
     e = cudaMemcpyAsync(mp->mem, all.data(), n * sizeof(Region), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -1393,6 +1379,10 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
         mp->points[l] = pts[l];
         off += lists[l].size();
     }
+    mp->fluid_frame.n = 0;
+    mp->fluid_frame.dev = ff.empty() ? nullptr : mp->mem + off;
+    mp->fluid_frame.dn = (int)ff.size();
+    mp->fluid_frame_blocks = (int)ff.size();
     return 0;
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "pact_internal.cuh"
+#include "tma.cuh"
 
 // one tensor map per array: u (3), sigma (6, Voigt), rho, lambda, mu, alpha
 enum { TM_U0 = 0, TM_S0 = 3, TM_RHO = 9, TM_LAM = 10, TM_MU = 11, TM_ALPHA = 12, TM_N = 13 };
@@ -66,6 +67,8 @@ struct alignas(128) InstDev {
     RegionList inner;     // work items of the interior tiles (off and on the z slabs)
     RegionList edge;      // work items of the frame tiles with one layer (x or y)
     RegionList corner;    // work items of the frame corner tiles (both layers)
+    RegionList ac;        // medium-adaptive handles: fluid no-layer items (acoustic body)
+    RegionList fl;        // medium-adaptive handles: fluid C-PML items (z slab, edge and corner kinds)
     RecTable rec;
     const float* src;     // adjoint: traces to inject
     float* dst;           // forward: traces to sample into
@@ -82,6 +85,8 @@ struct MultiTable {
     int pre_inner[kMaxInst + 1];   // first work item of each instance
     int pre_edge[kMaxInst + 1];
     int pre_corner[kMaxInst + 1];
+    int pre_ac[kMaxInst + 1];
+    int pre_fl[kMaxInst + 1];
     InstDev inst[kMaxInst];
 };
 
@@ -131,7 +136,9 @@ struct MixedPlan {
     RegionList list[MX_N];
     int blocks[MX_N] = {};
     long long points[MX_N] = {};
-    Region* mem = nullptr;   // device allocation behind the lists
+    RegionList fluid_frame;      // MX_INT_FZ, MX_EDGE_FL, MX_CORNER_FL in one list (serving)
+    int fluid_frame_blocks = 0;
+    Region* mem = nullptr;       // device allocation behind the lists
 };
 // Build the plan of the grid of p for the medium's mu (device array);
 // returns 0 on success (with no fluid item every list but the elastic ones is
@@ -186,7 +193,74 @@ long long role_points(int family, int mode, const StepParams& p);
 // persistent multi-instance half step (str = stress family) over a device
 // table: six launches (two directions x corner / edge / interior), launch k
 // taking its work items from the counter next[k], which must be zero beforehand
-constexpr int kMultiLaunches = 6;
+constexpr int kMultiLaunches = 10;
 void launch_multi_step_half(bool str, const MultiTable* dT, int* err, int* next, cudaStream_t st);
 void plan_instance_regions(const StepParams& p, int zc, RegionList& inner, int& ninner, RegionList& edge,
                            int& nedge, RegionList& corner, int& ncorner);
+
+// ---- persistent multi-instance loop --------------------------------------
+// The work lists of an instance that the persistent kernels walk.
+enum { ML_INNER = 0, ML_EDGE = 1, ML_CORNER = 2, ML_AC = 3, ML_FL = 4 };
+__device__ __forceinline__ const RegionList& inst_list(const InstDev& I, int which) {
+    return which == ML_INNER ? I.inner
+         : which == ML_EDGE  ? I.edge
+         : which == ML_CORNER ? I.corner
+         : which == ML_AC    ? I.ac
+                             : I.fl;
+}
+__device__ __forceinline__ const int* table_pre(const MultiTable* T, int which) {
+    return which == ML_INNER ? T->pre_inner
+         : which == ML_EDGE  ? T->pre_edge
+         : which == ML_CORNER ? T->pre_corner
+         : which == ML_AC    ? T->pre_ac
+                             : T->pre_fl;
+}
+
+// A fixed grid works through the items of list WHICH of every unfinished
+// instance of one direction (ADJ) in the table; each block takes the next item
+// from an atomic counter (zeroed before the launch).  body(p, maps, kind,
+// tile_x, tile_y, zc0, zc1, err, sm) runs one item and returns false if a
+// bounded wait gave up.  The instance's parameters are copied to shared memory.
+template <bool ADJ, int WHICH, typename Body>
+__device__ __forceinline__ void multi_loop(const MultiTable* __restrict__ T, int* err, int* next, float* sm,
+                                           Body&& body) {
+    __shared__ StepParams sp;
+    __shared__ int s_item;
+    const int nthreads = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int i0 = ADJ ? T->n_fwd : 0, i1 = ADJ ? T->n_inst : T->n_fwd;
+    const int* pre = table_pre(T, WHICH);
+    const int first = pre[i0], total = pre[i1];
+    for (;;) {
+        __syncthreads();  // the previous item is finished with s_item and sp
+        if (tid == 0) s_item = first + atomicAdd(next, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) return;
+        int i = i0;
+        while (i + 1 < i1 && item >= pre[i + 1]) ++i;
+        const InstDev& I = T->inst[i];
+        if (I.m >= I.nsteps) continue;  // finished instance (uniform per block)
+        int tile_x, tile_y, zc0, zc1, kind;
+        locate_item(inst_list(I, WHICH), item - pre[i], tile_x, tile_y, zc0, zc1, kind);
+        // a work item must lie inside its instance's grid and the instance
+        // must be of this kernel's direction; otherwise record the
+        // inconsistency and touch nothing
+        if (tile_x < 0 || tile_x * 32 >= I.p.nx || tile_y < 0 || tile_y * 8 >= I.p.ny || zc0 < 0 || zc0 >= zc1 ||
+            zc1 > I.p.nz || (I.adj != 0) != ADJ) {
+            if (tid == 0) atomicExch(err, 2);
+            continue;
+        }
+        for (int w = tid; w < (int)(sizeof(StepParams) / sizeof(int)); w += nthreads)
+            reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&I.p)[w];
+        if (tid == 0)
+            for (int b = 0; b < TM_N; ++b) tensormap_acquire(&I.tm.m[b]);
+        __syncthreads();
+        if (!body(sp, I.tm.m, kind, tile_x, tile_y, zc0, zc1, err, sm)) return;
+    }
+}
+
+// persistent launches over the fluid lists of medium-adaptive instances:
+// acoustic body (step_acoustic.cu) and fluid C-PML bodies (step_fluid.cu)
+void launch_multi_ac(bool str, bool adj, const MultiTable* dT, int* err, int* next, cudaStream_t st);
+void launch_multi_fl(bool str, bool adj, const MultiTable* dT, int* err, int* next, cudaStream_t st);

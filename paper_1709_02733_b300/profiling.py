@@ -41,9 +41,15 @@ def source_sha() -> str:
 
 
 def role_of(kernel_name: str):
-    """bench.py kernel role of a launch (None for the small kernels)."""
+    """bench.py kernel role of a launch (None for the small kernels).  In a
+    medium-adaptive step the fluid kernels (k_fluid<STR, ADJ, PM>, k_ac_vel,
+    k_ac_str) run inside the velocity and stress roles."""
     k = kernel_name.replace(" ", "")
-    for prefix, adj, role in (("k_vel_tiled<0", False, "fwd_velocity"), ("k_str_tiled<0", False, "fwd_stress"),
+    for prefix, adj, role in (("k_fluid<0,0", False, "fwd_velocity"), ("k_fluid<1,0", False, "fwd_stress"),
+                              ("k_fluid<0,1", True, "adj_a"), ("k_fluid<1,1", True, "adj_b"),
+                              ("k_ac_vel<0", False, "fwd_velocity"), ("k_ac_str<0", False, "fwd_stress"),
+                              ("k_ac_vel<1", True, "adj_a"), ("k_ac_str<1", True, "adj_b"),
+                              ("k_vel_tiled<0", False, "fwd_velocity"), ("k_str_tiled<0", False, "fwd_stress"),
                               ("k_vel_tiled<1", True, "adj_a"), ("k_str_tiled<1", True, "adj_b"),
                               ("k_fwd_velocity", False, "fwd_velocity"), ("k_fwd_stress", False, "fwd_stress"),
                               ("k_adj_a", True, "adj_a"), ("k_adj_b", True, "adj_b")):
