@@ -168,7 +168,9 @@ int pact_get_wavefield(pact_handle h, float* host_out);
  * forward, in = p0 (device, N floats), out = traces (device, (nsteps+1)*L),
  * row 0 is written now; is_adjoint = 1: adjoint, in = traces (device,
  * (nsteps+1)*L), out = image (device, N), written when the solve finishes.
- * Needs nx % 4 == 0 (TMA-staged kernels).  Errors as pact_forward. */
+ * Needs nx % 4 == 0 (TMA-staged kernels).  L = 0 is accepted here (a z-slab
+ * that owns no receiver): no traces are read or written and the trace
+ * pointer may be NULL.  Errors as pact_forward. */
 int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_xyz, int L, int nsteps, float* out);
 
 /* Advance every unfinished solve among hs[0..n-1] (n <= 64, one device) by
@@ -189,6 +191,42 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream);
  * GPU).  Results are complete once steps_done == nsteps and the stream has
  * reached that point. */
 int pact_poll(pact_handle h, int* steps_done);
+
+/* ---- z-slab decomposition: one slab of a larger grid per handle ------------
+ * The paper runs H and H^T on several GPUs (the CUDA + MPI implementation of
+ * its implementation section) by splitting the grid; here a slab handle holds
+ * planes [z_lo, z_hi) of the grid `global` (its own planes plus two halo planes
+ * on each side that touches another slab), and the caller exchanges the halo
+ * planes between the two half steps of every time step.  The C-PML z layer of
+ * a slab handle lies at the whole grid's ends (Appendix A.3): a slab in the
+ * middle has no z layer.  Medium, p0, traces, image and receiver coordinates of
+ * a slab handle are those of its own grid of (z_hi - z_lo) planes (receiver z
+ * relative to z_lo).  Errors: PACT_EINVAL (global fails the pact_create_grid
+ * checks, 0 <= z_lo < z_hi <= global->nz violated, or fewer than 5 planes),
+ * PACT_ENOMEM, PACT_ECUDA. */
+int pact_create_slab(const pact_grid_desc* global, int z_lo, int z_hi, void* stream, pact_handle* out);
+
+/* One half step of the solve prepared on h by pact_begin (any handle, a slab
+ * handle included): stress = 0 the velocity-family half (forward: phi, u of
+ * Eq. (it); adjoint: the transposes of the stress update, Eq. (backwardstep)),
+ * stress = 1 the stress-family half.  A time step is the velocity half, the
+ * stress half and pact_step_receivers, in that order.  Queued on the handle's
+ * stream.  Errors: PACT_ESTATE (no unfinished solve), PACT_EINVAL (a handle
+ * created with PACT_FUSED=1), PACT_ECUDA. */
+int pact_step_half(pact_handle h, int stress);
+
+/* Finish the time step of the solve prepared on h: forward, sample row m of
+ * the traces (Theta, Eq. (interpgrid)); adjoint, inject row nsteps - m
+ * (Theta^T); the adjoint's read-out (tau^T) follows the last step.  Advances
+ * the step count that pact_poll reports.  Errors as pact_step_half. */
+int pact_step_receivers(pact_handle h);
+
+/* Device address of wavefield array `field` of h (0..8: u^1, u^2, u^3,
+ * sigma^11, sigma^22, sigma^33, sigma^23, sigma^13, sigma^12; after an adjoint
+ * pact_begin the same slots hold w and Q): N floats, [z][y][x], one z plane
+ * of nx*ny floats contiguous.  For halo exchange between slab handles; the
+ * library owns the memory.  Errors: PACT_EINVAL. */
+int pact_field_ptr(pact_handle h, int field, float** out);
 
 /* Forward operator H that allocates no device memory.  The paper has no
  * counterpart: this is a deployment variant of pact_forward for callers that

@@ -205,6 +205,8 @@ extern "C" int pact_forward_noalloc(const pact_grid_desc* desc, const float* rho
     p.ny = d.ny;
     p.nz = d.nz;
     p.P = d.npml;
+    p.z0g = 0;
+    p.nzg = d.nz;
     p.dt = (float)d.dt;
     p.inv_dx = (float)(1.0 / d.dx);
     for (int i = 0; i < 3; ++i) p.u[i] = fields + i * N;

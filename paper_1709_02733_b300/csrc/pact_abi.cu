@@ -94,6 +94,8 @@ struct pact_grid {
     // kernels, the rest the elastic ones (plan built from the medium)
     bool mixed = false;
     MixedPlan mixed_plan{};
+    // a slab of a larger grid (pact_create_slab): plane k is plane z0g + k of nzg
+    int z0g = 0, nzg = 0;
     float* fields2 = nullptr;
     int cur = 0;
     TmaSet tmp[2]{};
@@ -225,6 +227,8 @@ static StepParams make_params(pact_handle h, int in = 0, int out = -1) {
     p.ny = d.ny;
     p.nz = d.nz;
     p.P = d.npml;
+    p.z0g = h->z0g;
+    p.nzg = h->nzg;
     p.dt = (float)d.dt;
     p.inv_dx = (float)(1.0 / d.dx);
     float* fi = buffer(h, in);
@@ -531,15 +535,16 @@ static int ensure_stage(pact_handle h, float** buf, size_t* cap, size_t n) {
 
 extern "C" {
 
-int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out) {
-    std::string why;
-    if (!out) return fail(nullptr, PACT_EINVAL, "out is NULL");
+// A handle for grid desc, which is planes [z0g, z0g + desc->nz) of a grid of
+// nzg planes (z0g = 0, nzg = desc->nz for a whole grid); desc is checked by
+// the caller.
+static int create_handle(const pact_grid_desc* desc, int z0g, int nzg, void* stream, pact_handle* out) {
     *out = nullptr;
-    int rc = check_desc(desc, why);
-    if (rc) return fail(nullptr, rc, why);
     pact_grid* h = new (std::nothrow) pact_grid();
     if (!h) return fail(nullptr, PACT_ENOMEM, "host allocation failed");
     h->d = *desc;
+    h->z0g = z0g;
+    h->nzg = nzg;
     h->stream = (cudaStream_t)stream;
     h->N = (size_t)desc->nx * desc->ny * desc->nz;
     h->nmax = std::max(desc->nx, std::max(desc->ny, desc->nz));
@@ -589,6 +594,8 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
             q.ny = desc->ny;
             q.nz = desc->nz;
             q.P = desc->npml;
+            q.z0g = z0g;
+            q.nzg = nzg;
             RegionList rl;
             int blocks = 0;
             h->fused = fused_plan(q, rl, blocks);
@@ -616,6 +623,28 @@ int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out)
     }
     *out = h;
     return PACT_OK;
+}
+
+int pact_create_grid(const pact_grid_desc* desc, void* stream, pact_handle* out) {
+    std::string why;
+    if (!out) return fail(nullptr, PACT_EINVAL, "out is NULL");
+    *out = nullptr;
+    const int rc = check_desc(desc, why);
+    if (rc) return fail(nullptr, rc, why);
+    return create_handle(desc, 0, desc->nz, stream, out);
+}
+
+int pact_create_slab(const pact_grid_desc* global, int z_lo, int z_hi, void* stream, pact_handle* out) {
+    std::string why;
+    if (!out) return fail(nullptr, PACT_EINVAL, "out is NULL");
+    *out = nullptr;
+    const int rc = check_desc(global, why);
+    if (rc) return fail(nullptr, rc, why);
+    if (z_lo < 0 || z_hi > global->nz || z_hi - z_lo < 5)
+        return fail(nullptr, PACT_EINVAL, "pact_create_slab: need 0 <= z_lo, z_hi <= nz and z_hi - z_lo >= 5");
+    pact_grid_desc d = *global;
+    d.nz = z_hi - z_lo;
+    return create_handle(&d, z_lo, global->nz, stream, out);
 }
 
 int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const float* mu, const float* alpha) {
@@ -662,12 +691,14 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     const pact_grid_desc& d = h->d;
     const double vmax = d.pml_vmax > 0 ? d.pml_vmax : cmax;
     std::vector<float> tab(18 * (size_t)h->nmax, 0.0f);
+    // the z profile of a slab handle is the whole grid's at the slab's planes
     const int dims[3] = {d.nx, d.ny, d.nz};
+    const int gdim[3] = {d.nx, d.ny, h->nzg}, goff[3] = {0, 0, h->z0g};
     for (int a = 0; a < 3; ++a)
         for (int l = 0; l < 2; ++l)
             for (int k = 0; k < dims[a]; ++k) {
                 double ca, cb, cc;
-                pml_coef(dims[a], d.npml, d.dx, d.dt, vmax, d.pml_R0, d.pml_f0, k + 0.5 * l, ca, cb, cc);
+                pml_coef(gdim[a], d.npml, d.dx, d.dt, vmax, d.pml_R0, d.pml_f0, goff[a] + k + 0.5 * l, ca, cb, cc);
                 tab[((a * 2 + l) * 3 + 0) * (size_t)h->nmax + k] = (float)ca;
                 tab[((a * 2 + l) * 3 + 1) * (size_t)h->nmax + k] = (float)cb;
                 tab[((a * 2 + l) * 3 + 2) * (size_t)h->nmax + k] = (float)cc;
@@ -840,11 +871,23 @@ int pact_role_points(pact_handle h, int kind, long long* points, long long* slab
 }
 
 int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_xyz, int L, int nsteps, float* out) {
-    int rc = precheck(h, in, out, nsteps);
-    if (rc) return rc;
+    int rc;
+    if (L == 0) {
+        // no receiver (a z-slab owning none): no traces, so the trace pointer
+        // may be NULL; p0 (forward) or the image (adjoint) is still required
+        const void* field = is_adjoint ? (const void*)out : (const void*)in;
+        rc = precheck(h, field, field, nsteps);
+        if (rc) return rc;
+        h->L = 0;
+        h->ncorner = 0;
+        h->rec_host.clear();
+    } else {
+        rc = precheck(h, in, out, nsteps);
+        if (rc) return rc;
+        rc = set_receivers(h, rec_xyz, L);
+        if (rc) return rc;
+    }
     if (!h->tiled) return fail(h, PACT_EINVAL, "serving uses the TMA-staged kernels: nx must be a multiple of 4");
-    rc = set_receivers(h, rec_xyz, L);
-    if (rc) return rc;
     h->cur = 0;
     rc = zero_state(h);
     if (rc) return rc;
@@ -860,7 +903,7 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_source(in, p, h->stream, band_counter(h));
         launch_sample(p, r, out, h->stream);
     } else {
-        launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
+        if (L > 0) launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
         if (nsteps == 0) launch_readout(out, p, h->stream);
     }
     if (h->mixed) {
@@ -950,6 +993,68 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
         }
     }
     if (cudaGetLastError() != cudaSuccess) return fail(nullptr, PACT_ECUDA, "pact_advance: launch failed");
+    return PACT_OK;
+}
+
+// ---- stepping a prepared solve one half step at a time ----------------------
+// (the z-slab decomposition exchanges halo planes between the halves)
+int pact_step_half(pact_handle h, int stress) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (!h->sv_active) return fail(h, PACT_ESTATE, "pact_step_half: no unfinished solve (pact_begin first)");
+    if (h->fused) return fail(h, PACT_EINVAL, "pact_step_half: not with the single-pass kernel (PACT_FUSED)");
+    CK(h, cudaSetDevice(h->device));
+    const bool adj = h->sv_adj != 0, str = stress != 0;
+    const StepParams p = make_params(h);
+    int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
+    const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join, h->aux2, h->ev_join2};
+    const MixedPlan* mp = h->mixed ? &h->mixed_plan : nullptr;
+    const int mode = step_mode(h);
+    if (!str) {
+        mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, h->tm, err, ss, mode, mp));
+        if (h->acoustic)
+            mark(h, adj ? PACT_K_ADJ_AC_A : PACT_K_FWD_AC_VEL, launch_acoustic_step(false, adj, p, h->tm, err, h->stream));
+    } else {
+        mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, h->tm, err, ss, mode, mp));
+        if (h->acoustic)
+            mark(h, adj ? PACT_K_ADJ_AC_B : PACT_K_FWD_AC_STR, launch_acoustic_step(true, adj, p, h->tm, err, h->stream));
+    }
+    CK(h, cudaGetLastError());
+    return PACT_OK;
+}
+
+int pact_step_receivers(pact_handle h) {
+    if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
+    if (!h->sv_active) return fail(h, PACT_ESTATE, "pact_step_receivers: no unfinished solve (pact_begin first)");
+    CK(h, cudaSetDevice(h->device));
+    const StepParams p = make_params(h);
+    const RecTable r = make_rec(h);
+    const int m = h->sv_m + 1;  // the step just completed
+    if (h->L > 0) {
+        if (!h->sv_adj) {
+            launch_sample(p, r, h->sv_out + (size_t)m * h->L, h->stream);
+            mark(h, PACT_K_SAMPLE);
+        } else {
+            launch_inject(p, r, h->sv_in + (size_t)(h->sv_nsteps - m) * h->L, h->stream);
+            mark(h, PACT_K_INJECT, r.ncorner > 0);
+        }
+    }
+    h->sv_m = m;
+    if (m == h->sv_nsteps) {
+        h->sv_active = false;
+        if (h->sv_adj) {
+            launch_readout(h->sv_out, p, h->stream);
+            mark(h, PACT_K_READOUT);
+        }
+    }
+    CK(h, cudaGetLastError());
+    return PACT_OK;
+}
+
+int pact_field_ptr(pact_handle h, int field, float** out) {
+    if (!h || !out) return fail(h, PACT_EINVAL, "pact_field_ptr: NULL argument");
+    if (field < 0 || field > 8) return fail(h, PACT_EINVAL, "pact_field_ptr: field must be 0..8");
+    if (h->fused) return fail(h, PACT_EINVAL, "pact_field_ptr: not with the single-pass kernel (PACT_FUSED)");
+    *out = h->fields + (size_t)field * h->N;
     return PACT_OK;
 }
 

@@ -25,6 +25,10 @@ __host__ __device__ constexpr int voigt(int i, int j) {
 struct StepParams {
     int nx, ny, nz;
     int P;                      // C-PML thickness (0: none)
+    // z-slab of a larger grid: this grid's plane k is plane z0g + k of a grid
+    // of nzg planes, whose z layers lie at its own ends (z0g = 0, nzg = nz
+    // for a whole grid)
+    int z0g, nzg;
     float dt, inv_dx;
     float* u[3];                // velocity components (input of a step)
     float* s[6];                // stress, Voigt order (input of a step)
@@ -49,6 +53,17 @@ __host__ __device__ __forceinline__ int slab_local(int k, int n, int P) {
     if (k < P) return k;
     int r = k - (n - P - 1);
     return r >= 0 ? P + r : -1;
+}
+
+// slab coordinate of plane z on the z layer (global position), -1 off it
+__host__ __device__ __forceinline__ int zslab(int z, const StepParams& p) {
+    return slab_local(z + p.z0g, p.nzg, p.P);
+}
+
+// slab coordinate of position k along axis A (z: global position)
+template <int A>
+__host__ __device__ __forceinline__ int axis_slab(int k, const StepParams& p) {
+    return A == 2 ? zslab(k, p) : slab_local(k, A == 0 ? p.nx : p.ny, p.P);
 }
 
 __device__ __forceinline__ size_t slab_index(int axis, int x, int y, int z, int l, const StepParams& p) {

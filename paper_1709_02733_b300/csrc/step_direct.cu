@@ -83,7 +83,7 @@ template <int I, int J>
 __device__ __forceinline__ float vel_term(int x, int y, int z, const StepParams& p) {
     const float g = dsig<I, J>(x, y, z, p);
     const int k = coord<J>(x, y, z);
-    const int l = slab_local(k, extent<J>(p), p.P);
+    const int l = axis_slab<J>(k, p);
     if (l < 0) return g;
     constexpr int h = (I == J);  // u^I is on the half lattice along I only
     const float a = ptab<J>(p, h, 0, k), b = ptab<J>(p, h, 1, k), chi = ptab<J>(p, h, 2, k);
@@ -126,7 +126,7 @@ template <int I, int J>
 __device__ __forceinline__ float psi_step(float g, int x, int y, int z, const StepParams& p, float& chi) {
     chi = 0.0f;
     const int k = coord<J>(x, y, z);
-    const int l = slab_local(k, extent<J>(p), p.P);
+    const int l = axis_slab<J>(k, p);
     if (l < 0) return 0.0f;
     constexpr int h = (I != J);  // sigma^{IJ}, I != J, is on the half lattice along J
     const float a = ptab<J>(p, h, 0, k), b = ptab<J>(p, h, 1, k);
@@ -181,7 +181,7 @@ __device__ __forceinline__ float adj_normal(int x, int y, int z, const StepParam
     const size_t q = lin3(x, y, z, p.nx, p.ny);
     const float qk = __ldg(p.s[K] + q);
     const int k = coord<K>(x, y, z);
-    const int l = slab_local(k, extent<K>(p), p.P);
+    const int l = axis_slab<K>(k, p);
     if (l < 0) return qk;
     const float a = ptab<K>(p, 0, 0, k), chi = ptab<K>(p, 0, 2, k);
     return qk + a * (__ldg(p.psi[K][K] + slab_index(K, x, y, z, l, p)) + chi * qk);
@@ -194,7 +194,7 @@ __device__ __forceinline__ float adj_shear(int x, int y, int z, const StepParams
     const size_t q = lin3(x, y, z, p.nx, p.ny);
     const float qs = __ldg(p.s[voigt(K, J)] + q);
     const int k = coord<J>(x, y, z);
-    const int l = slab_local(k, extent<J>(p), p.P);
+    const int l = axis_slab<J>(k, p);
     if (l < 0) return qs;
     const float a = ptab<J>(p, 1, 0, k), chi = ptab<J>(p, 1, 2, k);
     return qs + a * (__ldg(p.psi[K][J] + slab_index(J, x, y, z, l, p)) + chi * qs);
@@ -204,7 +204,7 @@ __device__ __forceinline__ float adj_shear(int x, int y, int z, const StepParams
 template <int K, int J>
 __device__ __forceinline__ void phi_tail(float w, int x, int y, int z, const StepParams& p) {
     const int k = coord<J>(x, y, z);
-    const int l = slab_local(k, extent<J>(p), p.P);
+    const int l = axis_slab<J>(k, p);
     if (l < 0) return;
     constexpr int h = (K == J);
     const float b = ptab<J>(p, h, 1, k), chi = ptab<J>(p, h, 2, k);
@@ -243,7 +243,7 @@ __device__ __forceinline__ float adj_vel(int x, int y, int z, const StepParams& 
     const size_t q = lin3(x, y, z, p.nx, p.ny);
     const float w = __ldg(p.u[I] + q);
     const int k = coord<J>(x, y, z);
-    const int l = slab_local(k, extent<J>(p), p.P);
+    const int l = axis_slab<J>(k, p);
     if (l < 0) return w;
     constexpr int h = (I == J);
     const float a = ptab<J>(p, h, 0, k), chi = ptab<J>(p, h, 2, k);
@@ -254,7 +254,7 @@ __device__ __forceinline__ float adj_vel(int x, int y, int z, const StepParams& 
 template <int I, int J>
 __device__ __forceinline__ void psi_tail(float qv, int x, int y, int z, const StepParams& p) {
     const int k = coord<J>(x, y, z);
-    const int l = slab_local(k, extent<J>(p), p.P);
+    const int l = axis_slab<J>(k, p);
     if (l < 0) return;
     constexpr int h = (I != J);
     const float b = ptab<J>(p, h, 1, k), chi = ptab<J>(p, h, 2, k);
@@ -306,7 +306,7 @@ __global__ void k_adj_b(StepParams p) {
 // The loop advances whole warps (blockDim is a multiple of 32) so that every
 // lane takes part in the ballot; one atomic per warp with a hit.
 __global__ void k_source(const float* __restrict__ p0, float* s0, float* s1, float* s2, size_t n, int nx, int ny,
-                         int nz, int band, unsigned long long* band_count) {
+                         int z0g, int nzg, int band, unsigned long long* band_count) {
     const unsigned lane = threadIdx.x & 31u;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t base = blockIdx.x * (size_t)blockDim.x + (threadIdx.x - lane); base < n; base += stride) {
@@ -322,8 +322,8 @@ __global__ void k_source(const float* __restrict__ p0, float* s0, float* s1, flo
                 const int x = (int)(i % (size_t)nx);
                 const size_t r = i / (size_t)nx;
                 const int y = (int)(r % (size_t)ny);
-                const int z = (int)(r / (size_t)ny);
-                const int dmin = min(min(min(x, nx - 1 - x), min(y, ny - 1 - y)), min(z, nz - 1 - z));
+                const int z = z0g + (int)(r / (size_t)ny);  // plane of the whole grid
+                const int dmin = min(min(min(x, nx - 1 - x), min(y, ny - 1 - y)), min(z, nzg - 1 - z));
                 hit = dmin < band;
             }
         }
@@ -450,7 +450,7 @@ static int ew_blocks(size_t n) {
 void launch_source(const float* p0, const StepParams& p, cudaStream_t st, unsigned long long* band_count) {
     const size_t n = (size_t)p.nx * p.ny * p.nz;
     unsigned long long* c = p.P > 0 ? band_count : nullptr;
-    k_source<<<ew_blocks(n), 256, 0, st>>>(p0, p.s[0], p.s[1], p.s[2], n, p.nx, p.ny, p.nz, p.P + 2, c);
+    k_source<<<ew_blocks(n), 256, 0, st>>>(p0, p.s[0], p.s[1], p.s[2], n, p.nx, p.ny, p.z0g, p.nzg, p.P + 2, c);
 }
 
 void launch_readout(float* img, const StepParams& p, cudaStream_t st) {
@@ -459,7 +459,7 @@ void launch_readout(float* img, const StepParams& p, cudaStream_t st) {
 }
 
 void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStream_t st) {
-    k_sample<<<(r.L + 127) / 128, 128, 0, st>>>(p.s[0], p.s[1], p.s[2], r, out);
+    if (r.L > 0) k_sample<<<(r.L + 127) / 128, 128, 0, st>>>(p.s[0], p.s[1], p.s[2], r, out);
 }
 
 void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st) {

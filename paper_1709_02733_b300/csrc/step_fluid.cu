@@ -137,7 +137,7 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
         nu[0] = p.u[0][g];
         nu[1] = p.u[1][g];
         nu[2] = p.u[2][g];
-        const int lz = slab_local(zn, p.nz, P);
+        const int lz = zslab(zn, p);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             if (in_axis<LX, LY>(j, px, lz)) nph[j] = p.phi[j][j][own_slab(j, px, lz, x, y, zn, p)];
@@ -147,7 +147,7 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
     auto prefetch_head = [&](int pn) {
         if constexpr (ADJ) {
             if (!own || pn < 0 || pn >= p.nz) return;
-            const int l = slab_local(pn, p.nz, P);
+            const int l = zslab(pn, p);
             if (l >= 0) nhp = p.psi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
         }
     };
@@ -184,7 +184,7 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
             float h33 = ring.stage(pl)[o];
             if constexpr (ADJ) {
                 // z-layer term of F33 (integer lattice, plane pl)
-                if (own && pl >= 0 && pl < p.nz && slab_local(pl, p.nz, P) >= 0) {
+                if (own && pl >= 0 && pl < p.nz && zslab(pl, p) >= 0) {
                     const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
                     h33 += a * (chp + chi * h33);
                 }
@@ -333,7 +333,7 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
         if (!own || zn < zc0 || zn >= zc1) return;
         const unsigned g = (unsigned)zn * nxy + gxy;
         ns = p.s[0][g];
-        const int lz = slab_local(zn, p.nz, P);
+        const int lz = zslab(zn, p);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             if (in_axis<LX, LY>(j, px, lz)) nps[j] = p.psi[j][j][own_slab(j, px, lz, x, y, zn, p)];
@@ -344,7 +344,7 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
         if constexpr (ADJ) {
             const int pm = pn - 1;
             if (!own || pm < 0 || pm >= p.nz) return;
-            const int l = slab_local(pm, p.nz, P);
+            const int l = zslab(pm, p);
             if (l >= 0) nhp = p.phi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
         }
     };
@@ -383,7 +383,7 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
             if constexpr (ADJ) {
                 // z-layer term of E33 (half lattice, plane pl-1)
                 const int zm = pl - 1;
-                if (own && spm && zm >= 0 && zm < p.nz && slab_local(zm, p.nz, P) >= 0) {
+                if (own && spm && zm >= 0 && zm < p.nz && zslab(zm, p) >= 0) {
                     const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
                     hz += a * (chp + c * hz);
                 }

@@ -119,7 +119,7 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         nu[1] = p.u[1][g];
         nu[2] = p.u[2][g];
         if constexpr (PML) {
-            const int lz = slab_local(zn, p.nz, P);
+            const int lz = zslab(zn, p);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if (in_axis<LX, LY>(j, px, lz)) {
@@ -136,12 +136,12 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         if constexpr (ADJ && PML) {
             if (!own) return;
             if (pn >= 0 && pn < p.nz) {
-                const int l = slab_local(pn, p.nz, P);
+                const int l = zslab(pn, p);
                 if (l >= 0) nhp[0] = p.psi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
             }
             const int pm = pn - 1;
             if (pm >= 0 && pm < p.nz) {
-                const int l = slab_local(pm, p.nz, P);
+                const int l = zslab(pm, p);
                 if (l >= 0) {
                     const unsigned si = ((unsigned)l * p.ny + y) * p.nx + x;
                     nhp[1] = p.psi[0][2][si];
@@ -204,12 +204,12 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
             if constexpr (ADJ && PML) {
                 // z-layer terms of F33 (integer lattice, plane pl) and of F13,
                 // F23 (half lattice, plane pl-1)
-                if (own && pl >= 0 && pl < p.nz && slab_local(pl, p.nz, P) >= 0) {
+                if (own && pl >= 0 && pl < p.nz && zslab(pl, p) >= 0) {
                     const float a = tabv(p, 2, 0, 0, pl), chi = tabv(p, 2, 0, 2, pl);
                     h33 += a * (chp[0] + chi * h33);
                 }
                 const int zm = pl - 1;
-                if (own && spm && zm >= 0 && zm < p.nz && slab_local(zm, p.nz, P) >= 0) {
+                if (own && spm && zm >= 0 && zm < p.nz && zslab(zm, p) >= 0) {
                     const float a = tabv(p, 2, 1, 0, zm), chi = tabv(p, 2, 1, 2, zm);
                     h13 += a * (chp[1] + chi * h13);
                     h23 += a * (chp[2] + chi * h23);
@@ -406,7 +406,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
 #pragma unroll
         for (int v = 0; v < 6; ++v) ns[v] = p.s[v][g];
         if constexpr (PML) {
-            const int lz = slab_local(zn, p.nz, P);
+            const int lz = zslab(zn, p);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if (in_axis<LX, LY>(j, px, lz)) {
@@ -423,7 +423,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         if constexpr (ADJ && PML) {
             if (!own) return;
             if (pn >= 0 && pn < p.nz) {
-                const int l = slab_local(pn, p.nz, P);
+                const int l = zslab(pn, p);
                 if (l >= 0) {
                     const unsigned si = ((unsigned)l * p.ny + y) * p.nx + x;
                     nhp[0] = p.phi[0][2][si];
@@ -432,7 +432,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
             }
             const int pm = pn - 1;
             if (pm >= 0 && pm < p.nz) {
-                const int l = slab_local(pm, p.nz, P);
+                const int l = zslab(pm, p);
                 if (l >= 0) nhp[2] = p.phi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
             }
         }
@@ -491,13 +491,13 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
             if constexpr (ADJ && PML) {
                 // z-layer terms of E13, E23 (integer lattice, plane pl) and E33
                 // (half lattice, plane pl-1)
-                if (own && pl >= 0 && pl < p.nz && slab_local(pl, p.nz, P) >= 0) {
+                if (own && pl >= 0 && pl < p.nz && zslab(pl, p) >= 0) {
                     const float a = tabv(p, 2, 0, 0, pl), c = tabv(p, 2, 0, 2, pl);
                     hx += a * (chp[0] + c * hx);
                     hy += a * (chp[1] + c * hy);
                 }
                 const int zm = pl - 1;
-                if (own && spm && zm >= 0 && zm < p.nz && slab_local(zm, p.nz, P) >= 0) {
+                if (own && spm && zm >= 0 && zm < p.nz && zslab(zm, p) >= 0) {
                     const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
                     hz += a * (chp[2] + c * hz);
                 }
@@ -750,6 +750,19 @@ __global__ void __launch_bounds__(NT, (multi_min_blocks<STR, ADJ, PM>())) k_mult
 // ---------------------------------------------------------------------------
 namespace {
 
+// Planes [za, zb) whose z-difference reach (two planes up and down, and the
+// adjoint's z-layer-augmented fields) stays off the z layers; the z layers
+// lie at the ends of the whole grid, which for a slab handle is larger.
+void no_layer_planes(const StepParams& p, int& za, int& zb) {
+    if (p.P <= 0) {
+        za = 0;
+        zb = p.nz;
+        return;
+    }
+    za = std::min(std::max(p.P + 2 - p.z0g, 0), p.nz);
+    zb = std::max(za, std::min(p.nzg - p.P - 3 - p.z0g, p.nz));
+}
+
 // tiles whose halo region (x0-2 .. x0+TX+2, y0-2 .. y0+TY+2) stays off the
 // x and y layer slabs; returns false if there are none
 bool interior_tiles(const StepParams& p, int& txlo, int& txhi, int& tylo, int& tyhi) {
@@ -812,6 +825,7 @@ struct FusedBox {
     int txlo, txhi, tylo, tyhi, za, zb;  // inclusive tile ranges, planes [za, zb)
 };
 bool fused_box(const StepParams& p, FusedBox& f) {
+    if (p.z0g != 0 || p.nzg != p.nz) return false;  // whole grids only
     const int P = p.P;
     const int hx = P > 0 ? p.nx - P - 2 : p.nx - 1, hy = P > 0 ? p.ny - P - 2 : p.ny - 1;
     const int hz = P > 0 ? p.nz - P - 2 : p.nz - 1;
@@ -891,8 +905,8 @@ void make_regions(const StepParams& p, long slots_inner, long slots_edge, long s
     // Output planes [za, zb) run without layer code: their z differences reach
     // two planes up and down, and the adjoint differences fields that carry
     // z-layer terms on the slab planes, so the reach must stay off the slabs.
-    const int za = P > 0 ? std::min(P + 2, p.nz) : 0;
-    const int zb = P > 0 ? std::max(za, p.nz - P - 3) : p.nz;
+    int za, zb;
+    no_layer_planes(p, za, zb);
     add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, za, zb, chunk_planes(tiles, zb - za, slots_inner), PM_NONE,
                inner_blocks);
     add_region(inner, txlo, txhi + 1, tylo, tyhi + 1, 0, za, za, PM_Z, inner_blocks);
@@ -900,7 +914,7 @@ void make_regions(const StepParams& p, long slots_inner, long slots_edge, long s
 }
 
 struct LaunchPlan {
-    int dev, nx, ny, nz, P, family, mode;
+    int dev, nx, ny, nz, P, z0g, nzg, family, mode;
     RegionList inner, edge, corner;  // interior, frame edges (PM_X, PM_Y), frame corners (PM_FULL)
     int inner_blocks, edge_blocks, corner_blocks;
     RegionList ac;                   // STEP_ACOUSTIC: the no-layer interior region (acoustic kernels)
@@ -960,7 +974,7 @@ LaunchPlan plan_for(int family, const StepParams& p, int mode) {
     for (int i = 0; i < nplans; ++i) {
         const LaunchPlan& L = plans[i];
         if (L.dev == dev && L.family == family && L.mode == mode && L.nx == p.nx && L.ny == p.ny && L.nz == p.nz &&
-            L.P == p.P)
+            L.P == p.P && L.z0g == p.z0g && L.nzg == p.nzg)
             return L;
     }
     const long si = device_slots(fam_fn(family, PM_NONE), fam_smem(family, PM_NONE), dev);
@@ -974,6 +988,8 @@ LaunchPlan plan_for(int family, const StepParams& p, int mode) {
     L.ny = p.ny;
     L.nz = p.nz;
     L.P = p.P;
+    L.z0g = p.z0g;
+    L.nzg = p.nzg;
     RegionList outer;
     int outer_blocks = 0;
     FusedBox fb;
@@ -1278,7 +1294,8 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
     if (p.P <= 0 || !interior_tiles(p, txlo, txhi, tylo, tyhi)) return 0;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY, ntiles = ntx * nty;
     // the no-layer planes of the interior tiles (as in make_regions)
-    const int za = std::min(p.P + 2, p.nz), zb = std::max(za, p.nz - p.P - 3);
+    int za, zb;
+    no_layer_planes(p, za, zb);
     unsigned char* d_flag = nullptr;
     const size_t nflag = (size_t)p.nz * ntiles;
     if (cudaMalloc(&d_flag, nflag) != cudaSuccess) return 1;
@@ -1289,11 +1306,14 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_flag);
     if (e != cudaSuccess) return 1;
-    // solid[z][t]: a solid node within planes z-3 .. z+3 of tile t's reach
+    // solid[z][t]: a solid node within planes z-3 .. z+3 of tile t's reach;
+    // on a slab of a larger grid the planes beyond its halo are unknown here,
+    // so a reach that crosses a cut between slabs counts as solid
     std::vector<unsigned char> solid(nflag);
+    const bool cut_lo = p.z0g > 0, cut_hi = p.z0g + p.nz < p.nzg;
     for (int t = 0; t < ntiles; ++t)
         for (int z = 0; z < p.nz; ++z) {
-            unsigned char any = 0;
+            unsigned char any = (cut_lo && z < 3) || (cut_hi && z > p.nz - 4);
             for (int k = std::max(0, z - 3); k <= std::min(p.nz - 1, z + 3); ++k) any |= flag[(size_t)k * ntiles + t];
             solid[(size_t)z * ntiles + t] = any;
         }

@@ -246,9 +246,7 @@ __device__ __forceinline__ float tabv(const StepParams& p, int axis, int half, i
 
 // position (axis coordinate k) inside the slab of `axis`? returns slab index or -1
 __device__ __forceinline__ long slab_at(const StepParams& p, int axis, int gx, int gy, int gz) {
-    const int k = axis == 0 ? gx : (axis == 1 ? gy : gz);
-    const int n = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
-    const int l = slab_local(k, n, p.P);
+    const int l = axis == 0 ? slab_local(gx, p.nx, p.P) : (axis == 1 ? slab_local(gy, p.ny, p.P) : zslab(gz, p));
     if (l < 0) return -1;
     return (long)slab_index(axis, gx, gy, gz, l, p);
 }
@@ -300,7 +298,7 @@ struct PmlZ {
 };
 
 __device__ __forceinline__ void pml_z_init(PmlZ& q, const StepParams& p, int z) {
-    q.lz = (z >= 0 && z < p.nz) ? slab_local(z, p.nz, p.P) : -1;
+    q.lz = (z >= 0 && z < p.nz) ? zslab(z, p) : -1;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh)
 #pragma unroll

@@ -29,7 +29,7 @@ EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint"
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
            "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
            "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces", "pact_check_bounded_wait",
-           "pact_support_warning"]
+           "pact_support_warning", "pact_create_slab", "pact_step_half", "pact_step_receivers", "pact_field_ptr"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
@@ -90,6 +90,10 @@ def load(path: str = SO_PATH):
     lib.pact_tv_prox_nn.argtypes = [fp, fp, i, i, i, ctypes.c_float, i, fp, vp]
     lib.pact_resample_traces.argtypes = [fp, i, fp, i, i, ctypes.c_double, ctypes.c_double, vp]
     lib.pact_check_bounded_wait.argtypes = [ctypes.c_uint, vp]
+    lib.pact_create_slab.argtypes = [D, i, i, vp, ctypes.POINTER(vp)]
+    lib.pact_step_half.argtypes = [vp, i]
+    lib.pact_step_receivers.argtypes = [vp]
+    lib.pact_field_ptr.argtypes = [vp, i, ctypes.POINTER(ctypes.c_void_p)]
     for name in EXPORTS:
         if name != "pact_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -193,16 +197,25 @@ class Grid:
     creation time); every call is ordered on it.
     """
 
-    def __init__(self, desc: GridDesc, stream=None):
+    def __init__(self, desc: GridDesc, stream=None, slab=None):
+        """slab=(z_lo, z_hi): a handle for planes [z_lo, z_hi) of the grid desc
+        (pact_create_slab); the handle's own grid then has z_hi - z_lo planes."""
         import torch
         self.lib = load()
-        self.desc = desc
-        self.shape = desc.shape
-        self.N = desc.N
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._h = ctypes.c_void_p()
-        _check(self.lib.pact_create_grid(ctypes.byref(pact_grid_desc.from_desc(desc)),
-                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)))
+        if slab is None:
+            self.desc = desc
+            _check(self.lib.pact_create_grid(ctypes.byref(pact_grid_desc.from_desc(desc)),
+                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)))
+        else:
+            z_lo, z_hi = int(slab[0]), int(slab[1])
+            _check(self.lib.pact_create_slab(ctypes.byref(pact_grid_desc.from_desc(desc)), z_lo, z_hi,
+                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)))
+            from dataclasses import replace
+            self.desc = replace(desc, nz=z_hi - z_lo)
+        self.shape = self.desc.shape
+        self.N = self.desc.N
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -299,6 +312,37 @@ class Grid:
         return int(n.value)
 
     support_warning = pact_support_warning
+
+    def pact_step_half(self, stress: bool):
+        _check(self.lib.pact_step_half(self._h, int(bool(stress))), self._h)
+
+    step_half = pact_step_half
+
+    def pact_step_receivers(self):
+        _check(self.lib.pact_step_receivers(self._h), self._h)
+
+    step_receivers = pact_step_receivers
+
+    def pact_field_ptr(self, field: int) -> int:
+        """Device address of wavefield array `field` (0..8)."""
+        ptr = ctypes.c_void_p()
+        _check(self.lib.pact_field_ptr(self._h, int(field), ctypes.byref(ptr)), self._h)
+        return int(ptr.value)
+
+    field_ptr = pact_field_ptr
+
+    def field_view(self, field: int):
+        """Wavefield array `field` (0..8) as a (nz, ny, nx) float32 CUDA tensor
+        sharing the handle's memory (valid while the handle lives)."""
+        import torch
+
+        class _Dev:
+            pass
+
+        d = _Dev()
+        d.__cuda_array_interface__ = {"shape": self.shape, "typestr": "<f4", "strides": None,
+                                      "data": (self.pact_field_ptr(field), False), "version": 3}
+        return torch.as_tensor(d, device="cuda")
 
     def pact_poll(self) -> int:
         n = ctypes.c_int(0)
