@@ -52,6 +52,10 @@ def parse():
                     help="serve a seeded Poisson stream (continuous batching vs one at a time)")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--ksteps", type=int, default=16)
+    ap.add_argument("--fill-points", type=int, default=None,
+                    help="serving: admit while the admitted solves hold fewer grid points than this")
+    ap.add_argument("--serving-requests", type=int, default=40,
+                    help="requests of the serving leg of the default bench line (0: no serving leg)")
     return ap.parse_args()
 
 
@@ -78,29 +82,67 @@ def workload_config(w, name):
 # clocks during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons of the bench's GPU while the timed
+    region runs: every 20 ms from a thread through NVML (read-only queries)
+    where its Python binding is installed, else nvidia-smi's query loop every
+    50 ms.  The GPU is found by its PCI address, so that the sample is of the
+    device torch uses whatever CUDA_VISIBLE_DEVICES holds."""
+    PERIOD = 0.02
 
     def __init__(self, device_index):
         self.dev = device_index
+        self.rows = []
+        self.h = None
+        self.thread = None
         self.proc = None
-        self.path = None
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def _bus(self):
+        import torch
+        pr = torch.cuda.get_device_properties(self.dev)
+        return f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
 
     def start(self):
+        import threading
+        self.proc = None
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
-                                         stderr=subprocess.DEVNULL)
+            import pynvml
+            pynvml.nvmlInit()
+            self.h = pynvml.nvmlDeviceGetHandleByPciBusId(self._bus())
+            self.smax = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
         except Exception:
-            self.proc = None
+            # no NVML binding: nvidia-smi's query loop (50 ms) on the same GPU
+            self.h = None
+            try:
+                fd, self.path = tempfile.mkstemp(suffix=".csv")
+                os.close(fd)
+                self.f = open(self.path, "w")
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", self._bus(), f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                                             stderr=subprocess.DEVNULL)
+            except Exception:
+                self.proc = None
+            return
+        self.stop_flag = threading.Event()
 
-    def stop(self):
-        if self.proc is None:
-            return None
+        def run():
+            import pynvml
+            while True:
+                try:
+                    sm = pynvml.nvmlDeviceGetClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+                    rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                    self.rows.append((sm, rs))
+                except Exception:
+                    pass
+                if self.stop_flag.wait(self.PERIOD):
+                    break
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+
+    def _stop_smi(self):
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -110,17 +152,34 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 6 and parts[0].replace(".", "").isdigit():
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(float(r[0]) for r in rows), "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi, 50 ms"}
+
+    def stop(self):
+        if self.proc is not None:
+            return self._stop_smi()
+        if self.h is None or self.thread is None:
+            return None
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        import pynvml
+        if not self.rows:
+            return None
+        bits = {"hw_slowdown": pynvml.nvmlClocksEventReasonHwSlowdown,
+                "hw_thermal_slowdown": pynvml.nvmlClocksEventReasonHwThermalSlowdown,
+                "sw_thermal_slowdown": pynvml.nvmlClocksEventReasonSwThermalSlowdown,
+                "sw_power_cap": pynvml.nvmlClocksEventReasonSwPowerCap}
+        reasons = sorted({k for _, rs in self.rows for k, b in bits.items() if rs & b})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": self.smax,
+                "reasons": reasons, "samples": len(self.rows), "source": "NVML, 20 ms"}
 
 
 # --------------------------------------------------------------------------
@@ -459,6 +518,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
 
+    # the metric's latency half: a short seeded serving stream, both arms
+    # (one GPU; rank 0 of a single-process run)
+    g.close()
+    serving = None
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        serving = serving_leg(args.serving_requests, args.ksteps, args.fill_points)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -466,37 +532,47 @@ def run_ours(args):
                 "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}",
                                **({"medium": "mu = 0 (acoustic ablation, lambda + 2 mu kept)"} if args.mu0 else {})),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-                "kernels": kernels, "clocks": clk}
+                "kernels": kernels, "clocks": clk, "serving": serving}
         print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_serving(args):
+SERVE_KW = dict(rate=40.0, seed=5, n_range=(96, 320), n_step=8, steps_range=(800, 2500), L_range=(64, 512))
+SERVE_BUDGET = 120 * 10 ** 9
+SERVE_SLOTS = 32
+
+
+def serving_leg(requests, ksteps, fill_points=None):
     """Serving workload: Poisson arrivals at 40 req/s, cubic grids of side 96..320
     (multiples of 8), dx 0.4 mm, 10-cell C-PML, 800..2500 steps, 64..512
     hemisphere receivers, forward/adjoint 50/50, 120 GB HBM budget, 32 slots.
     The same requests are served (a) with continuous batching through
-    pact_advance and (b) one at a time with pact_forward / pact_adjoint."""
+    pact_advance and (b) one at a time with pact_forward / pact_adjoint, in
+    real time on this GPU; returns both arms' statistics and their ratios."""
+    from paper_1709_02733_b300 import serving
+    cache = serving.InputCache()
+    cont = serving.run_continuous(serving.make_stream(requests, **SERVE_KW), SERVE_BUDGET, ksteps=ksteps,
+                                  max_slots=SERVE_SLOTS, cache=cache, realtime=True, fill_points=fill_points)
+    solo = serving.run_one_at_a_time(serving.make_stream(requests, **SERVE_KW), cache=cache, realtime=True)
+    return {"workload": f"serving stream: {requests} seeded Poisson requests at 40 req/s, sides 96..320 step 8, "
+                        "800..2500 steps, 64..512 receivers, fwd/adj 50/50, 120 GB budget, 32 slots",
+            "ksteps": ksteps, "fill_points": fill_points, "continuous": cont, "one_at_a_time": solo,
+            "throughput_ratio": cont["updates_per_s"] / solo["updates_per_s"],
+            "p50_ratio": cont["p50_s"] / solo["p50_s"], "p99_ratio": cont["p99_s"] / solo["p99_s"]}
+
+
+def run_serving(args):
+    """The serving workload alone (serving_leg), as its own JSON line."""
     import torch
     from paper_1709_02733_b300 import build as pbuild
-    from paper_1709_02733_b300 import serving
     pbuild.build()
     torch.cuda.set_device(0)
-    kw = dict(rate=40.0, seed=5, n_range=(96, 320), n_step=8, steps_range=(800, 2500), L_range=(64, 512))
-    cache = serving.InputCache()
-    cont = serving.run_continuous(serving.make_stream(args.requests, **kw), 120 * 10 ** 9, ksteps=args.ksteps,
-                                  max_slots=32, cache=cache, realtime=True)
-    solo = serving.run_one_at_a_time(serving.make_stream(args.requests, **kw), cache=cache, realtime=True)
-    line = {"metric": "served p50/p99 latency beside throughput", "value": cont["p99_s"], "unit": "s (p99)",
-            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serving stream: {args.requests} seeded Poisson requests at 40 req/s, "
-                                   "sides 96..320 step 8, 800..2500 steps, 64..512 receivers, fwd/adj 50/50, "
-                                   "120 GB budget, 32 slots", "ksteps": args.ksteps},
-            "continuous": cont, "one_at_a_time": solo,
-            "throughput_ratio": cont["updates_per_s"] / solo["updates_per_s"],
-            "p99_ratio": cont["p99_s"] / solo["p99_s"]}
+    sv = serving_leg(args.requests, args.ksteps, args.fill_points)
+    line = {"metric": "served p50/p99 latency beside throughput", "value": sv["continuous"]["p99_s"],
+            "unit": "s (p99)", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": sv["workload"], "ksteps": args.ksteps, "fill_points": args.fill_points}}
+    line.update({k: sv[k] for k in ("continuous", "one_at_a_time", "throughput_ratio", "p50_ratio", "p99_ratio")})
     print(json.dumps(line), flush=True)
 
 

@@ -103,8 +103,30 @@ struct pact_grid {
     // the C-PML frame launches overlap the interior launches on this stream
     cudaStream_t aux = nullptr, aux2 = nullptr;   // frame edges / frame corners
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    // medium-adaptive step: four more streams, one per work list
+    // (PACT_LISTSTREAMS=0 keeps the lists on the three streams above)
+    cudaStream_t xs[4] = {};
+    cudaEvent_t xj[4] = {};
+    bool list_streams = false;
+    // CUDA graphs of whole steps for pact_forward / pact_adjoint (two-pass
+    // TMA-staged path, profiling off): graphs[adjoint][0] one step,
+    // graphs[adjoint][1] kGraphSteps steps, captured on `cap` after one step
+    // launched directly (which builds every launch plan the capture uses);
+    // their receiver kernels read the solve from solve_dev.  Dropped when the
+    // medium changes (the launch lists depend on it).
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;
+        long long launches[PACT_NKIND] = {};
+    };
+    StepGraph graphs[2][2];
+    bool graph_warm[2] = {false, false};
+    bool graph_off = false;  // a capture failed: launch directly
+    SolveState* solve_dev = nullptr;
+    cudaStream_t cap = nullptr;
     // serving state (pact_begin / pact_advance / pact_poll)
     bool sv_active = false;
+    bool sv_solo = false;  // advanced by its own step graphs, not the multi-instance kernels
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
     const float* sv_in = nullptr;
     float* sv_out = nullptr;
@@ -394,25 +416,26 @@ static int step_mode(pact_handle h) {
     return h->fused ? STEP_FUSED : (h->acoustic ? STEP_ACOUSTIC : (h->mixed ? STEP_MIXED : STEP_TWO_PASS));
 }
 
-static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj) {
+static void tiled_step(pact_handle h, const StepParams& p, int c, bool adj, cudaStream_t st) {
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
     const bool fz = h->fused;
     const int mode = step_mode(h);
     const TmaSet& tm = fz ? h->tmp[c] : h->tm;
-    const SplitStreams ss{h->stream, fz ? nullptr : h->aux, h->ev_fork, h->ev_join, fz ? nullptr : h->aux2, h->ev_join2};
+    const SplitStreams ss{st,          fz ? nullptr : h->aux, h->ev_fork, h->ev_join, fz ? nullptr : h->aux2,
+                          h->ev_join2, h->list_streams ? h->xs : nullptr, h->xj};
     const MixedPlan* mp = h->mixed ? &h->mixed_plan : nullptr;
     mark(h, adj ? PACT_K_ADJ_A : PACT_K_FWD_VELOCITY, launch_vel_tiled(adj, p, tm, err, ss, mode, mp));
     if (h->acoustic)
-        mark(h, adj ? PACT_K_ADJ_AC_A : PACT_K_FWD_AC_VEL, launch_acoustic_step(false, adj, p, tm, err, h->stream));
-    if (fz) mark(h, adj ? PACT_K_ADJ_FUSED : PACT_K_FWD_FUSED, launch_fused_step(adj, p, h->fmp[c], err, h->stream));
+        mark(h, adj ? PACT_K_ADJ_AC_A : PACT_K_FWD_AC_VEL, launch_acoustic_step(false, adj, p, tm, err, st));
+    if (fz) mark(h, adj ? PACT_K_ADJ_FUSED : PACT_K_FWD_FUSED, launch_fused_step(adj, p, h->fmp[c], err, st));
     mark(h, adj ? PACT_K_ADJ_B : PACT_K_FWD_STRESS, launch_str_tiled(adj, p, tm, err, ss, mode, mp));
     if (h->acoustic)
-        mark(h, adj ? PACT_K_ADJ_AC_B : PACT_K_FWD_AC_STR, launch_acoustic_step(true, adj, p, tm, err, h->stream));
+        mark(h, adj ? PACT_K_ADJ_AC_B : PACT_K_FWD_AC_STR, launch_acoustic_step(true, adj, p, tm, err, st));
 }
 
 static void fwd_step(pact_handle h, const StepParams& p, int c) {
     if (h->tiled) {
-        tiled_step(h, p, c, false);
+        tiled_step(h, p, c, false, h->stream);
     } else {
         launch_fwd_velocity(p, h->stream);
         mark(h, PACT_K_FWD_VELOCITY);
@@ -423,7 +446,7 @@ static void fwd_step(pact_handle h, const StepParams& p, int c) {
 
 static void adj_step(pact_handle h, const StepParams& p, int c) {
     if (h->tiled) {
-        tiled_step(h, p, c, true);
+        tiled_step(h, p, c, true, h->stream);
     } else {
         launch_adj_a(p, h->stream);
         mark(h, PACT_K_ADJ_A);
@@ -467,6 +490,100 @@ static unsigned long long* band_counter(pact_handle h) {
     return reinterpret_cast<unsigned long long*>(h->scratch_u32 + 6);
 }
 
+// ---- CUDA graphs of whole steps ---------------------------------------------
+constexpr int kGraphSteps = 16;
+// grids of at least this many points fill the device alone: pact_advance
+// steps them on their own kernels (at 224^3 both ways ran alike on B300)
+constexpr long long kSoloPoints = 200LL * 200 * 200;
+
+static void drop_graphs(pact_handle h) {
+    for (auto& dir : h->graphs)
+        for (auto& g : dir) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = pact_grid::StepGraph{};
+        }
+    h->graph_warm[0] = h->graph_warm[1] = false;
+    h->graph_off = false;
+}
+
+static bool graphs_apply(pact_handle h) {
+    const char* genv = getenv("PACT_GRAPHS");
+    return h->tiled && !h->fused && !h->prof && h->cap && !(genv && std::strcmp(genv, "0") == 0);
+}
+
+// one step of the solve in h->solve_dev on stream st: the step kernels, then
+// the receiver kernel that reads the step count from the device
+static void state_step(pact_handle h, bool adj, cudaStream_t st) {
+    const StepParams p = make_params(h, 0);
+    tiled_step(h, p, 0, adj, st);
+    if (!adj) {
+        launch_sample_state(p, h->solve_dev, st);
+        mark(h, PACT_K_SAMPLE);
+    } else {
+        launch_inject_state(p, h->solve_dev, st);
+        mark(h, PACT_K_INJECT);
+    }
+}
+
+// Capture (once) and launch on st the graph of `steps` steps (1 or kGraphSteps).
+static int launch_step_graph(pact_handle h, bool adj, int steps, cudaStream_t st) {
+    pact_grid::StepGraph& g = h->graphs[adj ? 1 : 0][steps == 1 ? 0 : 1];
+    if (!g.exec) {
+        // the capture only records launches: keep the launch counts of one
+        // replay, and count them at each launch below
+        long long l0[PACT_NKIND];
+        std::memcpy(l0, h->launches, sizeof l0);
+        const long long k0 = h->kernels;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < steps; ++k) state_step(h, adj, h->cap);
+            e = cudaStreamEndCapture(h->cap, &graph);
+        }
+        for (int k = 0; k < PACT_NKIND; ++k) {
+            g.launches[k] = h->launches[k] - l0[k];
+            h->launches[k] = l0[k];
+        }
+        g.kernels = h->kernels - k0;
+        h->kernels = k0;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            // not capturable here: this handle launches its steps directly
+            g.exec = nullptr;
+            cudaGetLastError();
+            h->graph_off = true;
+            return PACT_OK;
+        }
+    }
+    CK(h, cudaGraphLaunch(g.exec, st));
+    for (int k = 0; k < PACT_NKIND; ++k) h->launches[k] += g.launches[k];
+    h->kernels += g.kernels;
+    return PACT_OK;
+}
+
+// Steps 1..nsteps of the solve set up in h->solve_dev: the first solve of a
+// handle and direction runs its first step directly, later steps replay the
+// graphs (kGraphSteps at a time, the rest one at a time).
+static int graph_steps(pact_handle h, bool adj, int nsteps, cudaStream_t st) {
+    int m = 0;
+    if (nsteps > 0 && !h->graph_warm[adj ? 1 : 0]) {
+        state_step(h, adj, st);
+        CK(h, cudaGetLastError());
+        h->graph_warm[adj ? 1 : 0] = true;
+        m = 1;
+    }
+    int rc = PACT_OK;
+    while (rc == PACT_OK && m < nsteps && !h->graph_off && graphs_apply(h)) {
+        const int k = nsteps - m >= kGraphSteps ? kGraphSteps : 1;
+        rc = launch_step_graph(h, adj, k, st);
+        if (!h->graph_off) m += k;
+    }
+    for (; rc == PACT_OK && m < nsteps; ++m) state_step(h, adj, st);
+    if (rc == PACT_OK) CK(h, cudaGetLastError());
+    return rc;
+}
+
 static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps) {
     int rc = ensure_pingpong(h);
     if (rc) return rc;
@@ -481,6 +598,15 @@ static int run_forward(pact_handle h, const float* p0, float* traces, int nsteps
     mark(h, PACT_K_SOURCE);
     launch_sample(p, r, traces, h->stream);
     mark(h, PACT_K_SAMPLE);
+    if (graphs_apply(h)) {
+        const SolveState v{0, 0u, nsteps, r, traces, nullptr};
+        launch_set_state(h->solve_dev, v, h->stream);
+        rc = graph_steps(h, false, nsteps, h->stream);
+        if (rc) return rc;
+        h->cur = 0;
+        CK(h, cudaGetLastError());
+        return PACT_OK;
+    }
     int c = 0;
     for (int m = 1; m <= nsteps; ++m) {
         const int out = h->fused ? 1 - c : -1;
@@ -506,6 +632,17 @@ static int run_adjoint(pact_handle h, const float* traces, float* image, int nst
     mark(h, -1);
     launch_inject(p, r, traces + (size_t)nsteps * h->L, h->stream);
     mark(h, PACT_K_INJECT, r.ncorner > 0);
+    if (graphs_apply(h)) {
+        const SolveState v{0, 0u, nsteps, r, nullptr, traces};
+        launch_set_state(h->solve_dev, v, h->stream);
+        rc = graph_steps(h, true, nsteps, h->stream);
+        if (rc) return rc;
+        launch_readout(image, p, h->stream);
+        mark(h, PACT_K_READOUT);
+        h->cur = 0;
+        CK(h, cudaGetLastError());
+        return PACT_OK;
+    }
     int c = 0;
     for (int m = nsteps; m >= 1; --m) {
         const int out = h->fused ? 1 - c : -1;
@@ -561,6 +698,8 @@ static int create_handle(const pact_grid_desc* desc, int z0g, int nzg, void* str
     if (e == cudaSuccess) e = cudaMalloc(&h->medium, 5 * h->N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->tables, 18 * (size_t)h->nmax * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->scratch_u32, 8 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->solve_dev, sizeof(SolveState));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         h->slab_n[a] = slab_points(*desc, a);
         if (h->slab_n[a]) e = cudaMalloc(&h->slabs[a], 6 * h->slab_n[a] * sizeof(float));
@@ -619,6 +758,16 @@ static int create_handle(const pact_grid_desc* desc, int z0g, int nzg, void* str
                 h->err = "creating the frame stream and its events failed";
                 return bail(PACT_ECUDA);
             }
+            const char* lenv = getenv("PACT_LISTSTREAMS");
+            if (!(lenv && std::strcmp(lenv, "0") == 0)) {
+                for (int k = 0; k < 4; ++k)
+                    if (cudaStreamCreateWithFlags(&h->xs[k], cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->xj[k], cudaEventDisableTiming) != cudaSuccess) {
+                        h->err = "creating the work-list streams failed";
+                        return bail(PACT_ECUDA);
+                    }
+                h->list_streams = true;
+            }
         }
     }
     *out = h;
@@ -653,6 +802,8 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     CK(h, cudaSetDevice(h->device));
     const size_t N = h->N;
     cudaStream_t s = h->stream;
+    CK(h, cudaStreamSynchronize(s));
+    drop_graphs(h);
     CK(h, cudaMemcpyAsync(h->medium, rho, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemcpyAsync(h->medium + N, lambda, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(h, cudaMemcpyAsync(h->medium + 2 * N, mu, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -773,11 +924,14 @@ int pact_destroy(pact_handle h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->fields);
-free_mixed_plan(&h->mixed_plan);
+    free_mixed_plan(&h->mixed_plan);
     cudaFree(h->fields2);
     cudaFree(h->medium);
     cudaFree(h->tables);
     cudaFree(h->scratch_u32);
+    drop_graphs(h);
+    cudaFree(h->solve_dev);
+    if (h->cap) cudaStreamDestroy(h->cap);
     for (int a = 0; a < 3; ++a) cudaFree(h->slabs[a]);
     free_rec(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -786,6 +940,10 @@ free_mixed_plan(&h->mixed_plan);
     if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
+    for (int k = 0; k < 4; ++k) {
+        if (h->xs[k]) cudaStreamDestroy(h->xs[k]);
+        if (h->xj[k]) cudaEventDestroy(h->xj[k]);
+    }
     cudaFree(h->stage_a);
     cudaFree(h->stage_b);
     delete h;
@@ -927,6 +1085,17 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         h->sv_fl = h->sv_ac;
         h->sv_nac = h->sv_nfl = 0;
     }
+    // a grid large enough to fill the device alone advances on its own step
+    // kernels (faster there than the multi-instance ones); the solve's state
+    // then lives in solve_dev.  PACT_SERVE_SOLO_POINTS overrides the size
+    // (a negative value sends every solve to the multi-instance kernels).
+    long long solo_points = kSoloPoints;
+    if (const char* senv = getenv("PACT_SERVE_SOLO_POINTS")) solo_points = std::atoll(senv);
+    h->sv_solo = h->tiled && !h->fused && solo_points >= 0 && (long long)h->N >= solo_points;
+    if (h->sv_solo) {
+        const SolveState v{0, 0u, nsteps, r, is_adjoint ? nullptr : out, is_adjoint ? in : nullptr};
+        launch_set_state(h->solve_dev, v, h->stream);
+    }
     h->sv_active = nsteps > 0;
     CK(h, cudaGetLastError());
     return PACT_OK;
@@ -948,6 +1117,10 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             if (!h) return fail(nullptr, PACT_EINVAL, "pact_advance: NULL handle");
             if (!h->sv_active || h->sv_adj != pass) continue;
             if (dev < 0) dev = h->device;
+            if (h->sv_solo) {
+                if (h->device != dev) return fail(h, PACT_EINVAL, "pact_advance: handles on different devices");
+                continue;
+            }
             if (h->device != dev) return fail(h, PACT_EINVAL, "pact_advance: handles on different devices");
             InstDev& e = T->inst[ni];
             e.tm = h->tm;
@@ -974,12 +1147,20 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
         if (pass == 0) T->n_fwd = ni;
     }
     T->n_inst = ni;
-    if (ni == 0) return PACT_OK;
+    if (dev < 0) return PACT_OK;
     if (cudaSetDevice(dev) != cudaSuccess) return fail(nullptr, PACT_ECUDA, "cudaSetDevice failed");
     std::string why;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = serve_run(*T, ksteps, st, why);
-    if (rc) return fail(nullptr, rc, why);
+    if (ni > 0) {
+        const int rc = serve_run(*T, ksteps, st, why);
+        if (rc) return fail(nullptr, rc, why);
+    }
+    for (int k = 0; k < n; ++k) {
+        pact_handle h = hs[k];
+        if (!h->sv_active || !h->sv_solo) continue;
+        const int rc = graph_steps(h, h->sv_adj != 0, std::min(ksteps, h->sv_nsteps - h->sv_m), st);
+        if (rc) return rc;
+    }
     for (int k = 0; k < n; ++k) {
         pact_handle h = hs[k];
         if (!h->sv_active) continue;
@@ -1006,7 +1187,8 @@ int pact_step_half(pact_handle h, int stress) {
     const bool adj = h->sv_adj != 0, str = stress != 0;
     const StepParams p = make_params(h);
     int* err = reinterpret_cast<int*>(h->scratch_u32 + 3);
-    const SplitStreams ss{h->stream, h->aux, h->ev_fork, h->ev_join, h->aux2, h->ev_join2};
+    const SplitStreams ss{h->stream,   h->aux, h->ev_fork, h->ev_join, h->aux2,
+                          h->ev_join2, h->list_streams ? h->xs : nullptr, h->xj};
     const MixedPlan* mp = h->mixed ? &h->mixed_plan : nullptr;
     const int mode = step_mode(h);
     if (!str) {

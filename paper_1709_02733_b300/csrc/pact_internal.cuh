@@ -143,3 +143,20 @@ struct RecTable {
     const int* inj_rec;     // [8L] receiver of each contribution
     const float* inj_w;     // [8L] weight of each contribution
 };
+
+// A solve advanced by CUDA graphs of whole steps: the graph's receiver
+// kernels take the step count, the trace buffers and the receiver table from
+// here, so that one captured graph serves every solve of its handle.  The
+// last block of each receiver launch advances m.
+struct SolveState {
+    int m;                 // steps done
+    unsigned int done;     // blocks of the running receiver launch that finished
+    int nsteps;
+    RecTable r;
+    float* out;            // forward: traces, (nsteps+1) x L
+    const float* in;       // adjoint: traces, (nsteps+1) x L
+};
+void launch_set_state(SolveState* st, const SolveState& v, cudaStream_t stream);
+// Theta row m+1 (forward) / Theta^T row nsteps-(m+1) (adjoint), then m += 1
+void launch_sample_state(const StepParams& p, SolveState* st, cudaStream_t stream);
+void launch_inject_state(const StepParams& p, SolveState* st, cudaStream_t stream);

@@ -374,6 +374,64 @@ __global__ void k_inject(float* s0, float* s1, float* s2, const float* __restric
     s2[q] -= acc;
 }
 
+// ---- receivers of a graph-launched solve (state in device memory) ----------
+// Fixed grids with grid-stride loops: the captured launch serves any L.
+constexpr int kRecBlocks = 16, kRecThreads = 256;
+
+// After every thread of the launch has read st->m: the last block to finish
+// advances the step count for the next step's launch.
+__device__ __forceinline__ void step_done(SolveState* st) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        st->done = 0;
+        st->m = st->m + 1;
+        __threadfence();
+    }
+}
+
+__global__ void k_set_state(SolveState* st, SolveState v) { *st = v; }
+
+__global__ void k_sample_state(const float* __restrict__ s0, const float* __restrict__ s1,
+                               const float* __restrict__ s2, SolveState* st) {
+    const int m = *(volatile int*)&st->m;
+    const RecTable r = st->r;
+    float* out = st->out + (size_t)(m + 1) * r.L;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < r.L; l += gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int q = __ldg(r.corner + 8 * l + c);
+            acc += __ldg(r.weight + 8 * l + c) * (__ldg(s0 + q) + __ldg(s1 + q) + __ldg(s2 + q));
+        }
+        out[l] = -acc;
+    }
+    step_done(st);
+}
+
+__global__ void k_inject_state(float* s0, float* s1, float* s2, const float* __restrict__ lam,
+                               const float* __restrict__ mu, SolveState* st) {
+    const int m = *(volatile int*)&st->m;
+    const RecTable r = st->r;
+    const float* ph = st->in + (size_t)(st->nsteps - (m + 1)) * r.L;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < r.ncorner; c += gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int e = __ldg(r.inj_off + c); e < __ldg(r.inj_off + c + 1); ++e)
+            acc += __ldg(r.inj_w + e) * __ldg(ph + __ldg(r.inj_rec + e));
+        const int q = __ldg(r.inj_point + c);
+        acc *= 3.0f * __ldg(lam + q) + 2.0f * __ldg(mu + q);
+        s0[q] -= acc;
+        s1[q] -= acc;
+        s2[q] -= acc;
+    }
+    step_done(st);
+}
+
 // 1/mu for the TMA-staged kernels (+inf at fluid nodes, where mu = 0)
 __global__ void k_inv_mu(const float* __restrict__ mu, float* inv, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -464,6 +522,18 @@ void launch_sample(const StepParams& p, const RecTable& r, float* out, cudaStrea
 
 void launch_inject(const StepParams& p, const RecTable& r, const float* ph, cudaStream_t st) {
     if (r.ncorner > 0) k_inject<<<(r.ncorner + 127) / 128, 128, 0, st>>>(p.s[0], p.s[1], p.s[2], p.lam, p.mu, r, ph);
+}
+
+void launch_set_state(SolveState* st, const SolveState& v, cudaStream_t stream) {
+    k_set_state<<<1, 1, 0, stream>>>(st, v);
+}
+
+void launch_sample_state(const StepParams& p, SolveState* st, cudaStream_t stream) {
+    k_sample_state<<<kRecBlocks, kRecThreads, 0, stream>>>(p.s[0], p.s[1], p.s[2], st);
+}
+
+void launch_inject_state(const StepParams& p, SolveState* st, cudaStream_t stream) {
+    k_inject_state<<<kRecBlocks, kRecThreads, 0, stream>>>(p.s[0], p.s[1], p.s[2], p.lam, p.mu, st);
 }
 
 void launch_inv_mu(const float* mu, float* inv, size_t n, cudaStream_t st) {

@@ -1048,22 +1048,51 @@ static int launch_mixed_half(const StepParams& p, const TmaSet& tm, int* err, co
     plan_for((STR ? 2 : 0) + (ADJ ? 1 : 0), p, STEP_TWO_PASS);
     const dim3 blk(TX, TY, 1);
     const int* nb = mp.blocks;
+    // a stream for each list: with the four extra streams every list runs on
+    // its own (in a captured step they become parallel branches of the
+    // graph); otherwise the frame lists share aux / aux2 and the interior
+    // lists the main stream.  The lists of a half write disjoint points and
+    // read only the other family, so any order among them is correct.
+    cudaStream_t sl[MX_N];
+    for (int l = 0; l < MX_N; ++l) sl[l] = ss.st;
     const bool frame = nb[MX_EDGE_EL] || nb[MX_EDGE_FL] || nb[MX_CORNER_EL] || nb[MX_CORNER_FL];
     const bool inner = nb[MX_INT_EL] || nb[MX_INT_AC] || nb[MX_INT_FZ];
-    const bool split = ss.aux && frame && inner;
-    cudaStream_t se = ss.st, sc = ss.st;
-    const bool split2 = split && ss.aux2;
-    if (split) {
-        cudaEventRecord(ss.fork, ss.st);
-        cudaStreamWaitEvent(ss.aux, ss.fork, 0);
-        se = sc = ss.aux;
-        if (split2) {
-            cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
-            sc = ss.aux2;
+    cudaStream_t used[MX_N];
+    cudaEvent_t joins[MX_N];
+    int nused = 0;
+    if (ss.aux && ss.aux2 && ss.more) {
+        const cudaStream_t own[MX_N] = {ss.more[0], ss.st, ss.more[1], ss.aux, ss.more[2], ss.aux2, ss.more[3]};
+        const cudaEvent_t oj[MX_N] = {ss.more_join[0], nullptr, ss.more_join[1], ss.join, ss.more_join[2],
+                                      ss.join2, ss.more_join[3]};
+        static_assert(MX_INT_EL == 0 && MX_INT_AC == 1 && MX_INT_FZ == 2 && MX_EDGE_EL == 3 && MX_EDGE_FL == 4 &&
+                          MX_CORNER_EL == 5 && MX_CORNER_FL == 6,
+                      "list order");
+        int nonempty = 0;
+        for (int l = 0; l < MX_N; ++l) nonempty += nb[l] > 0;
+        if (nonempty > 1)
+            for (int l = 0; l < MX_N; ++l)
+                if (nb[l] && own[l] != ss.st) {
+                    sl[l] = own[l];
+                    used[nused] = own[l];
+                    joins[nused++] = oj[l];
+                }
+    } else if (ss.aux && frame && inner) {
+        sl[MX_EDGE_EL] = sl[MX_EDGE_FL] = sl[MX_CORNER_EL] = sl[MX_CORNER_FL] = ss.aux;
+        used[nused] = ss.aux;
+        joins[nused++] = ss.join;
+        if (ss.aux2) {
+            sl[MX_CORNER_EL] = sl[MX_CORNER_FL] = ss.aux2;
+            used[nused] = ss.aux2;
+            joins[nused++] = ss.join2;
         }
+    }
+    if (nused) {
+        cudaEventRecord(ss.fork, ss.st);
+        for (int k = 0; k < nused; ++k) cudaStreamWaitEvent(used[k], ss.fork, 0);
     }
     int n = 0;
     if (nb[MX_CORNER_EL]) {
+        const cudaStream_t sc = sl[MX_CORNER_EL];
         if (STR)
             k_str_tiled<ADJ, PM_FULL><<<nb[MX_CORNER_EL], blk, StrCfg<ADJ, PM_FULL>::SMEM, sc>>>(p, tm, mp.list[MX_CORNER_EL], err);
         else
@@ -1071,40 +1100,38 @@ static int launch_mixed_half(const StepParams& p, const TmaSet& tm, int* err, co
         ++n;
     }
     if (nb[MX_CORNER_FL]) {
-        launch_fluid(STR, ADJ, PM_FULL, p, tm, mp.list[MX_CORNER_FL], nb[MX_CORNER_FL], err, sc);
+        launch_fluid(STR, ADJ, PM_FULL, p, tm, mp.list[MX_CORNER_FL], nb[MX_CORNER_FL], err, sl[MX_CORNER_FL]);
         ++n;
     }
     if (nb[MX_EDGE_EL]) {
+        const cudaStream_t se = sl[MX_EDGE_EL];
         if (STR) k_str_tiled<ADJ, PM_X><<<nb[MX_EDGE_EL], blk, StrCfg<ADJ, PM_X>::SMEM, se>>>(p, tm, mp.list[MX_EDGE_EL], err);
         else k_vel_tiled<ADJ, PM_X><<<nb[MX_EDGE_EL], blk, VelCfg<ADJ, PM_X>::SMEM, se>>>(p, tm, mp.list[MX_EDGE_EL], err);
         ++n;
     }
     if (nb[MX_EDGE_FL]) {
-        launch_fluid(STR, ADJ, PM_X, p, tm, mp.list[MX_EDGE_FL], nb[MX_EDGE_FL], err, se);
+        launch_fluid(STR, ADJ, PM_X, p, tm, mp.list[MX_EDGE_FL], nb[MX_EDGE_FL], err, sl[MX_EDGE_FL]);
         ++n;
     }
     if (nb[MX_INT_EL]) {
+        const cudaStream_t si = sl[MX_INT_EL];
         if (STR)
-            k_str_tiled<ADJ, PM_NONE><<<nb[MX_INT_EL], blk, StrCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, mp.list[MX_INT_EL], err);
+            k_str_tiled<ADJ, PM_NONE><<<nb[MX_INT_EL], blk, StrCfg<ADJ, PM_NONE>::SMEM, si>>>(p, tm, mp.list[MX_INT_EL], err);
         else
-            k_vel_tiled<ADJ, PM_NONE><<<nb[MX_INT_EL], blk, VelCfg<ADJ, PM_NONE>::SMEM, ss.st>>>(p, tm, mp.list[MX_INT_EL], err);
+            k_vel_tiled<ADJ, PM_NONE><<<nb[MX_INT_EL], blk, VelCfg<ADJ, PM_NONE>::SMEM, si>>>(p, tm, mp.list[MX_INT_EL], err);
         ++n;
     }
     if (nb[MX_INT_FZ]) {
-        launch_fluid(STR, ADJ, PM_Z, p, tm, mp.list[MX_INT_FZ], nb[MX_INT_FZ], err, ss.st);
+        launch_fluid(STR, ADJ, PM_Z, p, tm, mp.list[MX_INT_FZ], nb[MX_INT_FZ], err, sl[MX_INT_FZ]);
         ++n;
     }
     if (nb[MX_INT_AC]) {
-        launch_acoustic(STR, ADJ, p, tm, mp.list[MX_INT_AC], nb[MX_INT_AC], err, ss.st);
+        launch_acoustic(STR, ADJ, p, tm, mp.list[MX_INT_AC], nb[MX_INT_AC], err, sl[MX_INT_AC]);
         ++n;
     }
-    if (split) {
-        cudaEventRecord(ss.join, ss.aux);
-        cudaStreamWaitEvent(ss.st, ss.join, 0);
-        if (split2) {
-            cudaEventRecord(ss.join2, ss.aux2);
-            cudaStreamWaitEvent(ss.st, ss.join2, 0);
-        }
+    for (int k = 0; k < nused; ++k) {
+        cudaEventRecord(joins[k], used[k]);
+        cudaStreamWaitEvent(ss.st, joins[k], 0);
     }
     return n;
 }
@@ -1330,7 +1357,15 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
         const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);
         pts[li] += (long long)ex * ey * (b - a);
     };
-    constexpr int kChunk = 48;  // planes per work item at most
+    // planes per work item: 48 where the tiles alone give the device enough
+    // items; fewer (down to 8) on small grids, whose few blocks would
+    // otherwise march many planes one after another with most SMs idle
+    // (each block waits on its loads plane by plane)
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long want = 4L * sms;
+    const int kChunk = (int)std::min<long>(48, std::max<long>(8, (long)(zb - za) * ntiles / want));
     std::vector<int> cuts{0};
     if (za > 0) cuts.push_back(za);
     if (zb > za) {

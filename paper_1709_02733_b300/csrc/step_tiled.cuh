@@ -101,6 +101,10 @@ struct SplitStreams {
     cudaEvent_t fork, join;
     cudaStream_t aux2;           // optional: the corner launch runs here (join2 recorded after it)
     cudaEvent_t join2;
+    // optional (medium-adaptive step): four more streams, so that each of
+    // the seven work lists of a half step runs on a stream of its own
+    const cudaStream_t* more = nullptr;
+    const cudaEvent_t* more_join = nullptr;
 };
 // Step modes of the TMA-staged kernels:
 //   STEP_TWO_PASS  every tile runs the elastic velocity and stress kernels;

@@ -1,7 +1,8 @@
-"""Serving on the GPU: solves advanced together by the persistent
-multi-instance kernels give the same results as the same solves alone and as
-the FP64 oracle's H and H^T (Appendix A.3, Eqs. (HPML) and (AdjupPML)), and a
-queued stream served with continuous batching completes with correct results."""
+"""Serving on the GPU: solves advanced together by pact_advance (small grids
+on the persistent multi-instance kernels, large ones on their own step
+graphs) give the same results as the same solves alone and as the FP64
+oracle's H and H^T (Appendix A.3, Eqs. (HPML) and (AdjupPML)), and a queued
+stream served with continuous batching completes with correct results."""
 import numpy as np
 import pytest
 
@@ -88,14 +89,25 @@ def _serve_mix(cases, k=7):
     return served
 
 
-def test_mixed_solves_match_solo():
+# pact_advance steps grids of at least PACT_SERVE_SOLO_POINTS points on their
+# own step kernels and the rest on the multi-instance kernels: "150000" sends
+# four of the six cases to their own kernels and two to the multi-instance
+# ones, "-1" all to the multi-instance kernels
+SPLITS = [None, "150000", "-1"]
+
+
+@pytest.mark.parametrize("split", SPLITS)
+def test_mixed_solves_match_solo(split, monkeypatch):
+    if split is not None:
+        monkeypatch.setenv("PACT_SERVE_SOLO_POINTS", split)
     cases = _mix_cases()
     for (kind, *_rest), (_inp, got, ref) in zip(cases, _serve_mix(cases)):
         assert np.all(np.isfinite(got)), kind
         assert rel_l2(got, ref) <= TOL_MIX, kind
 
 
-def test_served_results_match_oracle():
+@pytest.mark.parametrize("split", SPLITS[1:])
+def test_served_results_match_oracle(split, monkeypatch):
     """Every solve of a served mix (forward and adjoint instances, on grids
     holding interior, z-slab, edge and corner work items) against the FP64
     oracle's H p0 / H^T y on the same inputs: this covers the persistent
@@ -103,6 +115,7 @@ def test_served_results_match_oracle():
     (sampling, and injection weighted by 3 lambda + 2 mu in the adjoint's
     variables)."""
     from oracle import Oracle
+    monkeypatch.setenv("PACT_SERVE_SOLO_POINTS", split)
     cases = _mix_cases()
     kinds = {c[0] for c in cases}
     assert kinds == {"fwd", "adj"}

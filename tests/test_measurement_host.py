@@ -92,17 +92,37 @@ class _Done:
 
 
 def test_clock_summary(tmp_path):
+    """nvidia-smi's query loop (no NVML binding): rows of SM clock, max clock
+    and the four reasons; rows without a clock reading are dropped."""
     s = bench.ClockSampler(0)
     s.path = str(tmp_path / "clk.csv")
     with open(s.path, "w") as f:
         for mhz, cap in ((2032, "Not Active"), (1995, "Active"), (2010, "Active"), ("[N/A]", "Not Active")):
-            f.write(f"0, {mhz}, 2032, 950.1, 0x4, Not Active, Not Active, Not Active, {cap}\n")
+            f.write(f"{mhz}, 2032, Not Active, Not Active, Not Active, {cap}\n")
     s.f = open(os.devnull, "w")
     s.proc = _Done()
     r = s.stop()
     assert r["sm_mhz"] == 2010.0 and r["sm_max_mhz"] == 2032.0
-    assert r["reasons"] == ["sw_power_cap"] and r["samples"] == 4
+    assert r["reasons"] == ["sw_power_cap"] and r["samples"] == 3
     assert not os.path.exists(s.path)
+
+
+def test_clock_summary_nvml():
+    """NVML samples: (SM clock, reason bit mask) pairs."""
+    pynvml = pytest.importorskip("pynvml")
+
+    class _Joined:
+        def join(self, timeout=None):
+            pass
+
+    import threading
+    s = bench.ClockSampler(0)
+    s.h, s.smax, s.thread, s.stop_flag = object(), 2032, _Joined(), threading.Event()
+    hw = pynvml.nvmlClocksEventReasonHwSlowdown
+    s.rows = [(2032, 0), (1900, hw), (2032, pynvml.nvmlClocksEventReasonGpuIdle)]
+    r = s.stop()
+    assert r["sm_mhz"] == 2032 and r["sm_max_mhz"] == 2032 and r["samples"] == 3
+    assert r["reasons"] == ["hw_slowdown"]
 
 
 def test_algorithmic_bytes_of_the_step():
