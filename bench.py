@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--ksteps", type=int, default=16)
     ap.add_argument("--fill-points", type=int, default=None,
                     help="serving: admit while the admitted solves hold fewer grid points than this")
+    ap.add_argument("--decomp", choices=["replicas", "slabs"], default="replicas",
+                    help="N > 1: independent solves per rank (replicas, weak scaling) or one solve split "
+                         "into z slabs over the ranks (strong scaling)")
     ap.add_argument("--serving-requests", type=int, default=40,
                     help="requests of the serving leg of the default bench line (0: no serving leg)")
     return ap.parse_args()
@@ -425,8 +428,10 @@ def run_ours(args):
     g.adjoint(wt, w.rec)
     torch.cuda.synchronize()
 
-    # timed region: H over K steps, then H^T over the K+1 samples
-    g.profile(True)
+    # timed region: H over K steps, then H^T over the K+1 samples, on the
+    # product path (pact_forward / pact_adjoint replaying their step graphs);
+    # pact_profile(False) only resets the launch counts
+    g.profile(False)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     barrier()
@@ -440,9 +445,19 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms, value = replica_rate(2.0 * d.N * K, e0.elapsed_time(e1), world, device="cuda")
+    gpu_launches = int(g.profile_read()["all"][0])  # kernel launches in the timed region
+    updates = 2.0 * d.N * K * world
+
+    # per-role device times from a second, profiled pass (events after every
+    # launch, so launched directly rather than from the step graphs) over
+    # Kp <= K steps; Kp takes the place of K in the per-launch figures below
+    Kp = min(K, 200)
+    g.profile(True)
+    g.forward(p0, w.rec, Kp, out=traces[:Kp + 1])
+    g.adjoint(traces[:Kp + 1], w.rec, out=image)
+    torch.cuda.synchronize()
     prof = g.profile_read()
     g.profile(False)
-    updates = 2.0 * d.N * K * world
 
     # roofline of the whole step pair (measured live over the timed region):
     # the compulsory bytes of the single-pass update (survey_bytes_per_step)
@@ -488,15 +503,14 @@ def run_ours(args):
                                    "achieved": dbytes / avg_s / 1e9, "frac": dbytes / avg_s / 1e9 / pk["hbm_gbs"],
                                    "grid_points_per_launch": role_points(dom),
                                    "design_bytes_per_update": dbytes / max(1, role_points(dom)),
-                                   "traffic": traffic_for(dom, wl)}
+                                   "traffic": traffic_for(dom, wl), "profiled_steps": Kp}
     # the bytes the library's kernels are designed to move, over the step's device time
     step_bytes = sum(role_bytes(k) * prof[k][0] for k in steps_kinds if prof[k][0])
     step_ms = sum(prof[k][1] for k in steps_kinds)
-    roofline["design"] = {"bytes_per_step_pair": step_bytes / K, "bytes_per_update": step_bytes / (2.0 * d.N * K),
+    roofline["design"] = {"bytes_per_step_pair": step_bytes / Kp, "bytes_per_update": step_bytes / (2.0 * d.N * Kp),
                           "achieved": step_bytes / (step_ms * 1e-3) / 1e9,
                           "frac": step_bytes / (step_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
     kernels = {k: {"invocations": v[0], "ms": v[1]} for k, v in prof.items() if v[0] and k != "all"}
-    gpu_launches = int(prof["all"][0])  # kernel launches in the timed region (a step half is 3 kernels)
 
     # end to end through the host-pointer C-ABI calls (pinned host buffers)
     e2e = None
@@ -576,10 +590,77 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_slabs(args):
+    """One solve of the workload split into z slabs over the WORLD_SIZE ranks
+    (slabs.py: halo planes exchanged over NCCL between the half steps), timed
+    like run_ours: K forward steps then K adjoint steps, max over ranks;
+    value = the whole grid's updates / that time (strong scaling)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_02733_b300 import build as pbuild
+    from paper_1709_02733_b300 import slabs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    w = make_workload(args.workload)
+    d = w.desc
+    K, W = args.steps, args.warmup
+    parts = slabs.partition(d.nz, world, d.npml)
+    s = slabs.make_slab(d, parts, rank, w.rec)
+    s.grid.set_medium(*[torch.from_numpy(np.ascontiguousarray(m[s.zl:s.zh])).cuda() for m in w.medium])
+    p0 = torch.from_numpy(np.ascontiguousarray(w.p0[s.zl:s.zh])).cuda()
+    y = torch.randn((K + 1, len(s.inj_idx)), device="cuda")
+    ex = slabs.DistExchange() if world > 1 else (lambda sl, f: None)
+    slabs.forward([s], [p0], W, ex)
+    slabs.adjoint([s], [y[:W + 1].contiguous()], W, ex)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    slabs.forward([s], [p0], K, ex)
+    slabs.adjoint([s], [y], K, ex)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks_of(e0.elapsed_time(e1), world, device="cuda")
+    value = 2.0 * d.N * K / (ms * 1e-3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded skull-like medium, vessel tubes, Fibonacci receivers)",
+                "config": dict(workload_config(w, args.workload), parallelism=f"z-slabs x{world}",
+                               slabs=[list(p) for p in parts]),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    s.grid.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.serving:
         run_serving(args)
+        return
+    if args.decomp == "slabs" and args.impl == "ours":
+        run_slabs(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -525,10 +525,11 @@ static void state_step(pact_handle h, bool adj, cudaStream_t st) {
     }
 }
 
-// Capture (once) and launch on st the graph of `steps` steps (1 or kGraphSteps).
-static int launch_step_graph(pact_handle h, bool adj, int steps, cudaStream_t st) {
+// Capture (once) the graph of `steps` steps (1 or kGraphSteps); a capture
+// that fails turns the graphs of this handle off (graph_off).
+static void ensure_step_graph(pact_handle h, bool adj, int steps) {
     pact_grid::StepGraph& g = h->graphs[adj ? 1 : 0][steps == 1 ? 0 : 1];
-    if (!g.exec) {
+    if (!g.exec && !h->graph_off) {
         // the capture only records launches: keep the launch counts of one
         // replay, and count them at each launch below
         long long l0[PACT_NKIND];
@@ -553,9 +554,15 @@ static int launch_step_graph(pact_handle h, bool adj, int steps, cudaStream_t st
             g.exec = nullptr;
             cudaGetLastError();
             h->graph_off = true;
-            return PACT_OK;
         }
     }
+}
+
+// Launch on st the graph of `steps` steps (captured first if need be).
+static int launch_step_graph(pact_handle h, bool adj, int steps, cudaStream_t st) {
+    ensure_step_graph(h, adj, steps);
+    if (h->graph_off) return PACT_OK;
+    const pact_grid::StepGraph& g = h->graphs[adj ? 1 : 0][steps == 1 ? 0 : 1];
     CK(h, cudaGraphLaunch(g.exec, st));
     for (int k = 0; k < PACT_NKIND; ++k) h->launches[k] += g.launches[k];
     h->kernels += g.kernels;
@@ -572,6 +579,12 @@ static int graph_steps(pact_handle h, bool adj, int nsteps, cudaStream_t st) {
         CK(h, cudaGetLastError());
         h->graph_warm[adj ? 1 : 0] = true;
         m = 1;
+        // both graphs now, whatever this solve's length: a capture only
+        // records launches, and later solves then start on graphs at once
+        if (graphs_apply(h)) {
+            ensure_step_graph(h, adj, 1);
+            ensure_step_graph(h, adj, kGraphSteps);
+        }
     }
     int rc = PACT_OK;
     while (rc == PACT_OK && m < nsteps && !h->graph_off && graphs_apply(h)) {
