@@ -200,26 +200,29 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
             if constexpr (ADJ && PXY) {
                 // F11 = Q + a (psi^xx + chi Q) in place at the x-band positions,
                 // F22 = Q + a (psi^yy + chi Q) in the extra box at the y-band ones
+                // (off the x layer F11 = Q, which the box holds already; both
+                // derivatives read the one Q box, so the y-band positions always
+                // get F22 in the extra box: the in-place F11 must not reach them)
                 float* E = der;
                 if (ok) {
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const unsigned char f = cross.f[k];
-                        if (!(f & CP_EXISTS)) continue;
                         const int q = cross.q[k];
-                        const float qv = sz[q];
-                        float f11 = qv, f22 = qv;
                         const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
+                        const float qv = sz[q];  // Q, read before F11 replaces it in place
                         if (LX && cpm.sx[k] >= 0) {
-                            const float* t = cxt + 4 * (q % BW);
-                            f11 += t[0] * (mv[0] + t[1] * qv);
+                            const float* t = cxt + cross.cx4[k];
+                            szw[q] = qv + t[0] * (mv[0] + t[1] * qv);
                         }
-                        if (LY && cpm.sy[k] >= 0) {
-                            const float* t = cyt + 4 * (q / BW);
-                            f22 += t[0] * (mv[YV * NCROSS] + t[1] * qv);
+                        if (f & CP_YB) {
+                            float f22 = qv;
+                            if (LY && cpm.sy[k] >= 0) {
+                                const float* t = cyt + cross.cy4[k];
+                                f22 += t[0] * (mv[YV * NCROSS] + t[1] * qv);
+                            }
+                            E[q] = f22;
                         }
-                        if (f & CP_YB) E[q] = f22;
-                        if (f & CP_XB) szw[q] = f11;
                     }
                 }
                 __syncthreads();
@@ -398,30 +401,33 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
             if constexpr (ADJ && PXY) {
                 // E11 = w1 + a (phi~xx + chi w1) in place at the x-band positions,
                 // E22 = w2 + a (phi~yy + chi w2) in the extra box at the y-band ones
+                // (off the x layer E11 = w1, which the box holds already;
+                // without a y layer E22 = w2 and the y derivative reads the box)
                 float* E0 = der;
                 if (ok) {
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const unsigned char f = cross.f[k];
-                        if (!(f & CP_EXISTS)) continue;
                         const int q = cross.q[k];
-                        const float wx = sz[q], wy = sz[BOXS + q];
-                        float exx = wx, eyy = wy;
                         const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
-                            const float* t = cxt + 4 * (q % BW);
-                            exx += t[2] * (mv[0] + t[3] * wx);
+                            const float wx = sz[q];
+                            const float* t = cxt + cross.cx4[k];
+                            szw[q] = wx + t[2] * (mv[0] + t[3] * wx);
                         }
-                        if (LY && cpm.sy[k] >= 0) {
-                            const float* t = cyt + 4 * (q / BW);
-                            eyy += t[2] * (mv[YV * NCROSS] + t[3] * wy);
+                        if (LY && (f & CP_YB)) {
+                            const float wy = sz[BOXS + q];
+                            float eyy = wy;
+                            if (cpm.sy[k] >= 0) {
+                                const float* t = cyt + cross.cy4[k];
+                                eyy += t[2] * (mv[YV * NCROSS] + t[3] * wy);
+                            }
+                            E0[q] = eyy;
                         }
-                        if (f & CP_XB) szw[q] = exx;
-                        if (f & CP_YB) E0[q] = eyy;
                     }
                 }
                 __syncthreads();
-                YD0 = E0;
+                if constexpr (LY) YD0 = E0;
             }
             if (ok && own) {
                 const float du[3] = {dmx(XD0, o) * h, dmy(YD0, o) * h, dq(qz) * h};

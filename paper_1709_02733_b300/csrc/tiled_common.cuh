@@ -156,6 +156,7 @@ constexpr unsigned char CP_EXISTS = 1, CP_IN = 2, CP_XB = 4, CP_YB = 8;
 struct CrossPos {
     int q[2];
     short dx[2], dy[2];
+    short cx4[2], cy4[2];  // offsets of the position's column / row in the coefficient tables
     unsigned char f[2];
 };
 
@@ -165,6 +166,7 @@ __device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0,
         const int i = tid + k * NT;
         c.q[k] = 0;
         c.dx[k] = c.dy[k] = 0;
+        c.cx4[k] = c.cy4[k] = 0;
         c.f[k] = 0;
         if (i >= NCROSS) continue;
         int bx, by;
@@ -184,6 +186,8 @@ __device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0,
         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
         const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         c.q[k] = by * BW + bx;
+        c.cx4[k] = (short)(4 * bx);
+        c.cy4[k] = (short)(4 * by);
         c.dx[k] = (gx + 1 < nx) ? 1 : 0;
         c.dy[k] = (gy + 1 < ny) ? BW : 0;
         c.f[k] = CP_EXISTS | (in ? CP_IN : 0) | (inx ? CP_XB : 0) | (iny ? CP_YB : 0);
