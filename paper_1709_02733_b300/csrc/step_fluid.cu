@@ -212,14 +212,14 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
                         const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         const float qv = sz[q];  // Q, read before F11 replaces it in place
                         if (LX && cpm.sx[k] >= 0) {
-                            const float* t = cxt + cross.cx4[k];
-                            szw[q] = qv + t[0] * (mv[0] + t[1] * qv);
+                            const float* t = cxt + cross.cxi[k];
+                            szw[q] = qv + t[0] * (mv[0] + t[BW] * qv);
                         }
                         if (f & CP_YB) {
                             float f22 = qv;
                             if (LY && cpm.sy[k] >= 0) {
-                                const float* t = cyt + cross.cy4[k];
-                                f22 += t[0] * (mv[YV * NCROSS] + t[1] * qv);
+                                const float* t = cyt + cross.cyi[k];
+                                f22 += t[0] * (mv[YV * NCROSS] + t[BH] * qv);
                             }
                             E[q] = f22;
                         }
@@ -412,15 +412,15 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
                         const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
                             const float wx = sz[q];
-                            const float* t = cxt + cross.cx4[k];
-                            szw[q] = wx + t[2] * (mv[0] + t[3] * wx);
+                            const float* t = cxt + cross.cxi[k];
+                            szw[q] = wx + t[2 * BW] * (mv[0] + t[3 * BW] * wx);
                         }
                         if (LY && (f & CP_YB)) {
                             const float wy = sz[BOXS + q];
                             float eyy = wy;
                             if (cpm.sy[k] >= 0) {
-                                const float* t = cyt + cross.cy4[k];
-                                eyy += t[2] * (mv[YV * NCROSS] + t[3] * wy);
+                                const float* t = cyt + cross.cyi[k];
+                                eyy += t[2 * BH] * (mv[YV * NCROSS] + t[3 * BH] * wy);
                             }
                             E0[q] = eyy;
                         }

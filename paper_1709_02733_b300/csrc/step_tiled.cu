@@ -246,16 +246,16 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
                         float f11 = q11, f21 = q12, f31 = q13, f22 = q22, f12 = q12, f32 = q23;
                         const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
-                            const float* t = cxt + cross.cx4[k];
-                            f11 += t[0] * (mv[0] + t[1] * q11);
-                            f21 += t[2] * (mv[NCROSS] + t[3] * q12);
-                            f31 += t[2] * (mv[2 * NCROSS] + t[3] * q13);
+                            const float* t = cxt + cross.cxi[k];
+                            f11 += t[0] * (mv[0] + t[BW] * q11);
+                            f21 += t[2 * BW] * (mv[NCROSS] + t[3 * BW] * q12);
+                            f31 += t[2 * BW] * (mv[2 * NCROSS] + t[3 * BW] * q13);
                         }
                         if (LY && cpm.sy[k] >= 0) {
-                            const float* t = cyt + cross.cy4[k];
-                            f22 += t[0] * (mv[YV * NCROSS] + t[1] * q22);
-                            f12 += t[2] * (mv[(YV + 1) * NCROSS] + t[3] * q12);
-                            f32 += t[2] * (mv[(YV + 2) * NCROSS] + t[3] * q23);
+                            const float* t = cyt + cross.cyi[k];
+                            f22 += t[0] * (mv[YV * NCROSS] + t[BH] * q22);
+                            f12 += t[2 * BH] * (mv[(YV + 1) * NCROSS] + t[3 * BH] * q12);
+                            f32 += t[2 * BH] * (mv[(YV + 2) * NCROSS] + t[3 * BH] * q23);
                         }
                         if (f & CP_XB) {
                             szw[q] = f11;
@@ -535,16 +535,16 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                         float exx = wx, eyx = wy, ezx = wz, eyy = wy, exy = wx, ezy = wz;
                         const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
-                            const float* t = cxt + cross.cx4[k];
-                            exx += t[2] * (mv[0] + t[3] * wx);
-                            eyx += t[0] * (mv[NCROSS] + t[1] * wy);
-                            ezx += t[0] * (mv[2 * NCROSS] + t[1] * wz);
+                            const float* t = cxt + cross.cxi[k];
+                            exx += t[2 * BW] * (mv[0] + t[3 * BW] * wx);
+                            eyx += t[0] * (mv[NCROSS] + t[BW] * wy);
+                            ezx += t[0] * (mv[2 * NCROSS] + t[BW] * wz);
                         }
                         if (LY && cpm.sy[k] >= 0) {
-                            const float* t = cyt + cross.cy4[k];
-                            eyy += t[2] * (mv[YV * NCROSS] + t[3] * wy);
-                            exy += t[0] * (mv[(YV + 1) * NCROSS] + t[1] * wx);
-                            ezy += t[0] * (mv[(YV + 2) * NCROSS] + t[1] * wz);
+                            const float* t = cyt + cross.cyi[k];
+                            eyy += t[2 * BH] * (mv[YV * NCROSS] + t[3 * BH] * wy);
+                            exy += t[0] * (mv[(YV + 1) * NCROSS] + t[BH] * wx);
+                            ezy += t[0] * (mv[(YV + 2) * NCROSS] + t[BH] * wz);
                         }
                         if (f & CP_XB) {
                             szw[q] = exx;

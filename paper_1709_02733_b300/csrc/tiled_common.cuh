@@ -156,7 +156,7 @@ constexpr unsigned char CP_EXISTS = 1, CP_IN = 2, CP_XB = 4, CP_YB = 8;
 struct CrossPos {
     int q[2];
     short dx[2], dy[2];
-    short cx4[2], cy4[2];  // offsets of the position's column / row in the coefficient tables
+    short cxi[2], cyi[2];  // the position's box column / row (index into the coefficient tables)
     unsigned char f[2];
 };
 
@@ -166,7 +166,7 @@ __device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0,
         const int i = tid + k * NT;
         c.q[k] = 0;
         c.dx[k] = c.dy[k] = 0;
-        c.cx4[k] = c.cy4[k] = 0;
+        c.cxi[k] = c.cyi[k] = 0;
         c.f[k] = 0;
         if (i >= NCROSS) continue;
         int bx, by;
@@ -186,8 +186,8 @@ __device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0,
         const int gx = x0 - 4 + bx, gy = y0 - 2 + by;
         const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         c.q[k] = by * BW + bx;
-        c.cx4[k] = (short)(4 * bx);
-        c.cy4[k] = (short)(4 * by);
+        c.cxi[k] = (short)bx;
+        c.cyi[k] = (short)by;
         c.dx[k] = (gx + 1 < nx) ? 1 : 0;
         c.dy[k] = (gy + 1 < ny) ? BW : 0;
         c.f[k] = CP_EXISTS | (in ? CP_IN : 0) | (inx ? CP_XB : 0) | (iny ? CP_YB : 0);
@@ -207,15 +207,19 @@ __device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy
                                                int x0, int y0, const StepParams& p) {
     const int W = 2 * p.P + 1;
     for (int i = tid; i < BW + BH; i += NT) {
-        float* t = i < BW ? cx + 4 * i : cy + 4 * (i - BW);
+        // one array per coefficient (stride W = BW or BH between them), so
+        // that a warp reading one coefficient of consecutive columns hits
+        // consecutive banks
         const int axis = i < BW ? 0 : 1;
+        const int W = axis == 0 ? BW : BH;
+        float* t = axis == 0 ? cx + i : cy + (i - BW);
         const int g = i < BW ? x0 - 4 + i : y0 - 2 + (i - BW);
         const int n = axis == 0 ? p.nx : p.ny;
         const bool in = g >= 0 && g < n && slab_local(g, n, p.P) >= 0;
-        t[0] = in ? __ldg(p.tab[axis][0][0] + g) : 0.f;  // a, integer lattice
-        t[1] = in ? __ldg(p.tab[axis][0][2] + g) : 0.f;  // chi, integer lattice
-        t[2] = in ? __ldg(p.tab[axis][1][0] + g) : 0.f;  // a, half lattice
-        t[3] = in ? __ldg(p.tab[axis][1][2] + g) : 0.f;  // chi, half lattice
+        t[0] = in ? __ldg(p.tab[axis][0][0] + g) : 0.f;      // a, integer lattice
+        t[W] = in ? __ldg(p.tab[axis][0][2] + g) : 0.f;      // chi, integer lattice
+        t[2 * W] = in ? __ldg(p.tab[axis][1][0] + g) : 0.f;  // a, half lattice
+        t[3 * W] = in ? __ldg(p.tab[axis][1][2] + g) : 0.f;  // chi, half lattice
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -230,8 +234,9 @@ __device__ __forceinline__ void cross_pml_init(CrossPml& c, float* cx, float* cy
     }
 }
 
-// Shared tables of the layer coefficients of the cross positions (per box
-// column: 4 floats, then per box row: 4 floats).  One allocation per kernel,
+// Shared tables of the layer coefficients of the cross positions (four
+// arrays of BW floats over the box columns, then four of BH over the rows:
+// a and chi on the integer lattice, a and chi on the half lattice).  One allocation per kernel,
 // shared by all its C-PML bodies (a block runs one body at a time), so that a
 // kernel that carries both edge bodies pays for the tables once.
 __device__ __forceinline__ float* frame_coef_tables() {
