@@ -64,9 +64,27 @@ const void* acoustic_fn(bool str, bool adj) {
                : (adj ? (const void*)k_ac_vel<true> : (const void*)k_ac_vel<false>);
 }
 
+// Shared memory first in the unified L1 / shared-memory array (the bodies
+// stage through TMA), so that it does not cap the blocks per SM below the
+// register limit; set once per device.
+static void prefer_shared_ac() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    for (int k = 0; k < 4; ++k)
+        cudaFuncSetAttribute(acoustic_fn(k & 2, k & 1), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_multi_ac<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_multi_ac<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_multi_ac<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_multi_ac<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    done[dev] = true;
+}
+
 void launch_acoustic(bool str, bool adj, const StepParams& p, const TmaSet& tm, const RegionList& rl, int blocks,
                      int* err, cudaStream_t st) {
     if (blocks <= 0) return;
+    prefer_shared_ac();
     const dim3 blk(TX, TY, 1);
     if (str) {
         if (adj) k_ac_str<true><<<blocks, blk, SMEM, st>>>(p, tm, rl, err);
@@ -89,6 +107,7 @@ static int multi_ac_grid() {
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
     if (!grid[dev]) {
+        prefer_shared_ac();
         int sms = 148, per_sm = 1;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_ac<STR, ADJ>, NT, SMEM);

@@ -498,10 +498,26 @@ size_t fluid_smem_of() {
     return STR ? StrFl<ADJ, PM>::SMEM : VelFl<ADJ, PM>::SMEM;
 }
 
+// Shared memory first in the unified L1 / shared-memory array (the bodies
+// stage through TMA, not L1), so that shared memory does not cap the blocks
+// per SM below the register limit; set once per kernel and device.
+template <bool STR, bool ADJ>
+void prefer_shared() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM_Z>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM_X>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM_FULL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    done[dev] = true;
+}
+
 template <bool STR, bool ADJ>
 void launch_fl(int pm, const StepParams& p, const TmaSet& tm, const RegionList& rl, int blocks, int* err,
                cudaStream_t st) {
     const dim3 blk(TX, TY, 1);
+    prefer_shared<STR, ADJ>();
     if (pm == PM_Z)
         k_fluid<STR, ADJ, PM_Z><<<blocks, blk, fluid_smem_of<STR, ADJ, PM_Z>(), st>>>(p, tm, rl, err);
     else if (pm == PM_X)
@@ -542,6 +558,7 @@ int multi_fl_grid() {
     if (!grid[dev]) {
         const size_t smem = fluid_smem_of<STR, ADJ, PM_FULL>();
         cudaFuncSetAttribute(k_multi_fl<STR, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_multi_fl<STR, ADJ>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         int sms = 148, per_sm = 1;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_fl<STR, ADJ>, NT, smem);

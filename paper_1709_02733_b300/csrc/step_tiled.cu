@@ -958,6 +958,8 @@ size_t fam_smem(int f, int pm) {
 // resident blocks of a kernel on the whole device
 long device_slots(const void* fn, size_t smem, int dev) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // shared memory first in the unified L1 / shared array (TMA staging)
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int sms = 148, per_sm = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
