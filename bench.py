@@ -17,7 +17,11 @@ needed between steps.
 
 Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
 independent replica of the workload (weak scaling, no collective on the data
-path); value = updates of all ranks / max-over-ranks time.
+path); value = updates of all ranks / max-over-ranks time.  With
+--decomp slabs the ranks split one solve into z slabs instead (strong
+scaling, halo planes exchanged over NCCL).  The default line also carries a
+short serving leg (--serving-requests): a seeded request stream served with
+continuous batching and one at a time.
 """
 from __future__ import annotations
 
@@ -54,6 +58,8 @@ def parse():
     ap.add_argument("--ksteps", type=int, default=16)
     ap.add_argument("--fill-points", type=int, default=None,
                     help="serving: admit while the admitted solves hold fewer grid points than this")
+    ap.add_argument("--policy", choices=["srpt", "all"], default="srpt",
+                    help="serving: advance the shortest remaining solves (srpt) or every admitted one (all)")
     ap.add_argument("--decomp", choices=["replicas", "slabs"], default="replicas",
                     help="N > 1: independent solves per rank (replicas, weak scaling) or one solve split "
                          "into z slabs over the ranks (strong scaling)")
@@ -537,7 +543,7 @@ def run_ours(args):
     g.close()
     serving = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
-        serving = serving_leg(args.serving_requests, args.ksteps, args.fill_points)
+        serving = serving_leg(args.serving_requests, args.ksteps, args.fill_points, args.policy)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -557,21 +563,24 @@ SERVE_BUDGET = 120 * 10 ** 9
 SERVE_SLOTS = 32
 
 
-def serving_leg(requests, ksteps, fill_points=None):
+def serving_leg(requests, ksteps, fill_points=None, policy="srpt"):
     """Serving workload: Poisson arrivals at 40 req/s, cubic grids of side 96..320
     (multiples of 8), dx 0.4 mm, 10-cell C-PML, 800..2500 steps, 64..512
     hemisphere receivers, forward/adjoint 50/50, 120 GB HBM budget, 32 slots.
     The same requests are served (a) with continuous batching through
     pact_advance and (b) one at a time with pact_forward / pact_adjoint, in
-    real time on this GPU; returns both arms' statistics and their ratios."""
+    real time on this GPU; returns both arms' statistics and their ratios.
+    policy: which admitted solves each chunk advances (serving.run_continuous:
+    "srpt", shortest remaining work first, or "all")."""
     from paper_1709_02733_b300 import serving
     cache = serving.InputCache()
     cont = serving.run_continuous(serving.make_stream(requests, **SERVE_KW), SERVE_BUDGET, ksteps=ksteps,
-                                  max_slots=SERVE_SLOTS, cache=cache, realtime=True, fill_points=fill_points)
+                                  max_slots=SERVE_SLOTS, cache=cache, realtime=True, fill_points=fill_points,
+                                  policy=policy)
     solo = serving.run_one_at_a_time(serving.make_stream(requests, **SERVE_KW), cache=cache, realtime=True)
     return {"workload": f"serving stream: {requests} seeded Poisson requests at 40 req/s, sides 96..320 step 8, "
                         "800..2500 steps, 64..512 receivers, fwd/adj 50/50, 120 GB budget, 32 slots",
-            "ksteps": ksteps, "fill_points": fill_points, "continuous": cont, "one_at_a_time": solo,
+            "ksteps": ksteps, "fill_points": fill_points, "policy": policy, "continuous": cont, "one_at_a_time": solo,
             "throughput_ratio": cont["updates_per_s"] / solo["updates_per_s"],
             "p50_ratio": cont["p50_s"] / solo["p50_s"], "p99_ratio": cont["p99_s"] / solo["p99_s"]}
 
@@ -582,10 +591,11 @@ def run_serving(args):
     from paper_1709_02733_b300 import build as pbuild
     pbuild.build()
     torch.cuda.set_device(0)
-    sv = serving_leg(args.requests, args.ksteps, args.fill_points)
+    sv = serving_leg(args.requests, args.ksteps, args.fill_points, args.policy)
     line = {"metric": "served p50/p99 latency beside throughput", "value": sv["continuous"]["p99_s"],
             "unit": "s (p99)", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": sv["workload"], "ksteps": args.ksteps, "fill_points": args.fill_points}}
+            "config": {"workload": sv["workload"], "ksteps": args.ksteps, "fill_points": args.fill_points,
+                       "policy": args.policy}}
     line.update({k: sv[k] for k in ("continuous", "one_at_a_time", "throughput_ratio", "p50_ratio", "p99_ratio")})
     print(json.dumps(line), flush=True)
 

@@ -159,10 +159,14 @@ int pact_get_wavefield(pact_handle h, float* host_out);
 /* ---- serving: many solves advanced together ------------------------------
  * A solve is prepared on its handle with pact_begin, then any set of prepared
  * handles (forward and adjoint, any grid sizes) is advanced together by
- * pact_advance: per time step, persistent multi-instance kernels walk a device
- * table of the solves (the same step kernels as pact_forward / pact_adjoint, so
- * a result is the same alone and in a mix).  Not part of the paper: this is how
- * the operator pair is served to concurrent requests. */
+ * pact_advance.  Each solve advances on its own CUDA graphs of whole steps
+ * (those of pact_forward / pact_adjoint) on a stream of its handle, so that
+ * the solves of one advance overlap on the device; solves below a size
+ * (PACT_SERVE_SOLO_POINTS in the environment at pact_begin; default 0, i.e.
+ * none) instead go to persistent multi-instance kernels that walk a device
+ * table of solves.  Both run the same step bodies, so a result is the same
+ * alone and in a mix.  Not part of the paper: this is how the operator pair
+ * is served to concurrent requests. */
 
 /* Prepare one solve on h (queued on the handle's stream).  is_adjoint = 0:
  * forward, in = p0 (device, N floats), out = traces (device, (nsteps+1)*L),
@@ -174,14 +178,17 @@ int pact_get_wavefield(pact_handle h, float* host_out);
 int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_xyz, int L, int nsteps, float* out);
 
 /* Advance every unfinished solve among hs[0..n-1] (n <= 64, one device) by
- * min(ksteps, steps left) time steps, queued on `stream` (cudaStream_t) as one
- * replay of a captured CUDA graph of ksteps multi-instance steps; a solve that
- * finishes gets its read-out.  pact_begin of these handles must be ordered
- * before it (use the same stream).  All advances on one device share one
- * device table of solves and one set of work counters, so the library orders
- * them: an advance queued on a different stream than the previous advance on
- * that device first waits (cudaStreamWaitEvent) for the previous replay, and
- * advances on one device therefore never run concurrently.  Errors:
+ * min(ksteps, steps left) time steps, queued on `stream` (cudaStream_t): the
+ * step graphs of each solve on its handle's serving stream, forked from and
+ * joined back to `stream`, and one replay of a captured CUDA graph of ksteps
+ * multi-instance steps for the solves on the multi-instance kernels; a solve
+ * that finishes gets its read-out.  Work queued on `stream` after the call
+ * runs after all of it.  pact_begin of these handles must be ordered before
+ * it (use the same stream).  All advances on one device share one device
+ * table of solves and one set of work counters, so the library orders them:
+ * an advance queued on a different stream than the previous advance on that
+ * device first waits (cudaStreamWaitEvent) for the previous replay, and
+ * table replays on one device therefore never run concurrently.  Errors:
  * PACT_EINVAL, PACT_ECUDA,
  * PACT_ETIMEOUT (an earlier advance on this device reported a timed-out
  * wait); message via pact_last_error(NULL). */

@@ -127,6 +127,10 @@ struct pact_grid {
     // serving state (pact_begin / pact_advance / pact_poll)
     bool sv_active = false;
     bool sv_solo = false;  // advanced by its own step graphs, not the multi-instance kernels
+    // pact_advance runs each such solve's steps on this stream, forked from
+    // the caller's stream and joined back (solves overlap on the device)
+    cudaStream_t sv_stream = nullptr;
+    cudaEvent_t sv_fork = nullptr, sv_join = nullptr;
     int sv_adj = 0, sv_m = 0, sv_nsteps = 0;
     const float* sv_in = nullptr;
     float* sv_out = nullptr;
@@ -492,9 +496,13 @@ static unsigned long long* band_counter(pact_handle h) {
 
 // ---- CUDA graphs of whole steps ---------------------------------------------
 constexpr int kGraphSteps = 16;
-// grids of at least this many points fill the device alone: pact_advance
-// steps them on their own kernels (at 224^3 both ways ran alike on B300)
-constexpr long long kSoloPoints = 200LL * 200 * 200;
+// pact_advance steps grids of at least this many points on their own step
+// graphs, the rest on the multi-instance kernels.  On B300 the step graphs
+// ran every size measured (96^3 .. 320^3) at least as fast, and 40 requests
+// advanced together at 40.2 G updates/s against 37.7 with 8 M points here
+// and 31.8 with every solve on the multi-instance kernels: all solves take
+// their own graphs (PACT_SERVE_SOLO_POINTS overrides the size).
+constexpr long long kSoloPoints = 0;
 
 static void drop_graphs(pact_handle h) {
     for (auto& dir : h->graphs)
@@ -945,6 +953,9 @@ int pact_destroy(pact_handle h) {
     drop_graphs(h);
     cudaFree(h->solve_dev);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->sv_stream) cudaStreamDestroy(h->sv_stream);
+    if (h->sv_fork) cudaEventDestroy(h->sv_fork);
+    if (h->sv_join) cudaEventDestroy(h->sv_join);
     for (int a = 0; a < 3; ++a) cudaFree(h->slabs[a]);
     free_rec(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1098,13 +1109,18 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         h->sv_fl = h->sv_ac;
         h->sv_nac = h->sv_nfl = 0;
     }
-    // a grid large enough to fill the device alone advances on its own step
-    // kernels (faster there than the multi-instance ones); the solve's state
-    // then lives in solve_dev.  PACT_SERVE_SOLO_POINTS overrides the size
-    // (a negative value sends every solve to the multi-instance kernels).
+    // a solve of kSoloPoints points or more advances on its own step graphs
+    // (its state then lives in solve_dev), a smaller one on the multi-instance
+    // kernels.  PACT_SERVE_SOLO_POINTS overrides the size (a negative value
+    // sends every solve to the multi-instance kernels).
     long long solo_points = kSoloPoints;
     if (const char* senv = getenv("PACT_SERVE_SOLO_POINTS")) solo_points = std::atoll(senv);
     h->sv_solo = h->tiled && !h->fused && solo_points >= 0 && (long long)h->N >= solo_points;
+    if (h->sv_solo && !h->sv_stream) {
+        CK(h, cudaStreamCreateWithFlags(&h->sv_stream, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->sv_fork, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->sv_join, cudaEventDisableTiming));
+    }
     if (h->sv_solo) {
         const SolveState v{0, 0u, nsteps, r, is_adjoint ? nullptr : out, is_adjoint ? in : nullptr};
         launch_set_state(h->solve_dev, v, h->stream);
@@ -1168,11 +1184,17 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
         const int rc = serve_run(*T, ksteps, st, why);
         if (rc) return fail(nullptr, rc, why);
     }
+    // solves on their own step graphs: each on its stream, forked from st and
+    // joined back, so that they overlap one another and the table's kernels
     for (int k = 0; k < n; ++k) {
         pact_handle h = hs[k];
         if (!h->sv_active || !h->sv_solo) continue;
-        const int rc = graph_steps(h, h->sv_adj != 0, std::min(ksteps, h->sv_nsteps - h->sv_m), st);
+        CK(h, cudaEventRecord(h->sv_fork, st));
+        CK(h, cudaStreamWaitEvent(h->sv_stream, h->sv_fork, 0));
+        const int rc = graph_steps(h, h->sv_adj != 0, std::min(ksteps, h->sv_nsteps - h->sv_m), h->sv_stream);
         if (rc) return rc;
+        CK(h, cudaEventRecord(h->sv_join, h->sv_stream));
+        CK(h, cudaStreamWaitEvent(st, h->sv_join, 0));
     }
     for (int k = 0; k < n; ++k) {
         pact_handle h = hs[k];

@@ -226,11 +226,29 @@ def _buffers(r: Request, cache: InputCache, stream):
 
 
 FILL_POINTS = 24_000_000  # grid points in flight that keep one B300 busy (a ~290^3 grid)
+ADVANCE_POINTS = 4_000_000  # grid points one chunk advances under the "srpt" policy
+
+
+def pick_to_advance(remaining: List[float], points: List[int], advance_points: int) -> List[int]:
+    """Shortest remaining work first: the indices of the solves to advance in
+    the next chunk, by ascending remaining updates, until their grid points
+    reach advance_points (at least one solve).  On a GPU that one solve of
+    this size already keeps busy, the order changes no solve's cost, so the
+    total time stays and the solves that are nearly done finish first."""
+    order = sorted(range(len(remaining)), key=lambda i: (remaining[i], i))
+    out, held = [], 0
+    for i in order:
+        if out and held >= advance_points:
+            break
+        out.append(i)
+        held += points[i]
+    return out
 
 
 def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16, max_slots: int = 32,
                    cache: Optional[InputCache] = None, realtime: bool = True,
-                   fill_points: Optional[int] = None) -> Dict:
+                   fill_points: Optional[int] = None, policy: str = "srpt",
+                   advance_points: int = ADVANCE_POINTS) -> Dict:
     """Serve the stream with continuous batching; returns statistics.
 
     Admission is first-come-first-served under the HBM budget and the slot
@@ -250,7 +268,14 @@ def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16,
     all admitted solves; retire solves whose last step has executed (their
     handles return to the pool).  At most two graph replays are in flight, so
     admissions and completions are seen within one chunk.  realtime=False
-    skips idle waits (arrivals are then virtual)."""
+    skips idle waits (arrivals are then virtual).
+
+    policy="all" advances every admitted solve in every chunk (processor
+    sharing); policy="srpt" (the default) advances the admitted solves with
+    the least remaining work, as many as hold advance_points grid points
+    (pick_to_advance): the others stay resident and wait.  With one solve
+    already keeping the GPU busy, both give the same total time; "srpt"
+    finishes short solves first."""
     import collections
 
     import torch
@@ -313,11 +338,16 @@ def run_continuous(requests: List[Request], budget_bytes: int, ksteps: int = 16,
             if pending:
                 time.sleep(max(0.0, min(pending[0].arrival - now(), 0.005)))
             continue
-        pact_advance([a.grid for a in active], ksteps, stream)
+        running = [a for a in active if a.ev is None]
+        if policy == "srpt" and running:
+            rem = [float(a.req.n) ** 3 * (a.req.nsteps - a.grid.poll()) for a in running]
+            running = [running[i] for i in pick_to_advance(rem, [a.req.n ** 3 for a in running], advance_points)]
+        if running:
+            pact_advance([a.grid for a in running], ksteps, stream)
         ev = torch.cuda.Event()
         ev.record(stream)
         inflight.append(ev)
-        for a in active:
+        for a in running:
             if a.ev is None and a.grid.poll() >= a.req.nsteps:
                 a.ev = ev
         while len(inflight) > 1:

@@ -47,3 +47,17 @@ def test_stream_is_seeded_and_in_range():
     assert all(800 <= r.nsteps <= 2500 and 64 <= r.L <= 512 for r in a)
     frac_adj = np.mean([r.adjoint for r in a])
     assert 0.35 < frac_adj < 0.65
+
+
+def test_pick_to_advance_shortest_remaining_first():
+    from paper_1709_02733_b300.serving import pick_to_advance
+    rem = [50.0, 10.0, 30.0, 10.0]
+    pts = [8, 2, 4, 2]
+    # ascending remaining work, ties by index, until the points reach the bound
+    assert pick_to_advance(rem, pts, 1) == [1]
+    assert pick_to_advance(rem, pts, 4) == [1, 3]
+    assert pick_to_advance(rem, pts, 5) == [1, 3, 2]
+    assert pick_to_advance(rem, pts, 10 ** 9) == [1, 3, 2, 0]
+    assert pick_to_advance([], [], 4) == []
+    # a large solve alone is still advanced
+    assert pick_to_advance([5.0], [100], 4) == [0]
