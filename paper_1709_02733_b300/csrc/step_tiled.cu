@@ -1359,15 +1359,16 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
         const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);
         pts[li] += (long long)ex * ey * (b - a);
     };
-    // planes per work item: 48 where the tiles alone give the device enough
-    // items; fewer (down to 8) on small grids, whose few blocks would
-    // otherwise march many planes one after another with most SMs idle
-    // (each block waits on its loads plane by plane)
+    // planes per work item: 32 where the tiles alone give the device enough
+    // items (on B300 the skull-512 step pair took 4.58 ms at 32 against 4.68
+    // at 48, 4.63 at 24 and 4.89 at 96); fewer (down to 8) on small grids,
+    // whose few blocks would otherwise march many planes one after another
+    // with most SMs idle (each block waits on its loads plane by plane)
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long want = 4L * sms;
-    const int kChunk = (int)std::min<long>(48, std::max<long>(8, (long)(zb - za) * ntiles / want));
+    const int kChunk = (int)std::min<long>(32, std::max<long>(8, (long)(zb - za) * ntiles / want));
     std::vector<int> cuts{0};
     if (za > 0) cuts.push_back(za);
     if (zb > za) {
