@@ -232,7 +232,11 @@ int pact_step_receivers(pact_handle h);
  * sigma^11, sigma^22, sigma^33, sigma^23, sigma^13, sigma^12; after an adjoint
  * pact_begin the same slots hold w and Q): N floats, [z][y][x], one z plane
  * of nx*ny floats contiguous.  For halo exchange between slab handles; the
- * library owns the memory.  Errors: PACT_EINVAL. */
+ * library owns the memory.  During a solve on a medium with fluid and solid
+ * nodes, sigma^22 and sigma^33 (Q^22, Q^33) of fluid points far from every
+ * solid node hold stale values (the library writes sigma^11 alone there and
+ * fills the other two before an image read-out or pact_get_wavefield); the
+ * planes a slab exchanges are never such points.  Errors: PACT_EINVAL. */
 int pact_field_ptr(pact_handle h, int field, float** out);
 
 /* Forward operator H that allocates no device memory.  The paper has no

@@ -59,6 +59,7 @@ struct pact_grid {
     double cmax = 0.0;
     // receivers
     std::vector<float> rec_host;
+    long long rec_medium_gen = -1;  // medium_gen the device tables were built for
     int L = 0;
     int rec_cap = 0;
     int* rec_corner = nullptr;
@@ -94,6 +95,7 @@ struct pact_grid {
     // kernels, the rest the elastic ones (plan built from the medium)
     bool mixed = false;
     MixedPlan mixed_plan{};
+    long long medium_gen = 0;  // pact_set_medium calls (the receiver tables depend on the plan)
     // a slab of a larger grid (pact_create_slab): plane k is plane z0g + k of nzg
     int z0g = 0, nzg = 0;
     float* fields2 = nullptr;
@@ -306,6 +308,15 @@ static void free_rec(pact_handle h) {
     h->rec_cap = 0;
 }
 
+// sigma^22, sigma^33 (adjoint: Q^22, Q^33) of the ITEM_AC_DEEP items hold
+// stale values during a solve (only sigma^11 is written there); copy
+// sigma^11 into them before anything reads the three (image read-out,
+// wavefield copy)
+static void ac_fill(pact_handle h, cudaStream_t st) {
+    if (!h->mixed || h->mixed_plan.deep_points == 0) return;
+    launch_ac_fill(make_params(h), h->mixed_plan.list[MX_INT_AC], h->mixed_plan.blocks[MX_INT_AC], st);
+}
+
 // Validate the HOST receiver array and (re)build the device tables when it changed.
 static int set_receivers(pact_handle h, const float* rec, int L) {
     if (!rec || L < 1) return fail(h, PACT_EINVAL, "receivers: rec_xyz must be non-NULL and L >= 1");
@@ -320,7 +331,8 @@ static int set_receivers(pact_handle h, const float* rec, int L) {
                 return fail(h, PACT_EINVAL, buf);
             }
         }
-    if (L == h->L && !h->rec_host.empty() && std::memcmp(h->rec_host.data(), rec, sizeof(float) * 3 * L) == 0)
+    if (L == h->L && !h->rec_host.empty() && h->rec_medium_gen == h->medium_gen &&
+        std::memcmp(h->rec_host.data(), rec, sizeof(float) * 3 * L) == 0)
         return PACT_OK;
     // host tables
     std::vector<int> corner(8 * (size_t)L);
@@ -342,7 +354,10 @@ static int set_receivers(pact_handle h, const float* rec, int L) {
                 for (int cx = 0; cx < 2; ++cx, ++c) {
                     const double w = (cx ? fx : 1 - fx) * (cy ? fy : 1 - fy) * (cz ? fz : 1 - fz);
                     const int q = ((k0 + cz) * d.ny + (j0 + cy)) * d.nx + (i0 + cx);
-                    corner[8 * l + c] = q;
+                    // a corner in an ITEM_AC_DEEP item is stored as ~q: the
+                    // sampler reads 3 sigma^11 there (sigma^22, sigma^33 stale)
+                    const bool deep = h->mixed && plan_deep(h->mixed_plan, i0 + cx, j0 + cy, k0 + cz);
+                    corner[8 * l + c] = deep ? ~q : q;
                     weight[8 * l + c] = (float)w;
                     con[8 * l + c] = {q, l, (float)w};
                 }
@@ -385,6 +400,7 @@ static int set_receivers(pact_handle h, const float* rec, int L) {
     h->ncorner = (int)ipoint.size();
     h->L = L;
     h->rec_host.assign(rec, rec + 3 * (size_t)L);
+    h->rec_medium_gen = h->medium_gen;
     return PACT_OK;
 }
 
@@ -658,6 +674,7 @@ static int run_adjoint(pact_handle h, const float* traces, float* image, int nst
         launch_set_state(h->solve_dev, v, h->stream);
         rc = graph_steps(h, true, nsteps, h->stream);
         if (rc) return rc;
+        ac_fill(h, h->stream);
         launch_readout(image, p, h->stream);
         mark(h, PACT_K_READOUT);
         h->cur = 0;
@@ -673,6 +690,7 @@ static int run_adjoint(pact_handle h, const float* traces, float* image, int nst
         launch_inject(p, r, traces + (size_t)(m - 1) * h->L, h->stream);
         mark(h, PACT_K_INJECT, r.ncorner > 0);
     }
+    ac_fill(h, h->stream);
     launch_readout(image, p, h->stream);
     mark(h, PACT_K_READOUT);
     h->cur = c;
@@ -892,6 +910,7 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
         const long long* np = h->mixed_plan.points;
         h->mixed = np[MX_INT_AC] + np[MX_INT_FZ] + np[MX_EDGE_FL] + np[MX_CORNER_FL] > 0;
     }
+    h->medium_gen++;
     h->medium_set = true;
     return PACT_OK;
 }
@@ -989,6 +1008,7 @@ int pact_get_wavefield(pact_handle h, float* host_out) {
     if (!h) return fail(nullptr, PACT_EINVAL, "handle is NULL");
     if (!host_out) return fail(h, PACT_EINVAL, "host_out is NULL");
     CK(h, cudaSetDevice(h->device));
+    ac_fill(h, h->stream);
     CK(h, cudaMemcpyAsync(host_out, buffer(h, h->cur), 9 * h->N * sizeof(float), cudaMemcpyDeviceToHost,
                           h->stream));
     return device_status(h);
@@ -1086,7 +1106,10 @@ int pact_begin(pact_handle h, int is_adjoint, const float* in, const float* rec_
         launch_sample(p, r, out, h->stream);
     } else {
         if (L > 0) launch_inject(p, r, in + (size_t)nsteps * L, h->stream);
-        if (nsteps == 0) launch_readout(out, p, h->stream);
+        if (nsteps == 0) {
+            ac_fill(h, h->stream);
+            launch_readout(out, p, h->stream);
+        }
     }
     if (h->mixed) {
         // a medium-adaptive handle serves its per-medium work lists
@@ -1204,6 +1227,7 @@ int pact_advance(pact_handle* hs, int n, int ksteps, void* stream) {
             h->sv_active = false;
             if (h->sv_adj) {
                 const StepParams p = make_params(h);
+                ac_fill(h, st);
                 launch_readout(h->sv_out, p, st);
             }
         }
@@ -1259,6 +1283,7 @@ int pact_step_receivers(pact_handle h) {
     if (m == h->sv_nsteps) {
         h->sv_active = false;
         if (h->sv_adj) {
+            ac_fill(h, h->stream);
             launch_readout(h->sv_out, p, h->stream);
             mark(h, PACT_K_READOUT);
         }

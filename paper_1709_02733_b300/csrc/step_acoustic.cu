@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(NT) k_ac_str(StepParams p, const __grid_consta
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    ac_str_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    ac_str_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, kind != ITEM_AC_DEEP);
 }
 
 // Persistent multi-instance kernel over the fluid no-layer items of the
@@ -40,9 +40,10 @@ template <bool STR, bool ADJ>
 __global__ void __launch_bounds__(NT) k_multi_ac(const MultiTable* __restrict__ T, int* err, int* next) {
     extern __shared__ __align__(128) float sm[];
     multi_loop<ADJ, ML_AC>(T, err, next, sm,
-                           [](const StepParams& sp, const CUtensorMap* maps, int, int tile_x, int tile_y, int zc0,
+                           [](const StepParams& sp, const CUtensorMap* maps, int kind, int tile_x, int tile_y, int zc0,
                               int zc1, int* e, float* smem) {
-                               return STR ? ac_str_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                               return STR ? ac_str_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem,
+                                                             kind != ITEM_AC_DEEP)
                                           : ac_vel_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
                            });
 }
@@ -93,6 +94,28 @@ void launch_acoustic(bool str, bool adj, const StepParams& p, const TmaSet& tm, 
         if (adj) k_ac_vel<true><<<blocks, blk, SMEM, st>>>(p, tm, rl, err);
         else k_ac_vel<false><<<blocks, blk, SMEM, st>>>(p, tm, rl, err);
     }
+}
+
+// sigma^22 = sigma^33 = sigma^11 on the ITEM_AC_DEEP items of an acoustic
+// list (one block per item; other items are left alone)
+__global__ void __launch_bounds__(NT) k_ac_fill(const float* __restrict__ s0, float* s1, float* s2, int nx, int ny,
+                                                RegionList rl) {
+    int tile_x, tile_y, zc0, zc1, kind;
+    locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
+    if (kind != ITEM_AC_DEEP) return;
+    const int x = tile_x * TX + threadIdx.x, y = tile_y * TY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const size_t nxy = (size_t)nx * ny;
+    for (int z = zc0; z < zc1; ++z) {
+        const size_t g = (size_t)z * nxy + (size_t)y * nx + x;
+        const float v = s0[g];
+        s1[g] = v;
+        s2[g] = v;
+    }
+}
+
+void launch_ac_fill(const StepParams& p, const RegionList& ac, int blocks, cudaStream_t st) {
+    if (blocks > 0) k_ac_fill<<<blocks, dim3(TX, TY, 1), 0, st>>>(p.s[0], p.s[1], p.s[2], p.nx, p.ny, ac);
 }
 
 void launch_any_shear(const float* mu, size_t n, unsigned int* out, cudaStream_t st) {

@@ -144,8 +144,9 @@ __device__ __forceinline__ bool ac_vel_body(const StepParams& p, const CUtensorM
 // Stress half: output plane z = pl - 2; the z queue of u3 holds planes
 // z-2 .. z+1 (half->integer difference), so its head is plane pl - 1.
 template <bool ADJ>
+// all3 = false (an ITEM_AC_DEEP item, no elastic reader): sigma^11 only
 __device__ __forceinline__ bool ac_str_body(const StepParams& p, const CUtensorMap* tmm, int tile_x, int tile_y,
-                                            int zc0, int zc1, int* err, float* sm) {
+                                            int zc0, int zc1, int* err, float* sm, bool all3 = true) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = (unsigned)(y0 + ty) * p.nx + (unsigned)(x0 + tx);
@@ -192,8 +193,10 @@ __device__ __forceinline__ bool ac_str_body(const StepParams& p, const CUtensorM
             const float res = so + ks * (lam * theta);
             const unsigned gi = (unsigned)z * nxy + gxy;
             p.s_out[0][gi] = res;
-            p.s_out[1][gi] = res;
-            p.s_out[2][gi] = res;
+            if (all3) {
+                p.s_out[1][gi] = res;
+                p.s_out[2][gi] = res;
+            }
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);

@@ -343,6 +343,14 @@ __global__ void k_readout(const float* __restrict__ s0, const float* __restrict_
     }
 }
 
+// sigma^11 + sigma^22 + sigma^33 at a receiver corner; a corner stored as ~q
+// lies in an item that writes sigma^11 alone (ITEM_AC_DEEP), where the three
+// are equal: 3 sigma^11, bitwise the sum (s + s is exact, so both round 3 s once)
+__device__ __forceinline__ float corner_trace(const float* __restrict__ s0, const float* __restrict__ s1,
+                                              const float* __restrict__ s2, int q) {
+    return q >= 0 ? __ldg(s0 + q) + __ldg(s1 + q) + __ldg(s2 + q) : 3.0f * __ldg(s0 + ~q);
+}
+
 // Theta (Eq. (interpgrid)): out[l] = -sum_c w_c (s11 + s22 + s33)(c)
 __global__ void k_sample(const float* __restrict__ s0, const float* __restrict__ s1, const float* __restrict__ s2,
                          RecTable r, float* out) {
@@ -350,10 +358,7 @@ __global__ void k_sample(const float* __restrict__ s0, const float* __restrict__
     if (l >= r.L) return;
     float acc = 0.0f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int q = __ldg(r.corner + 8 * l + c);
-        acc += __ldg(r.weight + 8 * l + c) * (__ldg(s0 + q) + __ldg(s1 + q) + __ldg(s2 + q));
-    }
+    for (int c = 0; c < 8; ++c) acc += __ldg(r.weight + 8 * l + c) * corner_trace(s0, s1, s2, __ldg(r.corner + 8 * l + c));
     out[l] = -acc;
 }
 
@@ -405,10 +410,8 @@ __global__ void k_sample_state(const float* __restrict__ s0, const float* __rest
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < r.L; l += gridDim.x * blockDim.x) {
         float acc = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int q = __ldg(r.corner + 8 * l + c);
-            acc += __ldg(r.weight + 8 * l + c) * (__ldg(s0 + q) + __ldg(s1 + q) + __ldg(s2 + q));
-        }
+        for (int c = 0; c < 8; ++c)
+            acc += __ldg(r.weight + 8 * l + c) * corner_trace(s0, s1, s2, __ldg(r.corner + 8 * l + c));
         out[l] = -acc;
     }
     step_done(st);

@@ -33,7 +33,10 @@
 //
 // Requirements: nx % 4 == 0 (TMA global strides are multiples of 16 bytes).
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 #include <type_traits>
 
@@ -1312,8 +1315,11 @@ __global__ void k_tile_solid(const float* __restrict__ mu, int nx, int ny, int t
     if (threadIdx.x == 0) out[(size_t)z * ntx * nty + t] = any ? 1 : 0;
 }
 
+static_assert(TX == kTileX && TY == kTileY, "plan_deep's tile size");
+
 void free_mixed_plan(MixedPlan* mp) {
     cudaFree(mp->mem);
+    delete[] mp->deep;
     *mp = MixedPlan{};
 }
 
@@ -1346,6 +1352,37 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
             for (int k = std::max(0, z - 3); k <= std::min(p.nz - 1, z + 3); ++k) any |= flag[(size_t)k * ntiles + t];
             solid[(size_t)z * ntiles + t] = any;
         }
+    // near[z][t]: an elastic item within one tile in x and y and three planes
+    // in z, i.e. within reach of an elastic body's sigma^22 / sigma^33 reads
+    // (two cells, two planes) with a margin.  A fluid no-layer item without it
+    // is ITEM_AC_DEEP (PACT_AC_DEEP=0: none is).
+    std::vector<unsigned char> near(nflag, 1);
+    const char* denv = getenv("PACT_AC_DEEP");
+    if (!(denv && std::strcmp(denv, "0") == 0)) {
+        std::vector<unsigned char> nxy(nflag);
+        for (int z = 0; z < p.nz; ++z)
+            for (int t = 0; t < ntiles; ++t) {
+                const int tx = t % ntx, ty = t / ntx;
+                unsigned char any = 0;
+                for (int dy = -1; dy <= 1 && !any; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int ux = tx + dx, uy = ty + dy;
+                        if (ux < 0 || ux >= ntx || uy < 0 || uy >= nty) continue;
+                        any |= solid[(size_t)z * ntiles + uy * ntx + ux];
+                    }
+                nxy[(size_t)z * ntiles + t] = any;
+            }
+        for (int t = 0; t < ntiles; ++t)
+            for (int z = 0; z < p.nz; ++z) {
+                unsigned char any = 0;
+                for (int k = std::max(0, z - 3); k <= std::min(p.nz - 1, z + 3); ++k) any |= nxy[(size_t)k * ntiles + t];
+                near[(size_t)z * ntiles + t] = any;
+            }
+    }
+    mp->ntx = ntx;
+    mp->nty = nty;
+    mp->deep = new (std::nothrow) unsigned char[nflag]();
+    if (!mp->deep) return 1;
     // Segments of every tile over common z chunks (the z-slab planes below
     // and above the interior planes, then chunks of the interior planes),
     // chunk by chunk, so that the blocks resident at one time work on the
@@ -1398,12 +1435,26 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
                 li_el = MX_CORNER_EL;
                 li_fl = MX_CORNER_FL;
             }
+            // runs of equal (solid, near) flags; near only matters for the
+            // fluid no-layer items
+            const bool ac = li_fl == MX_INT_AC;
+            auto key = [&](int z) {
+                const unsigned char f = solid[(size_t)z * ntiles + t];
+                return (int)f * 2 + ((!f && ac) ? (int)near[(size_t)z * ntiles + t] : 0);
+            };
             int a = c0;
             while (a < c1) {
-                const unsigned char f = solid[(size_t)a * ntiles + t];
+                const int kf = key(a);
                 int b = a + 1;
-                while (b < c1 && solid[(size_t)b * ntiles + t] == f) ++b;
-                add(f ? li_el : li_fl, tx, ty, a, b, kind);
+                while (b < c1 && key(b) == kf) ++b;
+                const bool f = kf >= 2;
+                const bool deep = !f && ac && (kf & 1) == 0;
+                add(f ? li_el : li_fl, tx, ty, a, b, deep ? ITEM_AC_DEEP : kind);
+                if (deep) {
+                    for (int z = a; z < b; ++z) mp->deep[(size_t)z * ntiles + t] = 1;
+                    const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);
+                    mp->deep_points += (long long)ex * ey * (b - a);
+                }
                 a = b;
             }
         }

@@ -152,3 +152,37 @@ def test_mixed_skull_512_split():
     assert 0.5 * w.desc.N < n_ac < 0.7 * w.desc.N
     assert g.role_points("fwd_velocity")[0] + n_ac == w.desc.N
     g.close()
+
+
+def test_deep_items_write_sigma11_only_and_change_nothing(monkeypatch):
+    """Fluid no-layer items with no elastic item within a tile and three planes
+    write sigma^11 alone; the sampler reads 3 sigma^11 there and the three
+    normal stresses are filled in before the image read-out and the wavefield
+    copy.  Traces, images and wavefields are bitwise those of the path that
+    writes all three everywhere (PACT_AC_DEEP=0), and match the FP64 oracle."""
+    d, med, p0, rec = _inclusion_case(shape=(64, 64, 192), npml=4, seed=37, L=23, cx=0.85, rx=12.0)
+    # receivers also deep inside the water, away from the inclusion
+    rec[:8, 0] = np.linspace(36.0, 90.0, 8)
+    rec[:8, 1] = np.linspace(20.0, 40.0, 8)
+    rec[:8, 2] = np.linspace(20.0, 44.0, 8)
+    g_d = make_grid(d, med)
+    monkeypatch.setenv("PACT_AC_DEEP", "0")
+    g_a = make_grid(d, med)
+    monkeypatch.delenv("PACT_AC_DEEP")
+    nsteps = 45
+    tr_d = g_d.forward(cuda(p0), rec, nsteps)
+    # inside the solve sigma^22 is stale on the deep items (raw device views)
+    raw11, raw22 = g_d.field_view(3), g_d.field_view(4)
+    assert not torch.equal(raw11, raw22)
+    tr_a = g_a.forward(cuda(p0), rec, nsteps)
+    assert torch.equal(tr_d, tr_a)
+    wf_d, wf_a = g_d.get_wavefield(), g_a.get_wavefield()
+    assert np.array_equal(wf_d, wf_a)
+    y = torch.from_numpy(np.random.default_rng(8).standard_normal(tuple(tr_d.shape)).astype(np.float32)).cuda()
+    img_d = g_d.adjoint(y, rec)
+    img_a = g_a.adjoint(y, rec)
+    assert torch.equal(img_d, img_a)
+    assert np.array_equal(g_d.get_wavefield(), g_a.get_wavefield())
+    o = Oracle(d.as_dict(), *med)
+    assert rel_l2(tr_d.cpu().numpy(), o.forward(p0, rec, nsteps)) <= TOL
+    assert rel_l2(img_d.cpu().numpy(), o.adjoint(y.cpu().numpy(), rec)) <= TOL
