@@ -308,13 +308,16 @@ static void free_rec(pact_handle h) {
     h->rec_cap = 0;
 }
 
-// sigma^22, sigma^33 (adjoint: Q^22, Q^33) of the ITEM_AC_DEEP items hold
+// sigma^22, sigma^33 (adjoint: Q^22, Q^33) of the ITEM_DEEP items hold
 // stale values during a solve (only sigma^11 is written there); copy
 // sigma^11 into them before anything reads the three (image read-out,
 // wavefield copy)
 static void ac_fill(pact_handle h, cudaStream_t st) {
     if (!h->mixed || h->mixed_plan.deep_points == 0) return;
-    launch_ac_fill(make_params(h), h->mixed_plan.list[MX_INT_AC], h->mixed_plan.blocks[MX_INT_AC], st);
+    const MixedPlan& mp = h->mixed_plan;
+    const StepParams p = make_params(h);
+    for (int l : {(int)MX_INT_AC, (int)MX_INT_FZ, (int)MX_EDGE_FL, (int)MX_CORNER_FL})
+        launch_deep_fill(p, mp.list[l], mp.blocks[l], st);
 }
 
 // Validate the HOST receiver array and (re)build the device tables when it changed.
@@ -354,7 +357,7 @@ static int set_receivers(pact_handle h, const float* rec, int L) {
                 for (int cx = 0; cx < 2; ++cx, ++c) {
                     const double w = (cx ? fx : 1 - fx) * (cy ? fy : 1 - fy) * (cz ? fz : 1 - fz);
                     const int q = ((k0 + cz) * d.ny + (j0 + cy)) * d.nx + (i0 + cx);
-                    // a corner in an ITEM_AC_DEEP item is stored as ~q: the
+                    // a corner in an ITEM_DEEP item is stored as ~q: the
                     // sampler reads 3 sigma^11 there (sigma^22, sigma^33 stale)
                     const bool deep = h->mixed && plan_deep(h->mixed_plan, i0 + cx, j0 + cy, k0 + cz);
                     corner[8 * l + c] = deep ? ~q : q;

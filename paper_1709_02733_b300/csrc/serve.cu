@@ -35,7 +35,7 @@ __global__ void k_multi_receivers(MultiTable* T) {
             float acc = 0.0f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                // a corner stored as ~q lies in an ITEM_AC_DEEP item (3 sigma^11)
+                // a corner stored as ~q lies in an ITEM_DEEP item (3 sigma^11)
                 const int q = r.corner[8 * l + c];
                 acc += r.weight[8 * l + c] * (q >= 0 ? p.s[0][q] + p.s[1][q] + p.s[2][q] : 3.0f * p.s[0][~q]);
             }

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(NT) k_ac_str(StepParams p, const __grid_consta
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    ac_str_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, kind != ITEM_AC_DEEP);
+    ac_str_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, !(kind & ITEM_DEEP));
 }
 
 // Persistent multi-instance kernel over the fluid no-layer items of the
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(NT) k_multi_ac(const MultiTable* __restrict__ 
                            [](const StepParams& sp, const CUtensorMap* maps, int kind, int tile_x, int tile_y, int zc0,
                               int zc1, int* e, float* smem) {
                                return STR ? ac_str_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem,
-                                                             kind != ITEM_AC_DEEP)
+                                                             !(kind & ITEM_DEEP))
                                           : ac_vel_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
                            });
 }
@@ -96,13 +96,13 @@ void launch_acoustic(bool str, bool adj, const StepParams& p, const TmaSet& tm, 
     }
 }
 
-// sigma^22 = sigma^33 = sigma^11 on the ITEM_AC_DEEP items of an acoustic
-// list (one block per item; other items are left alone)
-__global__ void __launch_bounds__(NT) k_ac_fill(const float* __restrict__ s0, float* s1, float* s2, int nx, int ny,
-                                                RegionList rl) {
+// sigma^22 = sigma^33 = sigma^11 on the ITEM_DEEP items of a list (one block
+// per item; other items are left alone)
+__global__ void __launch_bounds__(NT) k_deep_fill(const float* __restrict__ s0, float* s1, float* s2, int nx, int ny,
+                                                  RegionList rl) {
     int tile_x, tile_y, zc0, zc1, kind;
     locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    if (kind != ITEM_AC_DEEP) return;
+    if (!(kind & ITEM_DEEP)) return;
     const int x = tile_x * TX + threadIdx.x, y = tile_y * TY + threadIdx.y;
     if (x >= nx || y >= ny) return;
     const size_t nxy = (size_t)nx * ny;
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(NT) k_ac_fill(const float* __restrict__ s0, fl
     }
 }
 
-void launch_ac_fill(const StepParams& p, const RegionList& ac, int blocks, cudaStream_t st) {
-    if (blocks > 0) k_ac_fill<<<blocks, dim3(TX, TY, 1), 0, st>>>(p.s[0], p.s[1], p.s[2], p.nx, p.ny, ac);
+void launch_deep_fill(const StepParams& p, const RegionList& rl, int blocks, cudaStream_t st) {
+    if (blocks > 0) k_deep_fill<<<blocks, dim3(TX, TY, 1), 0, st>>>(p.s[0], p.s[1], p.s[2], p.nx, p.ny, rl);
 }
 
 void launch_any_shear(const float* mu, size_t n, unsigned int* out, cudaStream_t st) {

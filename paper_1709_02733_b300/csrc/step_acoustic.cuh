@@ -144,7 +144,7 @@ __device__ __forceinline__ bool ac_vel_body(const StepParams& p, const CUtensorM
 // Stress half: output plane z = pl - 2; the z queue of u3 holds planes
 // z-2 .. z+1 (half->integer difference), so its head is plane pl - 1.
 template <bool ADJ>
-// all3 = false (an ITEM_AC_DEEP item, no elastic reader): sigma^11 only
+// all3 = false (an ITEM_DEEP item, no elastic reader): sigma^11 only
 __device__ __forceinline__ bool ac_str_body(const StepParams& p, const CUtensorMap* tmm, int tile_x, int tile_y,
                                             int zc0, int zc1, int* err, float* sm, bool all3 = true) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;

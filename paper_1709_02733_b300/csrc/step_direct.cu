@@ -344,7 +344,7 @@ __global__ void k_readout(const float* __restrict__ s0, const float* __restrict_
 }
 
 // sigma^11 + sigma^22 + sigma^33 at a receiver corner; a corner stored as ~q
-// lies in an item that writes sigma^11 alone (ITEM_AC_DEEP), where the three
+// lies in an item that writes sigma^11 alone (ITEM_DEEP), where the three
 // are equal: 3 sigma^11, bitwise the sum (s + s is exact, so both round 3 s once)
 __device__ __forceinline__ float corner_trace(const float* __restrict__ s0, const float* __restrict__ s1,
                                               const float* __restrict__ s2, int q) {

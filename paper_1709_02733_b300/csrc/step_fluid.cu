@@ -277,8 +277,9 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
 // stress family
 // ---------------------------------------------------------------------------
 template <bool ADJ, int PM>
+// all3 = false (an ITEM_DEEP item, no elastic reader): sigma^11 only
 __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y,
-                                               int zc0, int zc1, int* err, float* sm) {
+                                               int zc0, int zc1, int* err, float* sm, bool all3 = true) {
     using Cfg = StrFl<ADJ, PM>;
     constexpr bool LX = Cfg::LX, LY = Cfg::LY, PXY = Cfg::PXY;
     constexpr int NV = Cfg::NV, YV = LX ? 1 : 0;
@@ -457,8 +458,10 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
                     res = so - lam * (du[0] + du[1] + du[2]);
                 }
                 p.s_out[0][gi] = res;
-                p.s_out[1][gi] = res;
-                p.s_out[2][gi] = res;
+                if (all3) {
+                    p.s_out[1][gi] = res;
+                    p.s_out[2][gi] = res;
+                }
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -482,14 +485,16 @@ __global__ void __launch_bounds__(NT) k_fluid(StepParams p, const __grid_constan
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
+    const bool all3 = !(kind & ITEM_DEEP);
+    kind &= ~ITEM_DEEP;
     if constexpr (PM == PM_X) {
         if (kind == PM_Y) {
-            if (STR) str_fluid_body<ADJ, PM_Y>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+            if (STR) str_fluid_body<ADJ, PM_Y>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, all3);
             else vel_fluid_body<ADJ, PM_Y>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
             return;
         }
     }
-    if (STR) str_fluid_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    if (STR) str_fluid_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, all3);
     else vel_fluid_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
 }
 
@@ -535,16 +540,18 @@ __global__ void __launch_bounds__(NT) k_multi_fl(const MultiTable* __restrict__ 
     multi_loop<ADJ, ML_FL>(T, err, next, sm,
                            [](const StepParams& sp, const CUtensorMap* maps, int kind, int tile_x, int tile_y, int zc0,
                               int zc1, int* e, float* smem) {
+                               const bool all3 = !(kind & ITEM_DEEP);
+                               kind &= ~ITEM_DEEP;
                                if (kind == PM_Z)
-                                   return STR ? str_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                   return STR ? str_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
                                               : vel_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
                                if (kind == PM_X)
-                                   return STR ? str_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                   return STR ? str_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
                                               : vel_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
                                if (kind == PM_Y)
-                                   return STR ? str_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                                   return STR ? str_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
                                               : vel_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
-                               return STR ? str_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem)
+                               return STR ? str_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
                                           : vel_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
                            });
 }

@@ -1354,8 +1354,8 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
         }
     // near[z][t]: an elastic item within one tile in x and y and three planes
     // in z, i.e. within reach of an elastic body's sigma^22 / sigma^33 reads
-    // (two cells, two planes) with a margin.  A fluid no-layer item without it
-    // is ITEM_AC_DEEP (PACT_AC_DEEP=0: none is).
+    // (two cells, two planes) with a margin.  A fluid item without it is
+    // ITEM_DEEP (PACT_AC_DEEP=0: none is).
     std::vector<unsigned char> near(nflag, 1);
     const char* denv = getenv("PACT_AC_DEEP");
     if (!(denv && std::strcmp(denv, "0") == 0)) {
@@ -1436,11 +1436,10 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
                 li_fl = MX_CORNER_FL;
             }
             // runs of equal (solid, near) flags; near only matters for the
-            // fluid no-layer items
-            const bool ac = li_fl == MX_INT_AC;
+            // fluid items
             auto key = [&](int z) {
                 const unsigned char f = solid[(size_t)z * ntiles + t];
-                return (int)f * 2 + ((!f && ac) ? (int)near[(size_t)z * ntiles + t] : 0);
+                return (int)f * 2 + (!f ? (int)near[(size_t)z * ntiles + t] : 0);
             };
             int a = c0;
             while (a < c1) {
@@ -1448,8 +1447,8 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
                 int b = a + 1;
                 while (b < c1 && key(b) == kf) ++b;
                 const bool f = kf >= 2;
-                const bool deep = !f && ac && (kf & 1) == 0;
-                add(f ? li_el : li_fl, tx, ty, a, b, deep ? ITEM_AC_DEEP : kind);
+                const bool deep = !f && (kf & 1) == 0;
+                add(f ? li_el : li_fl, tx, ty, a, b, deep ? (kind | ITEM_DEEP) : kind);
                 if (deep) {
                     for (int z = a; z < b; ++z) mp->deep[(size_t)z * ntiles + t] = 1;
                     const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);

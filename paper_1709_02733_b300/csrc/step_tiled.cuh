@@ -136,13 +136,14 @@ enum {
     MX_CORNER_FL,    // frame corners, fluid
     MX_N
 };
-// Region.kind of a fluid no-layer item that no elastic item reads (no solid
-// within one tile in x and y and three planes in z): only elastic bodies read
-// sigma^22 and sigma^33 of other points, so the acoustic stress body writes
-// sigma^11 alone there.  The other two hold stale values until
-// launch_ac_fill copies sigma^11 into them (before an image read-out or a
-// wavefield copy), and the receiver sampler reads 3 sigma^11 at such points.
-constexpr int ITEM_AC_DEEP = 6;
+// Flag bit of Region.kind: a fluid item (acoustic or fluid C-PML) that no
+// elastic item reads (no solid within one tile in x and y and three planes in
+// z).  Only elastic bodies read sigma^22 and sigma^33 of other points, so the
+// fluid stress bodies write sigma^11 alone there.  The other two hold stale
+// values until launch_deep_fill copies sigma^11 into them (before an image
+// read-out or a wavefield copy), and the receiver sampler reads 3 sigma^11 at
+// such points.
+constexpr int ITEM_DEEP = 0x100;
 
 struct MixedPlan {
     RegionList list[MX_N];
@@ -151,20 +152,20 @@ struct MixedPlan {
     RegionList fluid_frame;      // MX_INT_FZ, MX_EDGE_FL, MX_CORNER_FL in one list (serving)
     int fluid_frame_blocks = 0;
     Region* mem = nullptr;       // device allocation behind the lists
-    // host map [z][tile] of the planes of ITEM_AC_DEEP items (tile = ty * ntx + tx)
+    // host map [z][tile] of the planes of ITEM_DEEP items (tile = ty * ntx + tx)
     unsigned char* deep = nullptr;
     int ntx = 0, nty = 0;
     long long deep_points = 0;
 };
-// Is grid point (x, y, z) in an ITEM_AC_DEEP item of the plan?  (tiles of
+// Is grid point (x, y, z) in an ITEM_DEEP item of the plan?  (tiles of
 // kTileX x kTileY points, the step kernels' tiles)
 constexpr int kTileX = 32, kTileY = 8;
 inline bool plan_deep(const MixedPlan& mp, int x, int y, int z) {
     if (!mp.deep) return false;
     return mp.deep[(size_t)z * mp.ntx * mp.nty + (size_t)(y / kTileY) * mp.ntx + x / kTileX] != 0;
 }
-// sigma^22 = sigma^33 = sigma^11 on the ITEM_AC_DEEP items of list ac (blocks = its blocks)
-void launch_ac_fill(const StepParams& p, const RegionList& ac, int blocks, cudaStream_t st);
+// sigma^22 = sigma^33 = sigma^11 on the ITEM_DEEP items of list rl (blocks = its blocks)
+void launch_deep_fill(const StepParams& p, const RegionList& rl, int blocks, cudaStream_t st);
 // Build the plan of the grid of p for the medium's mu (device array);
 // returns 0 on success (with no fluid item every list but the elastic ones is
 // empty), nonzero on a CUDA error.  Synchronises st.
