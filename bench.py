@@ -493,9 +493,12 @@ def run_ours(args):
         ac = {"fwd_velocity": "fwd_ac_vel", "fwd_stress": "fwd_ac_str", "adj_a": "adj_ac_a", "adj_b": "adj_ac_b"}.get(k)
         return ac if ac and prof[ac][0] == 0 and pts[ac][0] > 0 else None
 
+    deep = g.deep_points()  # stress-family points writing sigma^11 alone: 8 B fewer each
+
     def role_bytes(k):
         ac = merged_ac(k)
-        return algorithmic_bytes(k, d, L, *pts[k]) + (algorithmic_bytes(ac, d, L, *pts[ac]) if ac else 0)
+        b = algorithmic_bytes(k, d, L, *pts[k]) + (algorithmic_bytes(ac, d, L, *pts[ac]) if ac else 0)
+        return b - (8 * deep if k in ("fwd_stress", "adj_b") else 0)
 
     def role_points(k):
         ac = merged_ac(k)

@@ -353,6 +353,13 @@ int pact_profile_read(pact_handle h, int kind, long long* launches, double* tota
  * role's device time into algorithmic bytes per second.  Errors: PACT_EINVAL. */
 int pact_role_points(pact_handle h, int kind, long long* points, long long* slab_points);
 
+/* Grid points whose stress-family update writes sigma^11 alone (fluid work
+ * items of a medium with fluid and solid nodes that no solid node's update
+ * reads: sigma^22 and sigma^33 equal sigma^11 there and are filled in before
+ * they are read); 0 on other media.  The stress-family halves move 8 bytes
+ * fewer per such point.  Errors: PACT_EINVAL. */
+int pact_deep_points(pact_handle h, long long* points);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1303,6 +1303,12 @@ int pact_field_ptr(pact_handle h, int field, float** out) {
     return PACT_OK;
 }
 
+int pact_deep_points(pact_handle h, long long* points) {
+    if (!h || !points) return fail(h, PACT_EINVAL, "pact_deep_points: NULL argument");
+    *points = h->mixed ? h->mixed_plan.deep_points : 0;
+    return PACT_OK;
+}
+
 int pact_support_warning(pact_handle h, long long* n_points) {
     if (!h || !n_points) return fail(h, PACT_EINVAL, "pact_support_warning: NULL argument");
     unsigned long long c = 0;

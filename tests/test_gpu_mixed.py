@@ -151,6 +151,8 @@ def test_mixed_skull_512_split():
     n_ac = g.role_points("fwd_ac_vel")[0]
     assert 0.5 * w.desc.N < n_ac < 0.7 * w.desc.N
     assert g.role_points("fwd_velocity")[0] + n_ac == w.desc.N
+    # most of the water writes sigma^11 alone (no solid within a tile)
+    assert 0.4 * w.desc.N < g.deep_points() < n_ac + 0.3 * w.desc.N
     g.close()
 
 
@@ -169,6 +171,7 @@ def test_deep_items_write_sigma11_only_and_change_nothing(monkeypatch):
     monkeypatch.setenv("PACT_AC_DEEP", "0")
     g_a = make_grid(d, med)
     monkeypatch.delenv("PACT_AC_DEEP")
+    assert g_d.deep_points() > 0 and g_a.deep_points() == 0
     nsteps = 45
     tr_d = g_d.forward(cuda(p0), rec, nsteps)
     # inside the solve sigma^22 is stale on the deep items (raw device views)
