@@ -147,3 +147,35 @@ def test_continuous_batching_stream():
         assert np.all(np.isfinite(a)) and np.linalg.norm(b) > 0, r.rid
         assert np.linalg.norm(a - b) <= TOL_MIX * np.linalg.norm(b), r.rid
         assert r.done >= r.arrival
+
+
+@pytest.mark.parametrize("split", [None, "-1"])
+def test_deep_items_served(split, monkeypatch):
+    """A medium with deep fluid items (sigma^11 written alone far from the
+    solid) served by pact_advance, on the step graphs and on the
+    multi-instance kernels: the multi-instance receiver kernel reads 3 sigma^11
+    at deep corners and the read-out follows the fill of sigma^22, sigma^33."""
+    if split is not None:
+        monkeypatch.setenv("PACT_SERVE_SOLO_POINTS", split)
+    nz, ny, nx = 64, 64, 192
+    rng = np.random.default_rng(41)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    inside = ((x - 0.85 * nx) / 12.0) ** 2 + ((y - ny / 2) / 9.0) ** 2 + ((z - nz / 2) / 12.0) ** 2 <= 1.0
+    cp = np.where(inside, 2900.0, 1480.0)
+    cs = np.where(inside, 1400.0, 0.0)
+    rho = np.where(inside, 1850.0, 1000.0)
+    lam, mu = synth.lame_from_speeds(cp, cs, rho)
+    med = tuple(np.ascontiguousarray(a, dtype=np.float32) for a in (rho, lam, mu, np.zeros_like(rho)))
+    d = GridDesc(nx, ny, nz, 0.4e-3, 0.3 * 0.4e-3 / 2900.0, npml=4, pml_vmax=2900.0)
+    p0 = np.zeros((nz, ny, nx), np.float32)
+    p0[8:-8, 8:-8, 8:-8] = rng.standard_normal((nz - 16, ny - 16, nx - 16))
+    rec = synth.random_receivers(19, (nz, ny, nx), 42)
+    rec[:6] = [[40.0 + 8 * k, 30.0, 20.0 + 3 * k] for k in range(6)]  # deep in the water
+    cases = [("fwd", d, med, p0, rec, 33), ("adj", d, med, p0, rec, 29)]
+    g = pact.Grid(d)
+    g.set_medium(*[cuda(m) for m in med])
+    assert g.deep_points() > 0
+    g.close()
+    for (kind, *_rest), (_inp, got, ref) in zip(cases, _serve_mix(cases, k=6)):
+        assert np.all(np.isfinite(got)), kind
+        assert rel_l2(got, ref) <= TOL_MIX, kind

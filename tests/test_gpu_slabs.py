@@ -147,3 +147,22 @@ def test_create_slab_rejects():
     for lo, hi in ((-1, 10), (0, 41), (10, 14)):
         with pytest.raises(pact.PactError):
             pact.Grid(d, slab=(lo, hi))
+
+
+def test_slabs_with_deep_items():
+    """Slabs cut through a medium with deep fluid items (sigma^11 written
+    alone): the planes a slab exchanges are never deep, so the slabs match the
+    whole grid."""
+    d, med, p0, rec = _inclusion_case(shape=(64, 64, 192), npml=4, seed=45, L=17)
+    g = pact.Grid(d)
+    g.set_medium(*[cuda(m) for m in med])
+    assert g.deep_points() > 0
+    nsteps = 41
+    y = np.random.default_rng(11).standard_normal((nsteps + 1, len(rec))).astype(np.float32)
+    tr_w = g.forward(cuda(p0), rec, nsteps).cpu().numpy()
+    img_w = g.adjoint(cuda(y), rec).cpu().numpy()
+    for R in (2, 3):
+        sl, traces, image = _slab_solves(d, med, p0, rec, y, nsteps, R)
+        assert sum(s.grid.deep_points() for s in sl) > 0
+        assert rel_l2(traces, tr_w) <= TOL_WHOLE
+        assert rel_l2(image, img_w) <= TOL_WHOLE
