@@ -902,17 +902,22 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     // the interior runs the acoustic kernels unless PACT_ACOUSTIC=0
     const char* aenv = getenv("PACT_ACOUSTIC");
     const bool ac_ok = h->tiled && !h->fused && !(aenv && std::strcmp(aenv, "0") == 0);
-    h->acoustic = ac_ok && red[4] == 0 && role_points(3, STEP_ACOUSTIC, make_params(h)) > 0;  // needs a layer (see plan_for)
-    // mu > 0 somewhere: the interior work items whose reach is all fluid run
-    // the acoustic kernels (the same operator there); PACT_ACOUSTIC=0 keeps
-    // the elastic kernels everywhere
+    // The medium-adaptive plan: the work items whose reach is all fluid run
+    // the acoustic and fluid C-PML kernels (the same operator there), the rest
+    // the elastic ones; with mu = 0 everywhere every item is fluid.
+    // PACT_ACOUSTIC=0 keeps the elastic kernels everywhere.  Without a plan
+    // (no C-PML layer, or no interior tile) a medium with mu = 0 everywhere
+    // runs the no-layer region on the acoustic kernels when it can.
     h->mixed = false;
-    if (ac_ok && red[4] != 0) {
+    h->acoustic = false;
+    if (ac_ok) {
         if (build_mixed_plan(make_params(h), h->medium + 2 * h->N, s, &h->mixed_plan) != 0)
             return fail(h, PACT_ECUDA, "building the fluid / solid work lists of the medium failed");
         const long long* np = h->mixed_plan.points;
         h->mixed = np[MX_INT_AC] + np[MX_INT_FZ] + np[MX_EDGE_FL] + np[MX_CORNER_FL] > 0;
     }
+    if (!h->mixed)
+        h->acoustic = ac_ok && red[4] == 0 && role_points(3, STEP_ACOUSTIC, make_params(h)) > 0;  // needs a layer (see plan_for)
     h->medium_gen++;
     h->medium_set = true;
     return PACT_OK;
