@@ -1,6 +1,7 @@
 """The acoustic operator pair H_{mu=0}, H^T_{mu=0} (mu = 0 at every node, the
-paper's ablation): the interior runs the one-stress-field kernels of
-step_acoustic.cu and the C-PML frame the elastic kernels.  Checked against
+paper's ablation): every work item of the medium-adaptive plan is fluid, so the
+interior runs the one-stress-field kernels of step_acoustic.cu and the C-PML
+frame the fluid C-PML kernels of step_fluid.cu.  Checked against
 the FP64 oracle (the elastic operator with mu = 0, 1e-4 relative L2), against
 the elastic kernels on the same medium (PACT_ACOUSTIC=0; FP32 rounding), and
 by the inner-product test (1e-5)."""
