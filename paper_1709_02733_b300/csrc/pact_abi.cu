@@ -911,7 +911,7 @@ int pact_set_medium(pact_handle h, const float* rho, const float* lambda, const 
     h->mixed = false;
     h->acoustic = false;
     if (ac_ok) {
-        if (build_mixed_plan(make_params(h), h->medium + 2 * h->N, s, &h->mixed_plan) != 0)
+        if (build_mixed_plan(make_params(h), h->medium + 2 * h->N, h->medium + 3 * h->N, s, &h->mixed_plan) != 0)
             return fail(h, PACT_ECUDA, "building the fluid / solid work lists of the medium failed");
         const long long* np = h->mixed_plan.points;
         h->mixed = np[MX_INT_AC] + np[MX_INT_FZ] + np[MX_EDGE_FL] + np[MX_CORNER_FL] > 0;

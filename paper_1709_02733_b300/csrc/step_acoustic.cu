@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(NT) k_ac_vel(StepParams p, const __grid_consta
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    ac_vel_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    ac_vel_body<ADJ>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, !(kind & ITEM_NOALPHA));
 }
 
 template <bool ADJ>
@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(NT) k_multi_ac(const MultiTable* __restrict__ 
                               int zc1, int* e, float* smem) {
                                return STR ? ac_str_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem,
                                                              !(kind & ITEM_DEEP))
-                                          : ac_vel_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                                          : ac_vel_body<ADJ>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem,
+                                                             !(kind & ITEM_NOALPHA));
                            });
 }
 

@@ -70,9 +70,11 @@ __device__ __forceinline__ void drain(uint64_t* bar, int pfrom, int pto, int pfi
 
 // Velocity half: output plane z = pl - 2 for ring plane pl (the z queue of s
 // holds planes z-1 .. z+2 for the integer->half difference).
+// alpha = false (an ITEM_NOALPHA item: alpha = 0 at every node it reads):
+// the alpha box is not loaded, and the damping factors are 1 exactly
 template <bool ADJ>
 __device__ __forceinline__ bool ac_vel_body(const StepParams& p, const CUtensorMap* tmm, int tile_x, int tile_y,
-                                            int zc0, int zc1, int* err, float* sm) {
+                                            int zc0, int zc1, int* err, float* sm, bool alpha = true) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = (unsigned)(y0 + ty) * p.nx + (unsigned)(x0 + tx);
@@ -88,10 +90,11 @@ __device__ __forceinline__ bool ac_vel_body(const StepParams& p, const CUtensorM
     }
     __syncthreads();
     auto stage = [&](int pl) { return sm + (size_t)(((pl - pfirst) & (D - 1)) * NB) * BOXS; };
+    const int nb = alpha ? NB : NB - 1;  // the alpha box is the last one
     auto issue = [&](int pl) {
         const int k = pl - pfirst;
-        mbar_arrive_expect_tx(&bar[k & (D - 1)], NB * BOX * sizeof(float));
-        for (int b = 0; b < NB; ++b) tma_load_3d(stage(pl) + b * BOXS, maps[b], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+        mbar_arrive_expect_tx(&bar[k & (D - 1)], nb * BOX * sizeof(float));
+        for (int b = 0; b < nb; ++b) tma_load_3d(stage(pl) + b * BOXS, maps[b], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
@@ -121,8 +124,8 @@ __device__ __forceinline__ bool ac_vel_body(const StepParams& p, const CUtensorM
             const float g[3] = {dpx(sz, o) * h, dpy(sz, o) * h, dq(qs) * h};
             const float rb[3] = {0.5f * (r0[o] + r0[o + 1]), 0.5f * (r0[o] + r0[o + BW]),
                                  0.5f * (r0[o] + sz1[BOXS + o])};
-            const float ab[3] = {0.5f * (a0[o] + a0[o + 1]), 0.5f * (a0[o] + a0[o + BW]),
-                                 0.5f * (a0[o] + sz1[2 * BOXS + o])};
+            const float ab[3] = {alpha ? 0.5f * (a0[o] + a0[o + 1]) : 0.f, alpha ? 0.5f * (a0[o] + a0[o + BW]) : 0.f,
+                                 alpha ? 0.5f * (a0[o] + sz1[2 * BOXS + o]) : 0.f};
             const unsigned gi = (unsigned)z * nxy + gxy;
 #pragma unroll
             for (int i = 0; i < 3; ++i)

@@ -72,9 +72,10 @@ static_assert(VelFl<true, PM_X>::SMEM == VelFl<true, PM_Y>::SMEM && StrFl<true, 
 // ---------------------------------------------------------------------------
 // velocity family
 // ---------------------------------------------------------------------------
+// alpha = false (an ITEM_NOALPHA item): no alpha box, damping factors 1
 template <bool ADJ, int PM>
 __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtensorMap* maps, int tile_x, int tile_y,
-                                               int zc0, int zc1, int* err, float* sm) {
+                                               int zc0, int zc1, int* err, float* sm, bool alpha = true) {
     using Cfg = VelFl<ADJ, PM>;
     constexpr bool LX = Cfg::LX, LY = Cfg::LY, PXY = Cfg::PXY;
     constexpr int NV = Cfg::NV, YV = LX ? 1 : 0;  // buffered values per position; the y value
@@ -100,11 +101,13 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
         for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
+    static_assert(Cfg::BALPHA == Cfg::NB - 1, "the alpha box is the last one");
+    const int nb = alpha ? Cfg::NB : Cfg::NB - 1;
     auto issue = [&](int pl) {
         const int k = pl - pfirst;
         float* dst = ring.stage(pl);
-        mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
-        for (int b = 0; b < Cfg::NB; ++b)
+        mbar_arrive_expect_tx(&bar[k & (D - 1)], nb * BOX * sizeof(float));
+        for (int b = 0; b < nb; ++b)
             tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
@@ -234,8 +237,9 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
                 const float* a0 = sz + Cfg::BALPHA * BOXS;
                 const float rb[3] = {0.5f * (r0[o] + r0[o + xc1]), 0.5f * (r0[o] + r0[o + yc1]),
                                      0.5f * (r0[o] + sz1[Cfg::BRHO * BOXS + o])};
-                const float ab[3] = {0.5f * (a0[o] + a0[o + xc1]), 0.5f * (a0[o] + a0[o + yc1]),
-                                     0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o])};
+                const float ab[3] = {alpha ? 0.5f * (a0[o] + a0[o + xc1]) : 0.f,
+                                     alpha ? 0.5f * (a0[o] + a0[o + yc1]) : 0.f,
+                                     alpha ? 0.5f * (a0[o] + sz1[Cfg::BALPHA * BOXS + o]) : 0.f};
                 PmlZ pz{};
                 pml_z_init(pz, p, z);
                 const unsigned gi = (unsigned)z * nxy + gxy;
@@ -485,17 +489,17 @@ __global__ void __launch_bounds__(NT) k_fluid(StepParams p, const __grid_constan
     extern __shared__ __align__(128) float sm[];
     int tile_x, tile_y, zc0, zc1, kind;
     locate_item(rl, blockIdx.x, tile_x, tile_y, zc0, zc1, kind);
-    const bool all3 = !(kind & ITEM_DEEP);
-    kind &= ~ITEM_DEEP;
+    const bool all3 = !(kind & ITEM_DEEP), alpha = !(kind & ITEM_NOALPHA);
+    kind &= ~ITEM_FLAGS;
     if constexpr (PM == PM_X) {
         if (kind == PM_Y) {
             if (STR) str_fluid_body<ADJ, PM_Y>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, all3);
-            else vel_fluid_body<ADJ, PM_Y>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+            else vel_fluid_body<ADJ, PM_Y>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, alpha);
             return;
         }
     }
     if (STR) str_fluid_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, all3);
-    else vel_fluid_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm);
+    else vel_fluid_body<ADJ, PM>(p, tm.m, tile_x, tile_y, zc0, zc1, err, sm, alpha);
 }
 
 template <bool STR, bool ADJ, int PM>
@@ -540,19 +544,19 @@ __global__ void __launch_bounds__(NT) k_multi_fl(const MultiTable* __restrict__ 
     multi_loop<ADJ, ML_FL>(T, err, next, sm,
                            [](const StepParams& sp, const CUtensorMap* maps, int kind, int tile_x, int tile_y, int zc0,
                               int zc1, int* e, float* smem) {
-                               const bool all3 = !(kind & ITEM_DEEP);
-                               kind &= ~ITEM_DEEP;
+                               const bool all3 = !(kind & ITEM_DEEP), alpha = !(kind & ITEM_NOALPHA);
+                               kind &= ~ITEM_FLAGS;
                                if (kind == PM_Z)
                                    return STR ? str_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
-                                              : vel_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                                              : vel_fluid_body<ADJ, PM_Z>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, alpha);
                                if (kind == PM_X)
                                    return STR ? str_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
-                                              : vel_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                                              : vel_fluid_body<ADJ, PM_X>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, alpha);
                                if (kind == PM_Y)
                                    return STR ? str_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
-                                              : vel_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                                              : vel_fluid_body<ADJ, PM_Y>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, alpha);
                                return STR ? str_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, all3)
-                                          : vel_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem);
+                                          : vel_fluid_body<ADJ, PM_FULL>(sp, maps, tile_x, tile_y, zc0, zc1, e, smem, alpha);
                            });
 }
 

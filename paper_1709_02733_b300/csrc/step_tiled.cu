@@ -1299,8 +1299,9 @@ int launch_str_tiled(bool adj, const StepParams& p, const TmaSet& tm, int* err, 
 }
 
 // ---- medium-adaptive interior (STEP_MIXED) ---------------------------------
-// out[z * ntiles + t] = 1 if mu > 0 at any node of interior tile t's x-y reach
-// (x0-3 .. x0+TX+2, y0-3 .. y0+TY+2, clipped to the grid) on plane z.
+// out[z * ntiles + t] = 1 if mu > 0 (or, called on alpha, alpha > 0) at any
+// node of tile t's x-y reach (x0-3 .. x0+TX+2, y0-3 .. y0+TY+2, clipped to
+// the grid) on plane z.
 __global__ void k_tile_solid(const float* __restrict__ mu, int nx, int ny, int txlo, int tylo, int ntx, int nty,
                              unsigned char* __restrict__ out) {
     const int t = blockIdx.x, z = blockIdx.y;
@@ -1323,7 +1324,7 @@ void free_mixed_plan(MixedPlan* mp) {
     *mp = MixedPlan{};
 }
 
-int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, MixedPlan* mp) {
+int build_mixed_plan(const StepParams& p, const float* mu, const float* alpha, cudaStream_t st, MixedPlan* mp) {
     free_mixed_plan(mp);
     int txlo, txhi, tylo, tyhi;
     if (p.P <= 0 || !interior_tiles(p, txlo, txhi, tylo, tyhi)) return 0;
@@ -1334,13 +1335,28 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
     unsigned char* d_flag = nullptr;
     const size_t nflag = (size_t)p.nz * ntiles;
     if (cudaMalloc(&d_flag, nflag) != cudaSuccess) return 1;
+    // the same reach test on alpha > 0 (absorbing nodes)
     k_tile_solid<<<dim3(ntiles, p.nz), 256, 0, st>>>(mu, p.nx, p.ny, 0, 0, ntx, nty, d_flag);
-    std::vector<unsigned char> flag(nflag);
+    std::vector<unsigned char> flag(nflag), aflag(nflag);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, nflag, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) k_tile_solid<<<dim3(ntiles, p.nz), 256, 0, st>>>(alpha, p.nx, p.ny, 0, 0, ntx, nty, d_flag);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(aflag.data(), d_flag, nflag, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_flag);
     if (e != cudaSuccess) return 1;
+    // absorb[z][t]: an absorbing node where the velocity body of plane z reads
+    // alpha (planes z and z+1 of the reach); a fluid item without one is
+    // ITEM_NOALPHA (PACT_NOALPHA=0: none is)
+    std::vector<unsigned char> absorb(nflag, 1);
+    const char* aenv = getenv("PACT_NOALPHA");
+    if (!(aenv && std::strcmp(aenv, "0") == 0))
+        for (int z = 0; z < p.nz; ++z)
+            for (int t = 0; t < ntiles; ++t)
+                absorb[(size_t)z * ntiles + t] =
+                    aflag[(size_t)z * ntiles + t] | (z + 1 < p.nz ? aflag[(size_t)(z + 1) * ntiles + t] : 0);
     // solid[z][t]: a solid node within planes z-3 .. z+3 of tile t's reach;
     // on a slab of a larger grid the planes beyond its halo are unknown here,
     // so a reach that crosses a cut between slabs counts as solid
@@ -1435,20 +1451,21 @@ int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, Mixe
                 li_el = MX_CORNER_EL;
                 li_fl = MX_CORNER_FL;
             }
-            // runs of equal (solid, near) flags; near only matters for the
-            // fluid items
+            // runs of equal (solid, near, absorb) flags; near and absorb
+            // only matter for the fluid items
             auto key = [&](int z) {
-                const unsigned char f = solid[(size_t)z * ntiles + t];
-                return (int)f * 2 + (!f ? (int)near[(size_t)z * ntiles + t] : 0);
+                const size_t i = (size_t)z * ntiles + t;
+                const unsigned char f = solid[i];
+                return (int)f * 4 + (!f ? (int)near[i] * 2 + (int)absorb[i] : 0);
             };
             int a = c0;
             while (a < c1) {
                 const int kf = key(a);
                 int b = a + 1;
                 while (b < c1 && key(b) == kf) ++b;
-                const bool f = kf >= 2;
-                const bool deep = !f && (kf & 1) == 0;
-                add(f ? li_el : li_fl, tx, ty, a, b, deep ? (kind | ITEM_DEEP) : kind);
+                const bool f = kf >= 4;
+                const bool deep = !f && (kf & 2) == 0, noalpha = !f && (kf & 1) == 0;
+                add(f ? li_el : li_fl, tx, ty, a, b, kind | (deep ? ITEM_DEEP : 0) | (noalpha ? ITEM_NOALPHA : 0));
                 if (deep) {
                     for (int z = a; z < b; ++z) mp->deep[(size_t)z * ntiles + t] = 1;
                     const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);

@@ -144,6 +144,11 @@ enum {
 // read-out or a wavefield copy), and the receiver sampler reads 3 sigma^11 at
 // such points.
 constexpr int ITEM_DEEP = 0x100;
+// Flag bit of Region.kind: a fluid item whose velocity body reads alpha = 0 at
+// every node (the node and its +1 neighbours in x, y and z over the item's
+// tiles and planes): it loads no alpha box and its damping factors are 1.
+constexpr int ITEM_NOALPHA = 0x200;
+constexpr int ITEM_FLAGS = ITEM_DEEP | ITEM_NOALPHA;
 
 struct MixedPlan {
     RegionList list[MX_N];
@@ -169,7 +174,7 @@ void launch_deep_fill(const StepParams& p, const RegionList& rl, int blocks, cud
 // Build the plan of the grid of p for the medium's mu (device array);
 // returns 0 on success (with no fluid item every list but the elastic ones is
 // empty), nonzero on a CUDA error.  Synchronises st.
-int build_mixed_plan(const StepParams& p, const float* mu, cudaStream_t st, MixedPlan* mp);
+int build_mixed_plan(const StepParams& p, const float* mu, const float* alpha, cudaStream_t st, MixedPlan* mp);
 void free_mixed_plan(MixedPlan* mp);
 
 // Both return the number of kernels launched.  With mode STEP_MIXED, mp

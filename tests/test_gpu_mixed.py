@@ -160,8 +160,10 @@ def test_deep_items_write_sigma11_only_and_change_nothing(monkeypatch):
     """Fluid no-layer items with no elastic item within a tile and three planes
     write sigma^11 alone; the sampler reads 3 sigma^11 there and the three
     normal stresses are filled in before the image read-out and the wavefield
-    copy.  Traces, images and wavefields are bitwise those of the path that
-    writes all three everywhere (PACT_AC_DEEP=0), and match the FP64 oracle."""
+    copy.  Fluid items that read no absorbing node (ITEM_NOALPHA) load no
+    alpha box.  Traces, images and wavefields are bitwise those of the path
+    without either (PACT_AC_DEEP=0, PACT_NOALPHA=0), and match the FP64
+    oracle."""
     d, med, p0, rec = _inclusion_case(shape=(64, 64, 192), npml=4, seed=37, L=23, cx=0.85, rx=12.0)
     # receivers also deep inside the water, away from the inclusion
     rec[:8, 0] = np.linspace(36.0, 90.0, 8)
@@ -169,8 +171,10 @@ def test_deep_items_write_sigma11_only_and_change_nothing(monkeypatch):
     rec[:8, 2] = np.linspace(20.0, 44.0, 8)
     g_d = make_grid(d, med)
     monkeypatch.setenv("PACT_AC_DEEP", "0")
+    monkeypatch.setenv("PACT_NOALPHA", "0")
     g_a = make_grid(d, med)
     monkeypatch.delenv("PACT_AC_DEEP")
+    monkeypatch.delenv("PACT_NOALPHA")
     assert g_d.deep_points() > 0 and g_a.deep_points() == 0
     nsteps = 45
     tr_d = g_d.forward(cuda(p0), rec, nsteps)
