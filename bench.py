@@ -493,12 +493,14 @@ def run_ours(args):
         ac = {"fwd_velocity": "fwd_ac_vel", "fwd_stress": "fwd_ac_str", "adj_a": "adj_ac_a", "adj_b": "adj_ac_b"}.get(k)
         return ac if ac and prof[ac][0] == 0 and pts[ac][0] > 0 else None
 
-    deep = g.deep_points()  # stress-family points writing sigma^11 alone: 8 B fewer each
+    # medium-adaptive item classes: stress-family points writing sigma^11
+    # alone move 8 B fewer, velocity-family points loading no alpha 4 B fewer
+    deep, noalpha = g.deep_points(), g.noalpha_points()
 
     def role_bytes(k):
         ac = merged_ac(k)
         b = algorithmic_bytes(k, d, L, *pts[k]) + (algorithmic_bytes(ac, d, L, *pts[ac]) if ac else 0)
-        return b - (8 * deep if k in ("fwd_stress", "adj_b") else 0)
+        return b - (8 * deep if k in ("fwd_stress", "adj_b") else 4 * noalpha)
 
     def role_points(k):
         ac = merged_ac(k)

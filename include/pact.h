@@ -353,12 +353,17 @@ int pact_profile_read(pact_handle h, int kind, long long* launches, double* tota
  * role's device time into algorithmic bytes per second.  Errors: PACT_EINVAL. */
 int pact_role_points(pact_handle h, int kind, long long* points, long long* slab_points);
 
-/* Grid points whose stress-family update writes sigma^11 alone (fluid work
- * items of a medium with fluid and solid nodes that no solid node's update
- * reads: sigma^22 and sigma^33 equal sigma^11 there and are filled in before
- * they are read); 0 on other media.  The stress-family halves move 8 bytes
- * fewer per such point.  Errors: PACT_EINVAL. */
-int pact_deep_points(pact_handle h, long long* points);
+/* Work-item classes of the medium-adaptive step (media with fluid nodes):
+ * PACT_ITEM_DEEP, fluid points that no solid node's update reads, whose
+ * stress-family update writes sigma^11 alone (sigma^22 and sigma^33 equal it
+ * there and are filled in before they are read: 8 bytes fewer per point and
+ * stress half); PACT_ITEM_NOALPHA, fluid points whose velocity-family update
+ * reads alpha = 0 at every node and loads no alpha (4 bytes fewer per point
+ * and velocity half).  *points = grid points of that class; 0 on media
+ * without fluid nodes.  Errors: PACT_EINVAL (unknown class, NULL). */
+#define PACT_ITEM_DEEP 1
+#define PACT_ITEM_NOALPHA 2
+int pact_item_points(pact_handle h, int item_class, long long* points);
 
 #ifdef __cplusplus
 }

@@ -1308,9 +1308,11 @@ int pact_field_ptr(pact_handle h, int field, float** out) {
     return PACT_OK;
 }
 
-int pact_deep_points(pact_handle h, long long* points) {
-    if (!h || !points) return fail(h, PACT_EINVAL, "pact_deep_points: NULL argument");
-    *points = h->mixed ? h->mixed_plan.deep_points : 0;
+int pact_item_points(pact_handle h, int item_class, long long* points) {
+    if (!h || !points) return fail(h, PACT_EINVAL, "pact_item_points: NULL argument");
+    if (item_class != PACT_ITEM_DEEP && item_class != PACT_ITEM_NOALPHA)
+        return fail(h, PACT_EINVAL, "pact_item_points: item_class must be PACT_ITEM_DEEP or PACT_ITEM_NOALPHA");
+    *points = !h->mixed ? 0 : (item_class == PACT_ITEM_DEEP ? h->mixed_plan.deep_points : h->mixed_plan.noalpha_points);
     return PACT_OK;
 }
 

@@ -1466,11 +1466,12 @@ int build_mixed_plan(const StepParams& p, const float* mu, const float* alpha, c
                 const bool f = kf >= 4;
                 const bool deep = !f && (kf & 2) == 0, noalpha = !f && (kf & 1) == 0;
                 add(f ? li_el : li_fl, tx, ty, a, b, kind | (deep ? ITEM_DEEP : 0) | (noalpha ? ITEM_NOALPHA : 0));
+                const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);
                 if (deep) {
                     for (int z = a; z < b; ++z) mp->deep[(size_t)z * ntiles + t] = 1;
-                    const int ex = std::min(p.nx - tx * TX, TX), ey = std::min(p.ny - ty * TY, TY);
                     mp->deep_points += (long long)ex * ey * (b - a);
                 }
+                if (noalpha) mp->noalpha_points += (long long)ex * ey * (b - a);
                 a = b;
             }
         }

@@ -160,7 +160,7 @@ struct MixedPlan {
     // host map [z][tile] of the planes of ITEM_DEEP items (tile = ty * ntx + tx)
     unsigned char* deep = nullptr;
     int ntx = 0, nty = 0;
-    long long deep_points = 0;
+    long long deep_points = 0, noalpha_points = 0;
 };
 // Is grid point (x, y, z) in an ITEM_DEEP item of the plan?  (tiles of
 // kTileX x kTileY points, the step kernels' tiles)

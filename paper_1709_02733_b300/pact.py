@@ -29,7 +29,7 @@ EXPORTS = ["pact_create_grid", "pact_set_medium", "pact_forward", "pact_adjoint"
            "pact_adjoint_host", "pact_destroy", "pact_last_error", "pact_query_bytes", "pact_get_wavefield",
            "pact_profile", "pact_profile_read", "pact_role_points", "pact_forward_noalloc", "pact_begin",
            "pact_advance", "pact_poll", "pact_tv_prox_nn", "pact_resample_traces", "pact_check_bounded_wait",
-           "pact_support_warning", "pact_create_slab", "pact_step_half", "pact_step_receivers", "pact_field_ptr", "pact_deep_points"]
+           "pact_support_warning", "pact_create_slab", "pact_step_half", "pact_step_receivers", "pact_field_ptr", "pact_item_points"]
 
 # kernel roles of pact_profile_read (include/pact.h PACT_K_*)
 KINDS = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "sample", "inject", "source", "readout", "fwd_fused",
@@ -94,7 +94,7 @@ def load(path: str = SO_PATH):
     lib.pact_step_half.argtypes = [vp, i]
     lib.pact_step_receivers.argtypes = [vp]
     lib.pact_field_ptr.argtypes = [vp, i, ctypes.POINTER(ctypes.c_void_p)]
-    lib.pact_deep_points.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.pact_item_points.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTS:
         if name != "pact_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -377,10 +377,18 @@ class Grid:
 
     role_points = pact_role_points
 
-    def pact_deep_points(self) -> int:
-        """Grid points whose stress update writes sigma^11 alone."""
+    def pact_item_points(self, item_class: int) -> int:
+        """Grid points of a work-item class: 1 (PACT_ITEM_DEEP: the stress update
+        writes sigma^11 alone) or 2 (PACT_ITEM_NOALPHA: the velocity update
+        loads no alpha)."""
         n = ctypes.c_longlong(0)
-        _check(self.lib.pact_deep_points(self._h, ctypes.byref(n)), self._h)
+        _check(self.lib.pact_item_points(self._h, int(item_class), ctypes.byref(n)), self._h)
         return int(n.value)
 
-    deep_points = pact_deep_points
+    item_points = pact_item_points
+
+    def deep_points(self) -> int:
+        return self.pact_item_points(1)
+
+    def noalpha_points(self) -> int:
+        return self.pact_item_points(2)

@@ -176,6 +176,7 @@ def test_deep_items_write_sigma11_only_and_change_nothing(monkeypatch):
     monkeypatch.delenv("PACT_AC_DEEP")
     monkeypatch.delenv("PACT_NOALPHA")
     assert g_d.deep_points() > 0 and g_a.deep_points() == 0
+    assert g_d.noalpha_points() > 0 and g_a.noalpha_points() == 0
     nsteps = 45
     tr_d = g_d.forward(cuda(p0), rec, nsteps)
     # inside the solve sigma^22 is stale on the deep items (raw device views)
