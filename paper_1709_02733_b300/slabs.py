@@ -274,3 +274,41 @@ def assemble_image(slabs: List[Slab], outs):
     import torch
     order = sorted(range(len(slabs)), key=lambda i: slabs[i].r)
     return torch.cat([outs[i][slabs[i].owned] for i in order], dim=0)
+
+
+# -- results across processes (one slab per rank) ---------------------------------
+
+def dist_gather_traces(s: Slab, tr, L: int, group=None):
+    """The whole (nsteps+1, L) trace array on every rank, from each rank's
+    sampled columns: every column is sampled by exactly one slab, so a sum
+    all-reduce over zero-filled arrays gathers them exactly (x + 0 = x)."""
+    import torch
+    import torch.distributed as dist
+    full = torch.zeros((tr.shape[0], L), dtype=tr.dtype, device=tr.device)
+    if len(s.rec_idx):
+        full[:, torch.as_tensor(s.rec_idx, device=tr.device)] = tr
+    dist.all_reduce(full, group=group)
+    return full
+
+
+def dist_assemble_image(s: Slab, img, nz: int, group=None):
+    """The whole (nz, ny, nx) image on every rank from each rank's owned planes
+    (disjoint, so the sum all-reduce is exact)."""
+    import torch
+    import torch.distributed as dist
+    full = torch.zeros((nz,) + tuple(img.shape[1:]), dtype=img.dtype, device=img.device)
+    full[s.lo:s.hi] = img[s.owned]
+    dist.all_reduce(full, group=group)
+    return full
+
+
+def dist_dot(a, b, group=None) -> float:
+    """sum(a * b) over all ranks in float64 (one scalar all-reduce): the
+    partial sums of the inner-product test <H p, y> = <p, H^T y> when each
+    rank holds its own columns (traces) or owned planes (images)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float((a.double() * b.double()).sum())], dtype=torch.float64,
+                     device=a.device)
+    dist.all_reduce(t, group=group)
+    return float(t.item())

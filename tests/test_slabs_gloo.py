@@ -8,7 +8,9 @@
   differences that reach two planes, receivers sampled and injected on two
   planes, zero outside the held planes) run slab by slab with DistExchange
   gives bitwise the traces and image of the same stand-in on the whole grid,
-  with receivers on both sides of the cuts.  A missing or misordered
+  with receivers on both sides of the cuts, and every rank assembles the
+  whole traces and image exactly (sum all-reduces over disjoint parts) and the
+  inner products' partial sums (one scalar all-reduce each).  A missing or misordered
   exchange, a wrong halo slice, or a receiver sampled twice or injected on the
   wrong slabs changes the result.
 """
@@ -203,7 +205,14 @@ def _rank(rank, world, port, out):
         ex = slabs.DistExchange()
         tr = slabs.forward([s], [p0[s.zl:s.zh].contiguous()], NSTEPS, ex)[0]
         img = slabs.adjoint([s], [y[:, torch.as_tensor(s.inj_idx, dtype=torch.long)].contiguous()], NSTEPS, ex)[0]
-        out[rank] = (s.rec_idx, tr.numpy().copy(), s.lo, s.hi, img[s.owned].numpy().copy())
+        # the whole results on every rank, and the inner products' partial sums
+        full_tr = slabs.dist_gather_traces(s, tr, len(rec))
+        full_img = slabs.dist_assemble_image(s, img, NZ)
+        own = torch.as_tensor(s.rec_idx, dtype=torch.long)
+        lhs = slabs.dist_dot(tr, y[:, own].to(tr.dtype))
+        rhs = slabs.dist_dot(img[s.owned], p0[s.lo:s.hi].to(img.dtype))
+        out[rank] = (s.rec_idx, tr.numpy().copy(), s.lo, s.hi, img[s.owned].numpy().copy(),
+                     full_tr.numpy().copy(), full_img.numpy().copy(), lhs, rhs)
     finally:
         dist.destroy_process_group()
 
@@ -225,11 +234,18 @@ def test_slab_march_equals_whole_grid(world):
     L = tr_w.shape[1]
     seen = np.zeros(L, int)
     img = np.zeros((NZ, NY, NX))
+    p0, _rec, y = _problem()
+    lhs_w = float((tr_w.double() * y.to(tr_w.dtype).double()).sum())
+    rhs_w = float((img_w.double() * p0.to(img_w.dtype).double()).sum())
     for r in range(world):
-        idx, tr, lo, hi, im = got[r]
+        idx, tr, lo, hi, im, full_tr, full_img, lhs, rhs = got[r]
         seen[idx] += 1
         assert np.array_equal(tr, tr_w.numpy()[:, idx])
         img[lo:hi] = im
+        # every rank holds the whole traces and image, exactly
+        assert np.array_equal(full_tr, tr_w.numpy())
+        assert np.array_equal(full_img, img_w.numpy())
+        assert abs(lhs - lhs_w) <= 1e-12 * abs(lhs_w) and abs(rhs - rhs_w) <= 1e-12 * abs(rhs_w)
     assert np.all(seen == 1)
     assert np.array_equal(img, img_w.numpy())
     assert np.abs(img).max() > 0 and np.abs(tr_w.numpy()).max() > 0
