@@ -19,8 +19,10 @@
 //   stress    psi^^kk <- b_k (psi^^kk + chi_k Q)  (deferred tail, own point;
 //             the off-diagonal psi^^ij stay zero, they are driven by the shear Q),
 //             Q <- Q - lambda sum_k D_k E^kk,  E^kk = w^k + a_k (phi~^kk + chi_k w^k)
-// F and E are formed at the cross positions of the x and y layers exactly as
-// in the elastic kernels, for the diagonal components only.  The off-diagonal
+// F and E are formed at the cross positions of the x and y layers as in the
+// elastic kernels, for the diagonal components only, but as each plane
+// arrives, two planes before it is differenced, so that the end-of-plane
+// barrier orders them and no barrier sits between forming and differencing.  The off-diagonal
 // adjoint memory variables of a fluid item's nodes matter nowhere: psi^^ij
 // and F^ij stay zero (the shear Q is zero), and phi~^ij enters only E^ij,
 // which only the shear update of a node within two cells reads; every such
@@ -41,8 +43,8 @@ namespace {
 template <bool ADJ, int PM> struct VelFl {
     static constexpr bool LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
     static constexpr int NB = 3, BS = 0, BRHO = 1, BALPHA = 2;  // s (or Q), rho, alpha
-    static constexpr int NDER = (ADJ && PXY) ? 1 : 0;           // F22 at the y-band positions
     static constexpr int NV = (LX ? 1 : 0) + (LY ? 1 : 0);      // psi^ values per cross position
+    static constexpr int NDER = (ADJ && PXY) ? D * NV : 0;      // F11 / F22 boxes, one set per ring stage
     static constexpr int MV = ADJ ? 2 * NV * NCROSS : 0;
     static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
     __host__ __device__ static constexpr int tm(int b) { return b == 0 ? TM_S0 : (b == 1 ? TM_RHO : TM_ALPHA); }
@@ -51,7 +53,7 @@ template <bool ADJ, int PM> struct VelFl {
 template <bool ADJ, int PM> struct StrFl {
     static constexpr bool LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
     static constexpr int NB = 4, BLAM = 3;                      // u^1, u^2, u^3 (or w), lambda
-    static constexpr int NDER = (ADJ && PXY) ? 1 : 0;           // E22 at the y-band positions
+    static constexpr int NDER = 0;                              // E11, E22 formed in place
     static constexpr int NV = (LX ? 1 : 0) + (LY ? 1 : 0);      // phi~ values per cross position
     static constexpr int MV = ADJ ? 2 * NV * NCROSS : 0;
     static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
@@ -165,9 +167,10 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
         prefetch(z + 1);
         prefetch_head(pl + 1);
         // adjoint layers: copy psi^xx (x band) and psi^yy (y rows) at the cross
-        // positions of plane z + 1 into its buffer slot
+        // positions of plane pl + 1 into its buffer slot (each thread reads
+        // back only its own copies)
         if constexpr (ADJ && PXY) {
-            const int zn = z + 1;
+            const int zn = pl + 1;
             if (zn >= zc0 && zn < zc1) {
                 float* dst = mvb + (size_t)(zn & 1) * NV * NCROSS + tid;
 #pragma unroll
@@ -193,43 +196,52 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
                 }
             }
             push(qs, h33);
-        }
-        if (out) {
-            float* szw = ring.stage(z);
-            const float* sz = szw;
-            const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
-            const float* XD = sz;  // s / F11
-            const float* YD = sz;  // s / F22
             if constexpr (ADJ && PXY) {
-                // F11 = Q + a (psi^xx + chi Q) in place at the x-band positions,
-                // F22 = Q + a (psi^yy + chi Q) in the extra box at the y-band ones
-                // (off the x layer F11 = Q, which the box holds already; both
-                // derivatives read the one Q box, so the y-band positions always
-                // get F22 in the extra box: the in-place F11 must not reach them)
-                float* E = der;
-                if (ok) {
+                // F11 = Q + a (psi^xx + chi Q) at the x-band positions and
+                // F22 = Q + a (psi^yy + chi Q) at the y-band ones of plane pl,
+                // formed as the plane arrives into the extra boxes of its ring
+                // stage (the Q box stays as loaded).  They are differenced two
+                // planes later: the end-of-plane barriers in between order
+                // these writes before every read.
+                if (pl >= zc0 && pl < zc1) {
+                    const float* sq = ring.stage(pl);
+                    float* e = der + (size_t)(kk & (D - 1)) * NV * BOXS;
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const unsigned char f = cross.f[k];
                         const int q = cross.q[k];
-                        const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
-                        const float qv = sz[q];  // Q, read before F11 replaces it in place
-                        if (LX && cpm.sx[k] >= 0) {
-                            const float* t = cxt + cross.cxi[k];
-                            szw[q] = qv + t[0] * (mv[0] + t[BW] * qv);
+                        const float* mv = mvb + (size_t)(pl & 1) * NV * NCROSS + k * NT + tid;
+                        if (LX && (f & CP_XB)) {
+                            const float qv = sq[q];
+                            float f11 = qv;
+                            if (cpm.sx[k] >= 0) {
+                                const float* t = cxt + cross.cxi[k];
+                                f11 += t[0] * (mv[0] + t[BW] * qv);
+                            }
+                            e[q] = f11;
                         }
-                        if (f & CP_YB) {
+                        if (LY && (f & CP_YB)) {
+                            const float qv = sq[q];
                             float f22 = qv;
-                            if (LY && cpm.sy[k] >= 0) {
+                            if (cpm.sy[k] >= 0) {
                                 const float* t = cyt + cross.cyi[k];
                                 f22 += t[0] * (mv[YV * NCROSS] + t[BH] * qv);
                             }
-                            E[q] = f22;
+                            e[YV * BOXS + q] = f22;
                         }
                     }
                 }
-                __syncthreads();
-                YD = E;
+            }
+        }
+        if (out) {
+            const float* sz = ring.stage(z);
+            const float* sz1 = (z + 1 < p.nz) ? ring.stage(z + 1) : sz;
+            const float* XD = sz;  // s / F11
+            const float* YD = sz;  // s / F22
+            if constexpr (ADJ && PXY) {
+                const float* e = der + (size_t)((z - pfirst) & (D - 1)) * NV * BOXS;
+                if constexpr (LX) XD = e;
+                if constexpr (LY) YD = e + YV * BOXS;
             }
             if (ok && own) {
                 const float g[3] = {dpx(XD, o) * h, dpy(YD, o) * h, dq(qs) * h};
@@ -367,9 +379,10 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
         prefetch(z + 1);
         prefetch_head(pl + 1);
         // adjoint layers: copy phi~^xx (x band) and phi~^yy (y rows) at the
-        // cross positions of plane z + 1 into its buffer slot
+        // cross positions of plane pl + 1 into its buffer slot (each thread
+        // reads back only its own copies)
         if constexpr (ADJ && PXY) {
-            const int zn = z + 1;
+            const int zn = pl + 1;
             if (zn >= zc0 && zn < zc1) {
                 float* dst = mvb + (size_t)(zn & 1) * NV * NCROSS + tid;
 #pragma unroll
@@ -397,43 +410,39 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
                 }
             }
             push(qz, hz);
-        }
-        if (out) {
-            float* szw = ring.stage(z);
-            const float* sz = szw;
-            const float* XD0 = sz;         // u^1 / E11 (D-x)
-            const float* YD0 = sz + BOXS;  // u^2 / E22 (D-y)
             if constexpr (ADJ && PXY) {
-                // E11 = w1 + a (phi~xx + chi w1) in place at the x-band positions,
-                // E22 = w2 + a (phi~yy + chi w2) in the extra box at the y-band ones
-                // (off the x layer E11 = w1, which the box holds already;
-                // without a y layer E22 = w2 and the y derivative reads the box)
-                float* E0 = der;
-                if (ok) {
+                // E11 = w1 + a (phi~xx + chi w1) in place in the w1 box at the
+                // x-band positions and E22 = w2 + a (phi~yy + chi w2) in the w2
+                // box at the y-band ones of plane pl, as the plane arrives (off
+                // the layers E = w, which the boxes hold already; each box is
+                // read by one difference only).  They are differenced two planes
+                // later, after the end-of-plane barriers in between.
+                if (pl >= zc0 && pl < zc1) {
+                    float* sw = ring.stage(pl);
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const unsigned char f = cross.f[k];
                         const int q = cross.q[k];
-                        const float* mv = mvb + (size_t)(z & 1) * NV * NCROSS + k * NT + tid;
+                        const float* mv = mvb + (size_t)(pl & 1) * NV * NCROSS + k * NT + tid;
                         if (LX && cpm.sx[k] >= 0) {
-                            const float wx = sz[q];
+                            const float wx = sw[q];
                             const float* t = cxt + cross.cxi[k];
-                            szw[q] = wx + t[2 * BW] * (mv[0] + t[3 * BW] * wx);
+                            sw[q] = wx + t[2 * BW] * (mv[0] + t[3 * BW] * wx);
                         }
-                        if (LY && (f & CP_YB)) {
-                            const float wy = sz[BOXS + q];
-                            float eyy = wy;
-                            if (cpm.sy[k] >= 0) {
-                                const float* t = cyt + cross.cyi[k];
-                                eyy += t[2 * BH] * (mv[YV * NCROSS] + t[3 * BH] * wy);
-                            }
-                            E0[q] = eyy;
+                        if (LY && cpm.sy[k] >= 0) {
+                            const float wy = sw[BOXS + q];
+                            const float* t = cyt + cross.cyi[k];
+                            sw[BOXS + q] = wy + t[2 * BH] * (mv[YV * NCROSS] + t[3 * BH] * wy);
                         }
                     }
+                    // these generic writes precede the TMA load that refills the stage
+                    fence_proxy_async_smem();
                 }
-                __syncthreads();
-                if constexpr (LY) YD0 = E0;
             }
+        }
+        if (out) {
+            const float* sz = ring.stage(z);
+            const float* XD0 = sz;         // u^1 / E11 (D-x)
+            const float* YD0 = sz + BOXS;  // u^2 / E22 (D-y)
             if (ok && own) {
                 const float du[3] = {dmx(XD0, o) * h, dmy(YD0, o) * h, dq(qz) * h};
                 PmlZ pz{};
@@ -509,16 +518,24 @@ size_t fluid_smem_of() {
 
 // Shared memory first in the unified L1 / shared-memory array (the bodies
 // stage through TMA, not L1), so that shared memory does not cap the blocks
-// per SM below the register limit; set once per kernel and device.
+// per SM below the register limit, and the dynamic shared memory of each
+// layout allowed (the adjoint corner layout is above the 48 KB default); set
+// once per kernel and device.
+template <bool STR, bool ADJ, int PM>
+void fluid_attrs() {
+    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fluid_smem_of<STR, ADJ, PM>());
+}
 template <bool STR, bool ADJ>
 void prefer_shared() {
     static bool done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM_Z>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM_X>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_fluid<STR, ADJ, PM_FULL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    fluid_attrs<STR, ADJ, PM_Z>();
+    fluid_attrs<STR, ADJ, PM_X>();
+    fluid_attrs<STR, ADJ, PM_FULL>();
     done[dev] = true;
 }
 

@@ -150,8 +150,13 @@ __device__ __forceinline__ float harm_inv(float a, float b, float c, float d) {
 // OY..OY+TY-1, columns OX-2..OX+TX+1) and four y rows (OY-2, OY-1, OY+TY,
 // OY+TY+1; columns OX..OX+TX-1): 416 positions, at most two per thread.  The
 // positions a thread owns are the same on every plane, so their box index,
-// clamped +x / +y neighbour offsets and band flags are computed once.
+// clamped +x / +y neighbour offsets and band flags are computed once.  A
+// thread's first position is its own point; the second, for the first 160
+// threads, is one of the 32 x-halo positions (four columns by TY rows) or one
+// of the 128 y-row positions, so that a warp's positions lie in one box row
+// (no shared-memory bank conflicts) except on the x-halo warp.
 constexpr int NCROSS = (TX + 4) * TY + 4 * TX;
+static_assert(NCROSS == NT + 4 * TY + 4 * TX && NCROSS <= 2 * NT, "two cross positions per thread");
 constexpr unsigned char CP_EXISTS = 1, CP_IN = 2, CP_XB = 4, CP_YB = 8;
 struct CrossPos {
     int q[2];
@@ -171,13 +176,18 @@ __device__ __forceinline__ void cross_init(CrossPos& c, int tid, int x0, int y0,
         if (i >= NCROSS) continue;
         int bx, by;
         bool inx, iny;
-        if (i < (TX + 4) * TY) {
-            bx = OX - 2 + i % (TX + 4);
-            by = OY + i / (TX + 4);
+        if (i < NT) {  // own point
+            bx = OX + i % TX;
+            by = OY + i / TX;
+            inx = iny = true;
+        } else if (i < NT + 4 * TY) {  // x halo: columns OX-2, OX-1, OX+TX, OX+TX+1
+            const int j = i - NT, c = j % 4;
+            bx = c < 2 ? OX - 2 + c : OX + TX - 2 + c;
+            by = OY + j / 4;
             inx = true;
-            iny = bx >= OX && bx < OX + TX;
-        } else {
-            const int j = i - (TX + 4) * TY, r = j / TX;
+            iny = false;
+        } else {  // y rows
+            const int j = i - NT - 4 * TY, r = j / TX;
             bx = OX + j % TX;
             by = r < 2 ? OY - 2 + r : OY + TY - 2 + r;
             inx = false;

@@ -83,6 +83,12 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses of the same shared memory
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Asynchronous 4-byte global -> shared copy (per-thread, no registers held
 // while in flight); groups are committed and waited for by the issuing thread.
 __device__ __forceinline__ void cp_async_4(void* smem_dst, const void* gsrc) {
