@@ -30,8 +30,10 @@
 // item's reach), so its shear modulus, and the weight of E^ij, is zero.
 //
 // Bytes per grid point against the elastic frame bodies: the velocity body
-// stages s, rho, alpha (3 boxes for 8), the stress body u x3, lambda (4 for
-// 5) and writes three stresses instead of six.  The stress body writes s to
+// stages s, rho, alpha (3 boxes for 8; s alone on the two planes beyond the
+// item that only feed its z queue), the stress body u^1 and u^2 (2 boxes for
+// 5; u^3 and lambda are read at the own point only, and come from own-point
+// loads) and writes three stresses instead of six.  The stress body writes s to
 // all three normal-stress arrays so that elastic neighbours read consistent
 // fields; the shear arrays stay zero.
 #include <algorithm>
@@ -52,12 +54,12 @@ template <bool ADJ, int PM> struct VelFl {
 
 template <bool ADJ, int PM> struct StrFl {
     static constexpr bool LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
-    static constexpr int NB = 4, BLAM = 3;                      // u^1, u^2, u^3 (or w), lambda
+    static constexpr int NB = 2;                                // u^1, u^2 (or w)
     static constexpr int NDER = 0;                              // E11, E22 formed in place
     static constexpr int NV = (LX ? 1 : 0) + (LY ? 1 : 0);      // phi~ values per cross position
     static constexpr int MV = ADJ ? 2 * NV * NCROSS : 0;
     static constexpr size_t SMEM = ((size_t)(D * NB + NDER) * BOXS + MV) * sizeof(float) + D * sizeof(uint64_t);
-    __host__ __device__ static constexpr int tm(int b) { return b < 3 ? TM_U0 + b : TM_LAM; }
+    __host__ __device__ static constexpr int tm(int b) { return TM_U0 + b; }
 };
 
 // the persistent kernel runs every fluid body with the corner layout
@@ -85,7 +87,9 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < p.nx && y < p.ny;
-    const int pfirst = zc0 - 2, plast = zc1 + 1;
+    // ring planes zc0-1 .. zc1+1: the outer two feed only the z queue (their
+    // s box alone is staged)
+    const int pfirst = zc0 - 1, plast = zc1 + 1;
     const Ring ring{sm, Cfg::NB, pfirst};
     float* der = sm + (size_t)D * Cfg::NB * BOXS;
     float* mvb = der + (size_t)Cfg::NDER * BOXS;
@@ -103,13 +107,14 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
         for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
-    static_assert(Cfg::BALPHA == Cfg::NB - 1, "the alpha box is the last one");
+    static_assert(Cfg::BALPHA == Cfg::NB - 1 && Cfg::BS == 0, "s box first, alpha box last");
     const int nb = alpha ? Cfg::NB : Cfg::NB - 1;
     auto issue = [&](int pl) {
         const int k = pl - pfirst;
+        const int n = (pl < zc0 || pl > zc1) ? 1 : nb;
         float* dst = ring.stage(pl);
-        mbar_arrive_expect_tx(&bar[k & (D - 1)], nb * BOX * sizeof(float));
-        for (int b = 0; b < nb; ++b)
+        mbar_arrive_expect_tx(&bar[k & (D - 1)], n * BOX * sizeof(float));
+        for (int b = 0; b < n; ++b)
             tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
@@ -277,11 +282,14 @@ __device__ __forceinline__ bool vel_fluid_body(const StepParams& p, const CUtens
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
-            drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
+            drain(bar, pl, min(plast, max(pfirst + D - 1, pl + 1)), pfirst);
             if constexpr (ADJ && PXY) cp_async_wait<0>();
             return false;
         }
-        if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
+        // the stage of plane z (= pl + 2 modulo the ring) is free once every
+        // thread has passed the barrier above; planes up to pfirst + D - 1
+        // were issued before the loop
+        if (tid == 0 && pl + 2 >= pfirst + D && pl + 2 <= plast) issue(pl + 2);
     }
     if constexpr (ADJ && PXY) cp_async_wait<0>();
     if (tid == 0)
@@ -303,7 +311,9 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
     const int x0 = tile_x * TX, y0 = tile_y * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < p.nx && y < p.ny;
-    const int pfirst = zc0 - 2, plast = zc1 + 1;
+    // ring planes zc0 .. zc1-1, the planes differenced in x and y (u^1, u^2
+    // boxes); the u^3 queue and lambda come from own-point loads
+    const int pfirst = zc0, plast = zc1 - 1;
     const Ring ring{sm, Cfg::NB, pfirst};
     float* der = sm + (size_t)D * Cfg::NB * BOXS;
     float* mvb = der + (size_t)Cfg::NDER * BOXS;
@@ -312,6 +322,13 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
     const float dt = p.dt, h = p.inv_dx;
     const int P = p.P;
     const unsigned nxy = (unsigned)p.nx * p.ny, gxy = own ? (unsigned)y * p.nx + x : 0u;
+    // u^3 (adjoint: w^3) at the own point of plane zq (0 off the grid, as the TMA fill)
+    auto u3at = [&](int zq) {
+        return (own && zq >= 0 && zq < p.nz) ? p.u[2][(unsigned)zq * nxy + gxy] : 0.f;
+    };
+    // u^3 of the next three queue planes (planes zc0-2 .. zc0 first), loaded
+    // three iterations before they enter the queue
+    float f0 = u3at(zc0 - 2), f1 = u3at(zc0 - 1), f2 = u3at(zc0);
     PmlXY px{};
     if constexpr (PXY) pml_xy_init<LX, LY>(px, p, x, y, own);
 
@@ -346,13 +363,15 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
     }
 
     // own-point values of the next output plane, loaded one visit ahead: the
-    // old s (or Q) and psi^kk (forward) / psi^^kk (adjoint) on the layer of axis k
-    float ns = 0.f;
+    // old s (or Q), lambda and psi^kk (forward) / psi^^kk (adjoint) on the
+    // layer of axis k
+    float ns = 0.f, nl = 0.f;
     float nps[3] = {0.f, 0.f, 0.f};
     auto prefetch = [&](int zn) {
         if (!own || zn < zc0 || zn >= zc1) return;
         const unsigned g = (unsigned)zn * nxy + gxy;
         ns = p.s[0][g];
+        nl = __ldg(p.lam + g);
         const int lz = zslab(zn, p);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
@@ -368,16 +387,21 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
             if (l >= 0) nhp = p.phi[2][2][((unsigned)l * p.ny + y) * p.nx + x];
         }
     };
-    prefetch_head(pfirst);
+    prefetch_head(zc0 - 1);
 
-    for (int pl = pfirst; pl <= plast; ++pl) {
+    // queue plane pl - 1 enters at visit pl; output plane z = pl - 2
+    for (int pl = zc0 - 1; pl <= zc1 + 1; ++pl) {
         const int z = pl - 2;
         const bool out = z >= zc0;
-        const float so = ns;
+        const float so = ns, lam = nl;
         const float cps[3] = {nps[0], nps[1], nps[2]};
         const float chp = nhp;
         prefetch(z + 1);
         prefetch_head(pl + 1);
+        float hz = f0;  // u^3 (adjoint: w^3) of plane pl - 1
+        f0 = f1;
+        f1 = f2;
+        if (pl + 2 <= zc1) f2 = u3at(pl + 2);
         // adjoint layers: copy phi~^xx (x band) and phi~^yy (y rows) at the
         // cross positions of plane pl + 1 into its buffer slot (each thread
         // reads back only its own copies)
@@ -396,15 +420,17 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
             cp_async_commit();
             cp_async_wait<1>();
         }
-        const int kk = pl - pfirst;
-        const bool ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
-        const float* spm = (pl - 1 >= pfirst) ? ring.stage(pl - 1) : nullptr;
+        const bool staged = pl >= zc0 && pl < zc1;
+        bool ok = true;
+        if (staged) {
+            const int kk = pl - pfirst;
+            ok = mbar_wait_bounded(&bar[kk & (D - 1)], (kk / D) & 1);
+        }
         if (ok) {
-            float hz = spm ? spm[2 * BOXS + o] : 0.f;
             if constexpr (ADJ) {
                 // z-layer term of E33 (half lattice, plane pl-1)
                 const int zm = pl - 1;
-                if (own && spm && zm >= 0 && zm < p.nz && zslab(zm, p) >= 0) {
+                if (own && zm >= 0 && zm < p.nz && zslab(zm, p) >= 0) {
                     const float a = tabv(p, 2, 1, 0, zm), c = tabv(p, 2, 1, 2, zm);
                     hz += a * (chp + c * hz);
                 }
@@ -417,7 +443,7 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
                 // the layers E = w, which the boxes hold already; each box is
                 // read by one difference only).  They are differenced two planes
                 // later, after the end-of-plane barriers in between.
-                if (pl >= zc0 && pl < zc1) {
+                if (staged) {
                     float* sw = ring.stage(pl);
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
@@ -447,7 +473,6 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
                 const float du[3] = {dmx(XD0, o) * h, dmy(YD0, o) * h, dq(qz) * h};
                 PmlZ pz{};
                 pml_z_init(pz, p, z);
-                const float lam = sz[Cfg::BLAM * BOXS + o];
                 const unsigned gi = (unsigned)z * nxy + gxy;
                 float res;
                 if constexpr (!ADJ) {
@@ -479,11 +504,15 @@ __device__ __forceinline__ bool str_fluid_body(const StepParams& p, const CUtens
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
-            drain(bar, pl, min(plast, max(pfirst + D - 1, pl - 3 + D)), pfirst);
+            // a failed wait is on a staged plane pl; drain it and the later ones issued
+            drain(bar, pl, min(plast, max(pfirst + D - 1, pl + 1)), pfirst);
             if constexpr (ADJ && PXY) cp_async_wait<0>();
             return false;
         }
-        if (tid == 0 && pl >= zc0 && pl - 2 + D <= plast) issue(pl - 2 + D);
+        // the stage of plane z (= pl + 2 modulo the ring) is free once every
+        // thread has passed the barrier above; planes up to pfirst + D - 1
+        // were issued before the loop
+        if (tid == 0 && pl + 2 >= pfirst + D && pl + 2 <= plast) issue(pl + 2);
     }
     if constexpr (ADJ && PXY) cp_async_wait<0>();
     if (tid == 0)
