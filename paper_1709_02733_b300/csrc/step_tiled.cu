@@ -82,12 +82,21 @@ __device__ __forceinline__ bool vel_body(const StepParams& p, const CUtensorMap*
         for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
+    // boxes a ring plane needs: the item's planes all of them; the planes
+    // beyond it feed only the z queues (sigma^13 and sigma^23 of plane pl-1,
+    // sigma^33 of plane pl) and, on plane zc1, the z averages of rho and alpha
+    // (box order sigma^11, 22, 33, 23, 13, 12, rho, alpha)
+    auto boxes = [&](int pl) -> unsigned {
+        const unsigned m = pl < zc0 - 1 ? 0x18u : pl < zc0 ? 0x1cu : pl < zc1 ? 0xffu : pl == zc1 ? 0xdcu : 0x04u;
+        return m & ((1u << Cfg::NB) - 1u);
+    };
     auto issue = [&](int pl) {
         const int k = pl - pfirst;
+        const unsigned m = boxes(pl);
         float* dst = ring.stage(pl);
-        mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
+        mbar_arrive_expect_tx(&bar[k & (D - 1)], __popc(m) * BOX * sizeof(float));
         for (int b = 0; b < Cfg::NB; ++b)
-            tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+            if ((m >> b) & 1u) tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
@@ -373,12 +382,21 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
+    // boxes a ring plane needs: u^1, u^2, u^3 and 1/mu on the item's planes
+    // and on plane zc1 (the z averages of mu); the planes beyond the item
+    // otherwise feed only the z queues (u^1 and u^2 of plane pl, u^3 of plane
+    // pl-1); lambda is read at the own point only and comes from own-point
+    // loads (box order u^1, u^2, u^3, lambda, 1/mu)
+    auto boxes = [&](int pl) -> unsigned {
+        return pl < zc0 - 1 ? 0x04u : pl < zc0 ? 0x07u : pl <= zc1 ? 0x17u : 0x03u;
+    };
     auto issue = [&](int pl) {
         const int k = pl - pfirst;
+        const unsigned m = boxes(pl);
         float* dst = ring.stage(pl);
-        mbar_arrive_expect_tx(&bar[k & (D - 1)], Cfg::NB * BOX * sizeof(float));
+        mbar_arrive_expect_tx(&bar[k & (D - 1)], __popc(m) * BOX * sizeof(float));
         for (int b = 0; b < Cfg::NB; ++b)
-            tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
+            if ((m >> b) & 1u) tma_load_3d(dst + b * BOXS, &maps[Cfg::tm(b)], x0 - 4, y0 - 2, pl, &bar[k & (D - 1)]);
     };
     if (tid == 0)
         for (int pl = pfirst; pl < pfirst + D && pl <= plast; ++pl) issue(pl);
@@ -400,14 +418,16 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         __syncthreads();
     }
 
-    // own stresses and psi of the next output plane, loaded one visit ahead
+    // own stresses, lambda and psi of the next output plane, loaded one visit ahead
     float ns[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float nl = 0.f;
     float nps[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     auto prefetch = [&](int zn) {
         if (!own || zn < zc0 || zn >= zc1) return;
         const unsigned g = (unsigned)zn * nxy + gxy;
 #pragma unroll
         for (int v = 0; v < 6; ++v) ns[v] = p.s[v][g];
+        nl = __ldg(p.lam + g);
         if constexpr (PML) {
             const int lz = zslab(zn, p);
 #pragma unroll
@@ -448,6 +468,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         float so[6];
 #pragma unroll
         for (int v = 0; v < 6; ++v) so[v] = ns[v];
+        const float lam = nl;
         float cps[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -576,7 +597,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 if constexpr (PML) pml_z_init(pz, p, z);
                 const float* m0 = sz + Cfg::BMU * BOXS;
                 const float* m1 = sz1 + Cfg::BMU * BOXS;
-                const float lam = sz[Cfg::BLAM * BOXS + o], mu2 = 2.0f * mu_of(m0[o]);
+                const float mu2 = 2.0f * mu_of(m0[o]);
                 const float m12 = harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
                 const float m13 = harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
                 const float m23 = harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);
