@@ -382,13 +382,16 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         for (int b = 0; b < Cfg::NB; ++b) tma_prefetch_desc(&maps[Cfg::tm(b)]);
     }
     __syncthreads();
-    // boxes a ring plane needs: u^1, u^2, u^3 and 1/mu on the item's planes
-    // and on plane zc1 (the z averages of mu); the planes beyond the item
-    // otherwise feed only the z queues (u^1 and u^2 of plane pl, u^3 of plane
-    // pl-1); lambda is read at the own point only and comes from own-point
-    // loads (box order u^1, u^2, u^3, lambda, 1/mu)
+    // lambda is read at the own point only: bodies without x or y layer take
+    // it from own-point loads, the frame bodies (short of registers) from the
+    // staged box
+    constexpr bool LAMBOX = PXY;
+    // boxes a ring plane needs: u^1, u^2, u^3, 1/mu (and lambda) on the item's
+    // planes, u^1, u^2, u^3 and 1/mu on plane zc1 (the z averages of mu); the
+    // planes beyond the item otherwise feed only the z queues (u^1 and u^2 of
+    // plane pl, u^3 of plane pl-1) (box order u^1, u^2, u^3, lambda, 1/mu)
     auto boxes = [&](int pl) -> unsigned {
-        return pl < zc0 - 1 ? 0x04u : pl < zc0 ? 0x07u : pl <= zc1 ? 0x17u : 0x03u;
+        return pl < zc0 - 1 ? 0x04u : pl < zc0 ? 0x07u : pl < zc1 ? (LAMBOX ? 0x1fu : 0x17u) : pl == zc1 ? 0x17u : 0x03u;
     };
     auto issue = [&](int pl) {
         const int k = pl - pfirst;
@@ -427,7 +430,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         const unsigned g = (unsigned)zn * nxy + gxy;
 #pragma unroll
         for (int v = 0; v < 6; ++v) ns[v] = p.s[v][g];
-        nl = __ldg(p.lam + g);
+        if constexpr (!LAMBOX) nl = __ldg(p.lam + g);
         if constexpr (PML) {
             const int lz = zslab(zn, p);
 #pragma unroll
@@ -468,7 +471,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
         float so[6];
 #pragma unroll
         for (int v = 0; v < 6; ++v) so[v] = ns[v];
-        const float lam = nl;
+        const float lo = nl;  // lambda of plane z (own-point load, bodies without a lambda box)
         float cps[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -597,7 +600,7 @@ __device__ __forceinline__ bool str_body(const StepParams& p, const CUtensorMap*
                 if constexpr (PML) pml_z_init(pz, p, z);
                 const float* m0 = sz + Cfg::BMU * BOXS;
                 const float* m1 = sz1 + Cfg::BMU * BOXS;
-                const float mu2 = 2.0f * mu_of(m0[o]);
+                const float lam = LAMBOX ? sz[Cfg::BLAM * BOXS + o] : lo, mu2 = 2.0f * mu_of(m0[o]);
                 const float m12 = harm_inv(m0[o], m0[o + xc1], m0[o + yc1], m0[oxy]);
                 const float m13 = harm_inv(m0[o], m0[o + xc1], m1[o], m1[o + xc1]);
                 const float m23 = harm_inv(m0[o], m0[o + yc1], m1[o], m1[o + yc1]);

@@ -61,8 +61,9 @@ template <bool ADJ, int PM> struct VelCfg {
 
 template <bool ADJ, int PM> struct StrCfg {
     static constexpr bool PML = PM != PM_NONE, LX = has_x(PM), LY = has_y(PM), PXY = LX || LY;
-    // stage boxes 0..2: u (forward) or w (adjoint); 3 lambda (not staged: it
-    // is read at the own point only, from own-point loads), 4 1/mu.  Full
+    // stage boxes 0..2: u (forward) or w (adjoint); 3 lambda (staged for the
+    // frame bodies only; the others read it at the own point from own-point
+    // loads), 4 1/mu.  Full
     // C-PML adjoint blocks form the layer-augmented fields E in place (the
     // x-differenced ones) and keep the y-differenced ones, which differ inside
     // the layers, in three extra boxes.
