@@ -206,7 +206,7 @@ def algorithmic_bytes(kind, d, L, points=None, slab=None):
     kernels read once and write once at the points they update (neighbour
     reads served from cache are not counted).  This is the library's own
     per-role figure (the two-pass roles re-read the fields the other pass
-    wrote); the roofline's compulsory bytes are survey_bytes_per_step.  points / slab: grid
+    wrote); the roofline's compulsory bytes are compulsory_bytes_per_step.  points / slab: grid
     points and C-PML slab points the role updates (default: the whole grid)."""
     N = d.N if points is None else points
     S = sum(slab_points(d)) if slab is None else slab
@@ -232,7 +232,7 @@ def algorithmic_bytes(kind, d, L, points=None, slab=None):
     return 0
 
 
-def survey_bytes_per_step(d):
+def compulsory_bytes_per_step(d):
     """Compulsory DRAM bytes of one time step of one operator (H or H^T) over
     the whole grid, for the single-pass update of Eq. (it) with the C-PML of
     Appendix A.3: the nine wavefield fields read once and written once (72 B)
@@ -466,13 +466,13 @@ def run_ours(args):
     g.profile(False)
 
     # roofline of the whole step pair (measured live over the timed region):
-    # the compulsory bytes of the single-pass update (survey_bytes_per_step)
+    # the compulsory bytes of the single-pass update (compulsory_bytes_per_step)
     # of H and of H^T over the device time of one forward + adjoint step
     pk, which = peaks()
     steps_kinds = ["fwd_velocity", "fwd_stress", "adj_a", "adj_b", "fwd_fused", "adj_fused", "fwd_ac_vel",
                    "fwd_ac_str", "adj_ac_a", "adj_ac_b"]
     pts = {k: g.role_points(k) for k in steps_kinds}
-    pair_bytes = 2.0 * survey_bytes_per_step(d)
+    pair_bytes = 2.0 * compulsory_bytes_per_step(d)
     achieved = pair_bytes / (ms / K * 1e-3) / 1e9
     wl = args.workload + (" mu=0" if args.mu0 else "")
     ran = [k for k in steps_kinds if prof[k][0]]

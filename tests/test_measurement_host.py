@@ -149,9 +149,9 @@ def test_compulsory_bytes_of_the_single_pass_step():
     slab planes per axis) that is 99.53 B per update, 26.7 GB per forward +
     adjoint step pair; a 7.581 ms step pair then runs at 0.554 of 6429 GB/s."""
     d = synth.GridDesc(512, 512, 512, 0.2e-3, 19.7e-9, npml=20)
-    b = bench.survey_bytes_per_step(d)
+    b = bench.compulsory_bytes_per_step(d)
     assert b == 88 * d.N + 48 * 3 * 512 * 512 * 41
     assert b / d.N == pytest.approx(99.53, abs=5e-3)
     assert 2 * b / 7.581e-3 / 1e9 / 6429.0 == pytest.approx(0.548, abs=2e-3)
     d0 = synth.GridDesc(64, 64, 64, 0.5e-3, 1e-7, npml=0)
-    assert bench.survey_bytes_per_step(d0) == 88 * 64 ** 3
+    assert bench.compulsory_bytes_per_step(d0) == 88 * 64 ** 3
