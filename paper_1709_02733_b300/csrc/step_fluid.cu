@@ -70,7 +70,9 @@ static_assert(VelFl<true, PM_FULL>::SMEM >= VelFl<true, PM_X>::SMEM && VelFl<tru
                   StrFl<false, PM_FULL>::SMEM >= StrFl<false, PM_X>::SMEM,
               "corner layout covers the other fluid bodies");
 // the edge kernels run the PM_X and PM_Y bodies with one layout
-static_assert(VelFl<true, PM_X>::SMEM == VelFl<true, PM_Y>::SMEM && StrFl<true, PM_X>::SMEM == StrFl<true, PM_Y>::SMEM,
+static_assert(VelFl<true, PM_X>::SMEM == VelFl<true, PM_Y>::SMEM && StrFl<true, PM_X>::SMEM == StrFl<true, PM_Y>::SMEM &&
+                  VelFl<false, PM_X>::SMEM == VelFl<false, PM_Y>::SMEM &&
+                  StrFl<false, PM_X>::SMEM == StrFl<false, PM_Y>::SMEM,
               "edge bodies share one layout");
 
 // ---------------------------------------------------------------------------
