@@ -227,7 +227,7 @@ def _free_port():
 def test_slab_march_equals_whole_grid(world):
     tr_w, img_w = _whole()
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         got = dict(out)
