@@ -47,7 +47,7 @@ def test_gradient_finite_differences(case):
         eps = 1.0
         fd = (_loss(g, w, p.detach() + eps * d, y) - _loss(g, w, p.detach() - eps * d, y)) / (2 * eps)
         an = float(torch.dot(grad.flatten().double(), d.flatten().double()))
-        assert abs(fd - an) <= 1e-4 * max(abs(fd), 1e-3 * float(loss)), (k, fd, an)
+        assert abs(fd - an) <= 1e-4 * max(abs(fd), 1e-3 * float(loss.detach())), (k, fd, an)
 
 
 def test_gradient_matches_oracle(case):
